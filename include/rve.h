@@ -1,0 +1,219 @@
+/*
+ * librve -- batched RVE computational homogenisation on one NVIDIA GB300.
+ *
+ * C ABI of the hot path of Ullah, Kaczmarczyk, Grammatikos, Evernden, Pearce,
+ * "Multi-scale computational homogenisation to predict the long-term
+ * durability of composite structures" (arXiv 1610.03484):
+ *
+ *   macro Gauss point (T, c, t) --degradation law (Sec. 4)--> constituent
+ *   tensors --RVE cell problems (Sec. 2)--> homogenised stiffness C (6x6),
+ *   thermal conductivity K (3x3) and moisture diffusivity D (3x3).
+ *
+ * Conventions shared by every call
+ *  - Return value: RVE_OK (0) or a negative RVE_ERR_* code.  rve_strerror()
+ *    names a code; rve_last_error() returns a thread-local detail string for
+ *    the last failing call on the calling thread.
+ *  - Handles (rve_ctx, rve_mesh) are opaque and library-owned.  All device
+ *    memory behind them is allocated by the library with cudaMalloc on the
+ *    context's device and freed by rve_mesh_free / rve_destroy.
+ *  - Host arrays passed in are read during the call only (copied); host
+ *    arrays passed out are written before the call returns.  Functions whose
+ *    name ends in _dev take device pointers instead and run on the context's
+ *    stream; they return after enqueueing all work and the caller synchronises.
+ *  - Units are SI on input and output (Pa, W/(m K), m^2/s, deg C, hours).
+ *  - Voigt order is the paper's (Sec. 2, definition of the macro strain):
+ *    strain (e11, e22, e33, 2e12, 2e23, 2e31), stress (s11, s22, s33, s12,
+ *    s23, s31).  C is returned row-major, C[6*i + j] = dsigma_i / deps_j.
+ *  - Not thread-safe per context: calls on one rve_ctx must be serialised.
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define RVE_OK                    0
+#define RVE_ERR_INVALID_ARGUMENT (-1)  /* null pointer, size or enum out of range */
+#define RVE_ERR_BAD_MESH         (-2)  /* degenerate tet, bad index, unmatched periodic faces */
+#define RVE_ERR_NOT_SPD          (-3)  /* constituent tensor not positive definite */
+#define RVE_ERR_NOT_CONVERGED    (-4)  /* PCG hit max_iter before rtol (results still written) */
+#define RVE_ERR_NUMERIC          (-5)  /* NaN / Inf met in a reduction */
+#define RVE_ERR_CUDA             (-6)  /* a CUDA runtime call failed (detail in rve_last_error) */
+#define RVE_ERR_NO_DEVICE        (-7)  /* no CUDA device or wrong architecture */
+#define RVE_ERR_OUT_OF_MEMORY    (-8)  /* device allocation failed */
+#define RVE_ERR_STATE            (-9)  /* call order violated (e.g. homogenise before set_materials) */
+#define RVE_ERR_TIMEOUT         (-10)  /* a bounded device wait gave up */
+
+/* ------------------------------------------------------------- enumerations */
+/* RVE boundary conditions of Sec. 2 (unified constraint approach,
+ * Eqs. eq_RVE_disc_Eqs / eq_mat_C_and_D). */
+#define RVE_BC_DIRICHLET 0   /* linear boundary displacement: fluctuation = 0 on the boundary */
+#define RVE_BC_PERIODIC  1   /* periodic fluctuation, anti-periodic traction */
+#define RVE_BC_NEUMANN   2   /* uniform traction t = sigma_bar n */
+
+#define RVE_PREC_FP64    0   /* FP64 operator, vectors and reductions */
+#define RVE_PREC_MIXED   1   /* FP32 operator and vectors, FP64 scalars, FP64 residual refinement */
+
+#define RVE_MODE_PCG     0   /* macro_update_gauss_points: plain batched PCG for every point */
+
+/* ------------------------------------------------------------------ types */
+typedef struct rve_ctx_s*  rve_ctx;
+typedef struct rve_mesh_s* rve_mesh;
+
+typedef struct rve_options {
+    int     device;          /* CUDA device ordinal (default 0) */
+    int     precision;       /* RVE_PREC_FP64 or RVE_PREC_MIXED (default FP64) */
+    double  rtol;            /* relative residual target of the cell solves (default 1e-10) */
+    int     max_iter;        /* PCG iteration cap per solve (default 20000) */
+    double  inner_rtol;      /* MIXED: relative tolerance of each FP32 inner solve (default 1e-6) */
+    int     max_refine;      /* MIXED: maximum FP64 refinement sweeps (default 4) */
+    int     check_every;     /* iterations between host convergence checks (default 16) */
+    int     batch;           /* RVEs solved together in macro_update_gauss_points, 0 = auto */
+    void*   stream;          /* cudaStream_t to run on; NULL = library-created stream */
+} rve_options;
+
+/* Isotropic matrix phase (Sec. 1, Sec. 7). */
+typedef struct rve_matrix_props {
+    double E;    /* Young's modulus [Pa] */
+    double nu;   /* Poisson ratio */
+    double k;    /* thermal conductivity [W/(m K)] */
+    double d;    /* moisture diffusivity [m^2/s] */
+} rve_matrix_props;
+
+/* Transversely isotropic yarn, axis 1 along the local fibre direction (Sec. 6). */
+typedef struct rve_yarn_props {
+    double E1, E2, G12, nu12, nu23;   /* [Pa], [Pa], [Pa], -, - */
+    double k1, k2;                    /* conductivity along / across the fibre */
+    double d1, d2;                    /* diffusivity along / across the fibre */
+} rve_yarn_props;
+
+/* Degradation law of Sec. 4 (Eqs. alphaT, Model_final1):
+ *   1 - omega = exp(-c * beta * ln(1 - T/Tg) * t), T and Tg in kelvin,
+ *   c = clamp(c_wt / c_sat_wt, 0, 1), t in days = t_h / 24.
+ * It scales the matrix Young's modulus (Sec. 5: only the matrix degrades);
+ * apply_to_yarn != 0 scales the yarn moduli by the same factor. */
+typedef struct rve_degradation {
+    double beta;        /* [1/day], paper: -0.001682 */
+    double Tg_C;        /* glass transition [deg C], paper: 126 */
+    double c_sat_wt;    /* moisture content that maps to c = 1 [wt%] */
+    int    apply_to_yarn;
+} rve_degradation;
+
+typedef struct rve_mesh_stats {
+    int64_t n_vertices, n_edges, n_faces, n_tets;   /* after periodic folding if periodic */
+    int64_t n_scalar_dofs;                          /* V + (p-1)E + (p-1)(p-2)/2 F */
+    int64_t n_constrained;                          /* Dirichlet-masked scalar DOFs */
+    int32_t p, bc;
+    double  volume;
+} rve_mesh_stats;
+
+typedef struct rve_stats {
+    int32_t iterations_mech;      /* PCG iterations, mechanical solve (max over RHS and batch) */
+    int32_t iterations_scalar;    /* PCG iterations, thermal + moisture solve */
+    int32_t refine_sweeps;        /* MIXED: FP64 residual refinement sweeps */
+    int32_t converged;            /* 1 if every RHS reached rtol */
+    double  rel_residual_mech;    /* final relative residual (max over RHS) */
+    double  rel_residual_scalar;
+    double  hill_mandel_mech;     /* |C_energy - C_sigma| / |C| (Eq. Hill_prin check) */
+    double  hill_mandel_scalar;
+    double  seconds;              /* wall time of the call */
+    int64_t kernel_launches;      /* device kernels launched by the call */
+    double  op_ms;                /* summed device time of operator launches (profile mode) */
+    int64_t op_launches;          /* operator launches counted in op_ms */
+} rve_stats;
+
+/* ------------------------------------------------------------------ calls */
+const char* rve_strerror(int code);
+const char* rve_last_error(void);
+void        rve_default_options(rve_options* opts);
+
+/* Context on one device.  opts may be NULL (defaults).  Fails with
+ * RVE_ERR_NO_DEVICE when no sm_103 device is present. */
+int rve_create(rve_ctx* out, const rve_options* opts);
+int rve_destroy(rve_ctx ctx);
+int rve_set_options(rve_ctx ctx, const rve_options* opts);
+int rve_get_options(rve_ctx ctx, rve_options* opts);
+
+/* Tetrahedral RVE mesh with hierarchic H1 basis of order p (Sec. 1, Sec. 7):
+ *   xyz [nv][3] vertex coordinates, tets [nt][4] vertex indices (any orientation),
+ *   phase [nt] 0 = matrix, 1 = yarn, fibre_dir [nt][3] yarn axis (need not be
+ *   normalised; ignored for matrix tets; NULL = x axis), p in 1..3.
+ * The box must be axis aligned with matching opposite faces if the periodic
+ * BC is used later.  The default BC is periodic. */
+int rve_mesh_load(rve_ctx ctx, const double* xyz, int64_t nv, const int32_t* tets, int64_t nt,
+                  const uint8_t* phase, const double* fibre_dir, int p, rve_mesh* out);
+int rve_mesh_free(rve_ctx ctx, rve_mesh mesh);
+int rve_mesh_info(rve_ctx ctx, rve_mesh mesh, rve_mesh_stats* out);
+
+/* Constituent properties and the degradation state (T_C, c_wt, t_h) of the
+ * macro point this RVE serves (Sec. 4, Sec. 5).  deg may be NULL: paper
+ * constants, matrix only.  Fails with RVE_ERR_NOT_SPD for non-physical
+ * constants. */
+int rve_set_materials(rve_ctx ctx, rve_mesh mesh, const rve_matrix_props* matrix,
+                      const rve_yarn_props* yarn, double T_C, double c_wt, double t_h,
+                      const rve_degradation* deg);
+
+/* Boundary condition switch of the unified constraint approach (Sec. 2). */
+int rve_set_bc(rve_ctx ctx, rve_mesh mesh, int bc);
+
+/* Solve the 6 mechanical and 3 + 3 transport unit cell problems (Eq. Eq_C_stress
+ * and its scalar counterpart) and return C (row-major 6x6), K and D (3x3).
+ * Any output pointer may be NULL; stats may be NULL.  Returns
+ * RVE_ERR_NOT_CONVERGED (outputs still written) if rtol was not reached. */
+int rve_homogenise(rve_ctx ctx, rve_mesh mesh, double* C, double* K, double* D, rve_stats* stats);
+
+/* Batched FE^2 evaluation (Sec. 5): for G macro Gauss points with states
+ * (T_C[g], c_wt[g], t_h[g]) and RVE meshes[mesh_id[g]] (each with materials and
+ * BC already set; the per-point state replaces the mesh's own), write
+ * C[g*36..], K[g*9..], D[g*9..] and status[g] (RVE_OK or a negative code).
+ * Points sharing a mesh are solved together, `batch` RVEs per device pass.
+ * Host arrays; the copy in and out is part of the call. */
+int macro_update_gauss_points(rve_ctx ctx, const rve_mesh* meshes, int n_meshes, int64_t G,
+                              const double* T_C, const double* c_wt, const double* t_h,
+                              const int32_t* mesh_id, double* C, double* K, double* D,
+                              int32_t* status, int mode, rve_stats* stats);
+
+/* Same with device-resident inputs and outputs (all pointers on the context's
+ * device); mesh_id_host is the host copy of mesh_id used for scheduling. */
+int macro_update_gauss_points_dev(rve_ctx ctx, const rve_mesh* meshes, int n_meshes, int64_t G,
+                                  const double* T_C_dev, const double* c_wt_dev,
+                                  const double* t_h_dev, const int32_t* mesh_id_host,
+                                  double* C_dev, double* K_dev, double* D_dev,
+                                  int32_t* status_dev, int mode, rve_stats* stats);
+
+/* ---------------------------------------------------- inspection entry points
+ * These expose single steps of the path for parity tests. */
+
+/* Degradation factor 1 - omega for n states, computed on the device by the
+ * same kernel the batched path uses (Sec. 4, Eq. Model_final1).  deg NULL =
+ * paper constants. */
+int rve_degradation_factor(rve_ctx ctx, int64_t n, const double* T_C, const double* c_wt,
+                           const double* t_h, const rve_degradation* deg, double* out);
+
+/* Per-tet constituent tensors after rve_set_materials, as built on the device
+ * (FP64): stiffness [nt][6][6] (Voigt, Pa), conductivity [nt][3][3],
+ * diffusivity [nt][3][3].  Any output may be NULL. */
+int rve_mesh_get_tensors(rve_ctx ctx, rve_mesh mesh, double* stiffness, double* conductivity,
+                         double* diffusivity);
+
+/* Apply the assembled-free operator y = K x of one field on the mesh's DOF
+ * numbering (the current BC's; no constraint applied).  field 0 = mechanics
+ * (x, y [n_scalar_dofs][3][ncols]), 1 = thermal, 2 = moisture
+ * ([n_scalar_dofs][ncols]); units of the current materials; FP64. */
+int rve_apply_operator(rve_ctx ctx, rve_mesh mesh, int field, int ncols, const double* x,
+                       double* y);
+
+/* Hierarchic DOF map of the current BC: edofs [nt][n_local] scalar DOF index of
+ * each local function (4 vertex, then 6 quadratic edge, 6 cubic edge, 4 face
+ * functions as p allows) and the vertex order used by each tet [nt][4]. */
+int rve_mesh_get_dofmap(rve_ctx ctx, rve_mesh mesh, int32_t* edofs, int32_t* local_vertices);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RVE_H */

@@ -1,0 +1,315 @@
+"""Python binding of librve (C ABI in include/rve.h): argument marshalling only.
+
+Every step of the homogenisation runs inside librve's CUDA kernels; this
+module converts numpy arrays to pointers and error codes to exceptions.  There
+is no CPU fallback: if librve.so is missing or no GB300 is visible, calls fail
+with ``RveError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librve.so")
+
+RVE_OK = 0
+ERRORS = {
+    -1: "INVALID_ARGUMENT", -2: "BAD_MESH", -3: "NOT_SPD", -4: "NOT_CONVERGED", -5: "NUMERIC",
+    -6: "CUDA", -7: "NO_DEVICE", -8: "OUT_OF_MEMORY", -9: "STATE", -10: "TIMEOUT",
+}
+BC_DIRICHLET, BC_PERIODIC, BC_NEUMANN = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+MODE_PCG = 0
+
+
+class RveError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: RVE_ERR_{ERRORS.get(code, code)} ({detail})")
+
+
+class Options(C.Structure):
+    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
+                ("max_iter", C.c_int), ("inner_rtol", C.c_double), ("max_refine", C.c_int),
+                ("check_every", C.c_int), ("batch", C.c_int), ("stream", C.c_void_p)]
+
+
+class MatrixProps(C.Structure):
+    _fields_ = [("E", C.c_double), ("nu", C.c_double), ("k", C.c_double), ("d", C.c_double)]
+
+
+class YarnProps(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("E1", "E2", "G12", "nu12", "nu23", "k1", "k2", "d1", "d2")]
+
+
+class Degradation(C.Structure):
+    _fields_ = [("beta", C.c_double), ("Tg_C", C.c_double), ("c_sat_wt", C.c_double),
+                ("apply_to_yarn", C.c_int)]
+
+
+class MeshStats(C.Structure):
+    _fields_ = [("n_vertices", C.c_int64), ("n_edges", C.c_int64), ("n_faces", C.c_int64),
+                ("n_tets", C.c_int64), ("n_scalar_dofs", C.c_int64), ("n_constrained", C.c_int64),
+                ("p", C.c_int32), ("bc", C.c_int32), ("volume", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations_mech", C.c_int32), ("iterations_scalar", C.c_int32),
+                ("refine_sweeps", C.c_int32), ("converged", C.c_int32),
+                ("rel_residual_mech", C.c_double), ("rel_residual_scalar", C.c_double),
+                ("hill_mandel_mech", C.c_double), ("hill_mandel_scalar", C.c_double),
+                ("seconds", C.c_double), ("kernel_launches", C.c_int64), ("op_ms", C.c_double),
+                ("op_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "rve_strerror": (C.c_char_p, [C.c_int]),
+    "rve_last_error": (C.c_char_p, []),
+    "rve_default_options": (None, [C.POINTER(Options)]),
+    "rve_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Options)]),
+    "rve_destroy": (C.c_int, [C.c_void_p]),
+    "rve_set_options": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
+    "rve_get_options": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
+    "rve_mesh_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "rve_mesh_free": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rve_mesh_info": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(MeshStats)]),
+    "rve_set_materials": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(MatrixProps), C.POINTER(YarnProps),
+                                    C.c_double, C.c_double, C.c_double, C.POINTER(Degradation)]),
+    "rve_set_bc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "rve_homogenise": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(Stats)]),
+    "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Stats)]),
+    "macro_update_gauss_points_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
+                                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                                C.POINTER(Stats)]),
+    "rve_degradation_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.POINTER(Degradation), C.c_void_p]),
+    "rve_mesh_get_tensors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "rve_mesh_get_dofmap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librve.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RveError(-6, "load_library", f"{path} not built; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int, where: str, allow=()):
+    if rc != RVE_OK and rc not in allow:
+        detail = _lib.rve_last_error().decode(errors="replace") if _lib else ""
+        raise RveError(rc, where, detail)
+    return rc
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def default_options() -> Options:
+    lib = load_library()
+    o = Options()
+    lib.rve_default_options(C.byref(o))
+    return o
+
+
+@dataclass
+class Result:
+    C: np.ndarray
+    K: np.ndarray
+    D: np.ndarray
+    stats: dict
+    code: int
+
+
+class Context:
+    """One librve context (device + stream).  Use as a context manager."""
+
+    def __init__(self, precision=PREC_FP64, rtol=1e-10, max_iter=20000, inner_rtol=1e-6,
+                 max_refine=4, check_every=16, batch=0, stream=None, device=0):
+        lib = load_library()
+        o = default_options()
+        o.device, o.precision, o.rtol, o.max_iter = device, precision, rtol, max_iter
+        o.inner_rtol, o.max_refine, o.check_every, o.batch = inner_rtol, max_refine, check_every, batch
+        o.stream = stream
+        h = C.c_void_p()
+        _check(lib.rve_create(C.byref(h), C.byref(o)), "rve_create")
+        self.h = h
+        self.lib = lib
+
+    def set_options(self, **kw):
+        o = Options()
+        _check(self.lib.rve_get_options(self.h, C.byref(o)), "rve_get_options")
+        for k, v in kw.items():
+            setattr(o, k, v)
+        _check(self.lib.rve_set_options(self.h, C.byref(o)), "rve_set_options")
+
+    def close(self):
+        if self.h:
+            self.lib.rve_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------------- mesh
+    def mesh_load(self, xyz, tets, p, phase=None, fibre_dir=None) -> "Mesh":
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        tets = np.ascontiguousarray(tets, np.int32)
+        ph = None if phase is None else np.ascontiguousarray(phase, np.uint8)
+        fd = None if fibre_dir is None else np.ascontiguousarray(fibre_dir, np.float64)
+        h = C.c_void_p()
+        _check(self.lib.rve_mesh_load(self.h, _ptr(xyz), len(xyz), _ptr(tets), len(tets), _ptr(ph), _ptr(fd),
+                                      int(p), C.byref(h)), "rve_mesh_load")
+        return Mesh(self, h, len(tets), int(p))
+
+    def degradation_factor(self, T_C, c_wt, t_h, beta=-0.001682, Tg_C=126.0, c_sat_wt=1.5):
+        T = np.ascontiguousarray(T_C, np.float64)
+        c = np.ascontiguousarray(c_wt, np.float64)
+        t = np.ascontiguousarray(t_h, np.float64)
+        out = np.zeros_like(T)
+        dg = Degradation(beta, Tg_C, c_sat_wt, 0)
+        _check(self.lib.rve_degradation_factor(self.h, len(T), _ptr(T), _ptr(c), _ptr(t), C.byref(dg),
+                                               _ptr(out)), "rve_degradation_factor")
+        return out
+
+    def macro_update(self, meshes, T_C, c_wt, t_h, mesh_id, allow_not_converged=False):
+        G = len(T_C)
+        arr = (C.c_void_p * len(meshes))(*[m.h for m in meshes])
+        T = np.ascontiguousarray(T_C, np.float64)
+        c = np.ascontiguousarray(c_wt, np.float64)
+        t = np.ascontiguousarray(t_h, np.float64)
+        mid = np.ascontiguousarray(mesh_id, np.int32)
+        Cc = np.zeros((G, 6, 6))
+        Kk = np.zeros((G, 3, 3))
+        Dd = np.zeros((G, 3, 3))
+        st = np.zeros(G, np.int32)
+        s = Stats()
+        allow = (-4,) if allow_not_converged else ()
+        rc = _check(self.lib.macro_update_gauss_points(self.h, arr, len(meshes), G, _ptr(T), _ptr(c), _ptr(t),
+                                                       _ptr(mid), _ptr(Cc), _ptr(Kk), _ptr(Dd), _ptr(st),
+                                                       MODE_PCG, C.byref(s)),
+                    "macro_update_gauss_points", allow)
+        return Cc, Kk, Dd, st, s.as_dict(), rc
+
+    def macro_update_dev(self, meshes, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev, D_dev, status_dev):
+        """Device-pointer variant: every *_dev argument is an integer device address."""
+        G = len(mesh_id_host)
+        arr = (C.c_void_p * len(meshes))(*[m.h for m in meshes])
+        mid = np.ascontiguousarray(mesh_id_host, np.int32)
+        s = Stats()
+        rc = _check(self.lib.macro_update_gauss_points_dev(self.h, arr, len(meshes), G, C.c_void_p(T_dev),
+                                                           C.c_void_p(c_dev), C.c_void_p(t_dev), _ptr(mid),
+                                                           C.c_void_p(C_dev), C.c_void_p(K_dev),
+                                                           C.c_void_p(D_dev), C.c_void_p(status_dev),
+                                                           MODE_PCG, C.byref(s)),
+                    "macro_update_gauss_points_dev", (-4,))
+        return s.as_dict(), rc
+
+
+class Mesh:
+    def __init__(self, ctx: Context, h, nt: int, p: int):
+        self.ctx, self.h, self.nt, self.p = ctx, h, nt, p
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.rve_mesh_free(self.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            if self.ctx.h:
+                self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        s = MeshStats()
+        _check(self.ctx.lib.rve_mesh_info(self.ctx.h, self.h, C.byref(s)), "rve_mesh_info")
+        return {n: getattr(s, n) for n, _ in s._fields_}
+
+    def set_materials(self, matrix, yarn, T_C=20.0, c_wt=0.0, t_h=0.0, beta=-0.001682, Tg_C=126.0,
+                      c_sat_wt=1.5, apply_to_yarn=False):
+        mp = MatrixProps(matrix.E, matrix.nu, matrix.k, matrix.d)
+        yp = YarnProps(yarn.E1, yarn.E2, yarn.G12, yarn.nu12, yarn.nu23, yarn.k1, yarn.k2, yarn.d1, yarn.d2)
+        dg = Degradation(beta, Tg_C, c_sat_wt, int(apply_to_yarn))
+        _check(self.ctx.lib.rve_set_materials(self.ctx.h, self.h, C.byref(mp), C.byref(yp), T_C, c_wt, t_h,
+                                              C.byref(dg)), "rve_set_materials")
+
+    def set_bc(self, bc: int):
+        _check(self.ctx.lib.rve_set_bc(self.ctx.h, self.h, int(bc)), "rve_set_bc")
+
+    def homogenise(self, allow_not_converged=False) -> Result:
+        Cc = np.zeros((6, 6))
+        Kk = np.zeros((3, 3))
+        Dd = np.zeros((3, 3))
+        s = Stats()
+        allow = (-4,) if allow_not_converged else ()
+        rc = _check(self.ctx.lib.rve_homogenise(self.ctx.h, self.h, _ptr(Cc), _ptr(Kk), _ptr(Dd), C.byref(s)),
+                    "rve_homogenise", allow)
+        return Result(Cc, Kk, Dd, s.as_dict(), rc)
+
+    def tensors(self):
+        D = np.zeros((self.nt, 6, 6))
+        K = np.zeros((self.nt, 3, 3))
+        Dd = np.zeros((self.nt, 3, 3))
+        _check(self.ctx.lib.rve_mesh_get_tensors(self.ctx.h, self.h, _ptr(D), _ptr(K), _ptr(Dd)),
+               "rve_mesh_get_tensors")
+        return D, K, Dd
+
+    def apply_operator(self, field: int, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, np.float64)
+        ncols = x.shape[-1]
+        y = np.zeros_like(x)
+        _check(self.ctx.lib.rve_apply_operator(self.ctx.h, self.h, int(field), int(ncols), _ptr(x), _ptr(y)),
+               "rve_apply_operator")
+        return y
+
+    def dofmap(self):
+        ne = {1: 4, 2: 10, 3: 20}[self.p]
+        ed = np.zeros((self.nt, ne), np.int32)
+        lv = np.zeros((self.nt, 4), np.int32)
+        _check(self.ctx.lib.rve_mesh_get_dofmap(self.ctx.h, self.h, _ptr(ed), _ptr(lv)), "rve_mesh_get_dofmap")
+        return ed, lv
+
+
+__all__ = ["Context", "Mesh", "RveError", "load_library", "exported_symbols", "BC_DIRICHLET", "BC_PERIODIC",
+           "BC_NEUMANN", "PREC_FP64", "PREC_MIXED", "Options", "Stats"]

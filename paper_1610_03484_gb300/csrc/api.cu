@@ -1,0 +1,1192 @@
+// C ABI of librve: handles, mesh set-up, the multi-RHS projected PCG driver
+// and the homogenised-tensor assembly.  Device work lives in kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "rve_internal.h"
+
+namespace rve {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& s) { g_last_error = s; }
+
+#define RVE_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
+            return e_ == cudaErrorMemoryAllocation ? RVE_ERR_OUT_OF_MEMORY : RVE_ERR_CUDA; \
+        }                                                                                \
+    } while (0)
+
+#define RVE_TRY(call)          \
+    do {                       \
+        int rc_ = (call);      \
+        if (rc_ != RVE_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------------ device buffer
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int ensure(size_t b) {
+        if (b <= bytes && p) return RVE_OK;
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return RVE_ERR_OUT_OF_MEMORY;
+        }
+        bytes = b;
+        return RVE_OK;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+template <typename T>
+static int upload(DevBuf& d, const T* h, size_t n, cudaStream_t s) {
+    RVE_TRY(d.ensure(n * sizeof(T)));
+    if (n) RVE_CUDA(cudaMemcpyAsync(d.p, h, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return RVE_OK;
+}
+
+// Constraint rows and preconditioner data of one field on the current BC.
+struct FieldDev {
+    int nc = 3;
+    int nfield = 1;
+    int64_t n_rows = 0;
+    DevBuf diag64, diag32, mask;
+    int m = 0;
+    int64_t n_sup = 0;
+    DevBuf sup_row, sup_coef, sup_of_row;
+};
+
+}  // namespace rve
+
+using namespace rve;
+
+struct rve_ctx_s {
+    rve_options opt;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int64_t launches = 0;
+};
+
+struct rve_mesh_s {
+    rve_ctx ctx = nullptr;
+    int p = 1;
+    int bc = RVE_BC_DIRICHLET;
+    int64_t nv = 0, nt = 0;
+    std::vector<double> xyz;
+    std::vector<int32_t> tets;
+    std::vector<uint8_t> phase;
+    std::vector<double> tangent;
+    DofMap map;
+    double volume = 0;
+    // device mesh
+    DevBuf d_xyz, d_edofs, d_lverts, d_geo64, d_geo32, d_phase, d_tangent, d_flag;
+    DevBuf d_matm64, d_matm32, d_mats64, d_mats32;
+    FieldDev mech, scal;
+    bool have_materials = false;
+    MaterialConsts mc{};
+    rve_degradation deg{};
+    double T_C = 20, c_wt = 0, t_h = 0;
+    // solve workspace
+    DevBuf x64, r64, b64, p64, q64, x32, r32, p32, q32;
+    DevBuf epart, rzp, cpart, gpart, mpart, gsum, msum;
+    DevBuf colstate, scale64, scale32, wdev;
+    int64_t ws_rows = 0;
+    int ws_cols = 0;
+};
+
+namespace {
+
+int check_ctx(rve_ctx c) {
+    if (!c) {
+        set_error("null context");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    cudaSetDevice(c->device);
+    return RVE_OK;
+}
+
+// ------------------------------------------------------------ geometry + map
+int rebuild_map(rve_mesh m) {
+    cudaStream_t s = m->ctx->stream;
+    std::string err;
+    int rc = build_dofmap(m->xyz.data(), m->nv, m->tets.data(), m->nt, m->p,
+                          m->bc == RVE_BC_PERIODIC, m->map, err);
+    if (rc != RVE_OK) {
+        set_error(err);
+        return rc;
+    }
+    const int ne = n_local(m->p);
+    RVE_TRY(upload(m->d_edofs, m->map.edofs.data(), (size_t)m->nt * ne, s));
+    RVE_TRY(upload(m->d_lverts, m->map.lverts.data(), (size_t)m->nt * 4, s));
+    RVE_TRY(m->d_geo64.ensure(sizeof(double) * m->nt * 10));
+    RVE_TRY(m->d_geo32.ensure(sizeof(float) * m->nt * 10));
+    RVE_TRY(m->d_flag.ensure(sizeof(int32_t) * 4));
+    RVE_CUDA(cudaMemsetAsync(m->d_flag.p, 0, sizeof(int32_t) * 4, s));
+    launch_geometry(m->nt, m->d_xyz.as<double>(), m->d_lverts.as<int32_t>(), m->d_geo64.as<double>(),
+                    m->d_geo32.as<float>(), m->d_flag.as<int32_t>(), s);
+    m->ctx->launches++;
+    int32_t bad = 0;
+    RVE_CUDA(cudaMemcpyAsync(&bad, m->d_flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    if (bad) {
+        set_error("degenerate (zero-volume) tetrahedron");
+        return RVE_ERR_BAD_MESH;
+    }
+    return RVE_OK;
+}
+
+// Constraint rows of the current BC (FP64), normalised per row.
+int build_constraints(rve_mesh m, FieldDev& f, const std::vector<double>& geo) {
+    cudaStream_t s = m->ctx->stream;
+    const DofMap& M = m->map;
+    const int nc = f.nc;
+    const int64_t N = M.N;
+    f.n_rows = N * nc;
+    // Dirichlet mask
+    std::vector<uint8_t> mask;
+    if (m->bc == RVE_BC_DIRICHLET) mask = M.boundary;
+    RVE_TRY(upload(f.mask, mask.data(), mask.size(), s));
+    f.m = 0;
+    f.n_sup = 0;
+    if (m->bc == RVE_BC_DIRICHLET) return RVE_OK;
+
+    // vertex coordinates relative to the centroid (rotation rows)
+    double cen[3] = {0, 0, 0};
+    int64_t nvx = 0;
+    for (int64_t d = 0; d < N; ++d)
+        if (M.dof_vertex[d] >= 0) {
+            for (int a = 0; a < 3; ++a) cen[a] += m->xyz[3 * M.dof_vertex[d] + a];
+            ++nvx;
+        }
+    for (int a = 0; a < 3; ++a) cen[a] /= std::max<int64_t>(nvx, 1);
+    // g_d = int_Omega grad phi_d (Neumann strain / flux rows), nonzero on boundary DOFs only
+    std::vector<double> g;
+    const bool neu = m->bc == RVE_BC_NEUMANN;
+    if (neu) {
+        g.assign(N * 3, 0.0);
+        const Basis& B = basis(m->p);
+        const int ne = B.ne, nm = B.nm;
+        for (int64_t e = 0; e < m->nt; ++e) {
+            const double* G = &geo[e * 10];
+            for (int j = 0; j < ne; ++j) {
+                double a[3];
+                for (int k = 0; k < 3; ++k) a[k] = B.A[(k * nm + 0) * ne + j];
+                const int64_t d = M.edofs[e * ne + j];
+                for (int l = 0; l < 3; ++l)
+                    g[d * 3 + l] += G[9] * (a[0] * G[l] + a[1] * G[3 + l] + a[2] * G[6 + l]);
+            }
+        }
+    }
+    const int m_rows = nc == 3 ? (neu ? 12 : 3) : (neu ? 4 : 1);
+    f.m = m_rows;
+    std::vector<int64_t> rows;
+    std::vector<double> coef;
+    for (int64_t d = 0; d < N; ++d) {
+        const bool isv = M.dof_vertex[d] >= 0;
+        const bool isb = neu && M.boundary[d];
+        if (!isv && !isb) continue;
+        double y[3] = {0, 0, 0};
+        if (isv)
+            for (int a = 0; a < 3; ++a) y[a] = m->xyz[3 * M.dof_vertex[d] + a] - cen[a];
+        for (int c = 0; c < nc; ++c) {
+            std::vector<double> cr(m_rows, 0.0);
+            if (nc == 3) {
+                if (isv) {
+                    cr[c] = 1.0;   // translation c
+                    if (neu) {
+                        // rotation k: (e_k x y)_c
+                        const double rot[3][3] = {{0, -y[2], y[1]}, {y[2], 0, -y[0]}, {-y[1], y[0], 0}};
+                        for (int k = 0; k < 3; ++k) cr[3 + k] = rot[k][c];
+                    }
+                }
+                if (isb) {
+                    // strain rows: (E_k g_d)_c with E_k the Voigt basis of symmetric tensors
+                    const double* gd = &g[d * 3];
+                    static const int VI[6] = {0, 1, 2, 0, 1, 2}, VJ[6] = {0, 1, 2, 1, 2, 0};
+                    for (int k = 0; k < 6; ++k) {
+                        double v = 0;
+                        if (c == VI[k]) v += gd[VJ[k]];
+                        if (k >= 3 && c == VJ[k]) v += gd[VI[k]];
+                        cr[6 + k] = v;
+                    }
+                }
+            } else {
+                if (isv) cr[0] = 1.0;
+                if (isb)
+                    for (int k = 0; k < 3; ++k) cr[1 + k] = g[d * 3 + k];
+            }
+            rows.push_back(d * nc + c);
+            coef.insert(coef.end(), cr.begin(), cr.end());
+        }
+    }
+    // normalise each constraint row
+    std::vector<double> nrm(m_rows, 0.0);
+    for (size_t i = 0; i < rows.size(); ++i)
+        for (int k = 0; k < m_rows; ++k) nrm[k] += coef[i * m_rows + k] * coef[i * m_rows + k];
+    for (int k = 0; k < m_rows; ++k) nrm[k] = nrm[k] > 0 ? 1.0 / std::sqrt(nrm[k]) : 0.0;
+    for (size_t i = 0; i < rows.size(); ++i)
+        for (int k = 0; k < m_rows; ++k) coef[i * m_rows + k] *= nrm[k];
+    std::vector<int32_t> of_row(f.n_rows, -1);
+    for (size_t i = 0; i < rows.size(); ++i) of_row[rows[i]] = (int32_t)i;
+    f.n_sup = (int64_t)rows.size();
+    RVE_TRY(upload(f.sup_row, rows.data(), rows.size(), s));
+    RVE_TRY(upload(f.sup_coef, coef.data(), coef.size(), s));
+    RVE_TRY(upload(f.sup_of_row, of_row.data(), of_row.size(), s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    return RVE_OK;
+}
+
+int build_field_data(rve_mesh m) {
+    cudaStream_t s = m->ctx->stream;
+    std::vector<double> geo(m->nt * 10);
+    RVE_CUDA(cudaMemcpyAsync(geo.data(), m->d_geo64.p, sizeof(double) * geo.size(),
+                             cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    m->volume = 0;
+    for (int64_t e = 0; e < m->nt; ++e) m->volume += geo[e * 10 + 9];
+    m->mech.nc = 3;
+    m->mech.nfield = 1;
+    m->scal.nc = 1;
+    m->scal.nfield = 2;
+    RVE_TRY(build_constraints(m, m->mech, geo));
+    RVE_TRY(build_constraints(m, m->scal, geo));
+    return RVE_OK;
+}
+
+// Jacobi diagonals per phase (needs materials and the DOF map).
+int build_diagonals(rve_mesh m) {
+    cudaStream_t s = m->ctx->stream;
+    for (FieldDev* f : {&m->mech, &m->scal}) {
+        const int64_t n = f->n_rows * 2 * f->nfield;
+        RVE_TRY(f->diag64.ensure(sizeof(double) * n));
+        RVE_TRY(f->diag32.ensure(sizeof(float) * n));
+        RVE_CUDA(cudaMemsetAsync(f->diag64.p, 0, sizeof(double) * n, s));
+        ElemView<double> ev;
+        ev.nt = m->nt;
+        ev.edofs = m->d_edofs.as<int32_t>();
+        ev.geo = m->d_geo64.as<double>();
+        ev.mat = (f->nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
+        ev.phase = m->d_phase.as<uint8_t>();
+        launch_diag<double>(m->p, f->nc, f->n_rows, ev, f->diag64.as<double>(), s);
+        launch_cast_d2f(n, f->diag64.as<double>(), f->diag32.as<float>(), s);
+        m->ctx->launches += 2;
+    }
+    RVE_CUDA(cudaGetLastError());
+    return RVE_OK;
+}
+
+// ------------------------------------------------------------- launch shape
+Launch make_launch(int ncols, int64_t work, cudaStream_t s) {
+    Launch L;
+    L.ncols = ncols;
+    const int B = ncols / 6;
+    int gcd = 1;
+    for (int d = 8; d >= 1; d >>= 1)
+        if (B % d == 0) {
+            gcd = d;
+            break;
+        }
+    L.cpb = 6 * gcd;
+    L.rows_per_block = 256 / L.cpb;
+    const int gx = ncols / L.cpb;
+    const int64_t want = (work + L.rows_per_block - 1) / L.rows_per_block;
+    const int64_t cap = std::max<int64_t>(1, (152 * 8) / gx);
+    L.nby = (int)std::max<int64_t>(1, std::min(want, cap));
+    L.stream = s;
+    return L;
+}
+
+// ----------------------------------------------------------- the solver
+struct SolveOut {
+    std::vector<double> tensor;    // [B][6][6] energy form (internal units)
+    std::vector<double> sig;       // [B][6][6] sigma form (diagnostic)
+    int iterations = 0;
+    int sweeps = 0;
+    bool converged = true;
+    double rel_res = 0;
+    bool numeric = false;
+};
+
+struct Solver {
+    rve_mesh m;
+    FieldDev& f;
+    int B, ncols;
+    int64_t n_rows;
+    Launch L;
+    cudaStream_t s;
+    ColState cs64{};
+    int64_t* launches;
+
+    Solver(rve_mesh mm, FieldDev& ff, int b)
+        : m(mm), f(ff), B(b), ncols(6 * b), n_rows(ff.n_rows), s(mm->ctx->stream),
+          launches(&mm->ctx->launches) {
+        L = make_launch(ncols, std::max<int64_t>(n_rows, mm->nt), s);
+    }
+
+    template <typename T>
+    ElemView<T> ev(const DevBuf& scale) const {
+        ElemView<T> e;
+        e.nt = m->nt;
+        e.edofs = m->d_edofs.as<int32_t>();
+        if constexpr (sizeof(T) == 8) {
+            e.geo = m->d_geo64.as<double>();
+            e.mat = (f.nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
+        } else {
+            e.geo = m->d_geo32.as<float>();
+            e.mat = (f.nc == 3 ? m->d_matm32 : m->d_mats32).as<float>();
+        }
+        e.phase = m->d_phase.as<uint8_t>();
+        e.scale = scale.as<T>();
+        return e;
+    }
+    template <typename T>
+    RowView<T> rv(const DevBuf& scale) const {
+        RowView<T> r;
+        r.n_rows = n_rows;
+        r.diag = (sizeof(T) == 8 ? f.diag64 : f.diag32).as<T>();
+        r.mask = m->bc == RVE_BC_DIRICHLET ? f.mask.as<uint8_t>() : nullptr;
+        r.scale = scale.as<T>();
+        r.nfield = f.nfield;
+        r.nc = f.nc;
+        r.m = f.m;
+        r.n_sup = f.n_sup;
+        r.sup_row = f.sup_row.as<int64_t>();
+        r.sup_coef = f.sup_coef.as<double>();
+        r.sup_of_row = f.sup_of_row.as<int32_t>();
+        return r;
+    }
+
+    int alloc(bool mixed) {
+        const size_t nv = (size_t)n_rows * ncols;
+        RVE_TRY(m->x64.ensure(nv * 8));
+        RVE_TRY(m->r64.ensure(nv * 8));
+        RVE_TRY(m->b64.ensure(nv * 8));
+        if (mixed) {
+            RVE_TRY(m->x32.ensure(nv * 4));
+            RVE_TRY(m->r32.ensure(nv * 4));
+            RVE_TRY(m->p32.ensure(nv * 4));
+            RVE_TRY(m->q32.ensure(nv * 4));
+        } else {
+            RVE_TRY(m->p64.ensure(nv * 8));
+            RVE_TRY(m->q64.ensure(nv * 8));
+        }
+        const size_t np = (size_t)L.nby * ncols;
+        RVE_TRY(m->epart.ensure(np * 8));
+        RVE_TRY(m->rzp.ensure(np * 8));
+        RVE_TRY(m->cpart.ensure(np * 12 * 8));
+        RVE_TRY(m->gpart.ensure(np * 12 * 8));
+        RVE_TRY(m->mpart.ensure(np * 12 * 8));
+        RVE_TRY(m->gsum.ensure((size_t)ncols * 12 * 8));
+        RVE_TRY(m->msum.ensure((size_t)ncols * 12 * 8));
+        // col state: rz, rz0, alpha, beta (4*ncols) + mu (12*ncols) + schur (144*ncols) doubles,
+        // then active, iters (ints) and flags
+        const size_t nd = (size_t)ncols * (4 + 12 + 144);
+        RVE_TRY(m->colstate.ensure(nd * 8 + (size_t)ncols * 8 + 64));
+        double* base = m->colstate.as<double>();
+        cs64.rz = base;
+        cs64.rz0 = base + ncols;
+        cs64.alpha = base + 2 * ncols;
+        cs64.beta = base + 3 * ncols;
+        cs64.mu = base + 4 * ncols;
+        cs64.schur = base + 16 * ncols;
+        int32_t* ib = reinterpret_cast<int32_t*>(base + nd);
+        cs64.active = ib;
+        cs64.iters = ib + ncols;
+        cs64.flags = ib + 2 * ncols;
+        RVE_CUDA(cudaMemsetAsync(cs64.flags, 0, sizeof(int32_t), s));
+        return RVE_OK;
+    }
+
+    // y = -(K x + macro)  (FP64): the fluctuation residual b - K x
+    int residual64(const double* x, double* y) {
+        RVE_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n_rows * ncols, s));
+        launch_operator<double>(m->p, f.nc, true, ev<double>(m->scale64), x, y, nullptr, L);
+        launch_neg(n_rows * ncols, y, s);
+        *launches += 2;
+        return RVE_OK;
+    }
+
+    template <typename T>
+    int pcg(T* x, T* r, T* p, T* q, const DevBuf& scale, double tol, int max_iter, int& iters_out,
+            bool& conv) {
+        const int check = std::max(1, m->ctx->opt.check_every);
+        ColState cs = cs64;
+        cs.tol = tol;
+        RowView<T> rvw = rv<T>(scale);
+        ElemView<T> evw = ev<T>(scale);
+        launch_schur<T>(rvw, cs, L);
+        launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), false, L);
+        launch_constraint_dot<T>(rvw, r, m->cpart.as<double>(), L);
+        launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, true, L);
+        launch_pupdate<T>(rvw, r, p, q, cs, true, L);
+        *launches += 6;
+        std::vector<int32_t> act(ncols);
+        int it = 0;
+        conv = false;
+        while (it < max_iter) {
+            for (int k = 0; k < check && it < max_iter; ++k, ++it) {
+                launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), L);
+                launch_finalize_alpha<T>(m->epart.as<double>(), cs, L);
+                launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, L);
+                launch_constraint_dot<T>(rvw, r, m->cpart.as<double>(), L);
+                launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, L);
+                launch_pupdate<T>(rvw, r, p, q, cs, false, L);
+                *launches += f.m > 0 ? 6 : 5;
+            }
+            RVE_CUDA(cudaGetLastError());
+            RVE_CUDA(cudaMemcpyAsync(act.data(), cs.active, sizeof(int32_t) * ncols,
+                                     cudaMemcpyDeviceToHost, s));
+            RVE_CUDA(cudaStreamSynchronize(s));
+            bool any = false;
+            for (int c = 0; c < ncols; ++c) any |= act[c] != 0;
+            if (!any) {
+                conv = true;
+                break;
+            }
+        }
+        std::vector<int32_t> its(ncols);
+        RVE_CUDA(cudaMemcpyAsync(its.data(), cs.iters, sizeof(int32_t) * ncols,
+                                 cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaStreamSynchronize(s));
+        iters_out = *std::max_element(its.begin(), its.end());
+        return RVE_OK;
+    }
+
+    // relative projected residual sqrt((r, P r) / (b, P b)) per column
+    int rel_residual(const double* r, const std::vector<double>& bnorm2, double& worst) {
+        ColState cs = cs64;
+        cs.tol = 0;
+        RowView<double> rvw = rv<double>(m->scale64);
+        launch_update<double>(rvw, nullptr, const_cast<double*>(r), nullptr, nullptr, cs,
+                              m->rzp.as<double>(), false, L);
+        launch_constraint_dot<double>(rvw, r, m->cpart.as<double>(), L);
+        launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, true, L);
+        *launches += 3;
+        std::vector<double> rz(ncols);
+        RVE_CUDA(cudaMemcpyAsync(rz.data(), cs.rz0, sizeof(double) * ncols, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaStreamSynchronize(s));
+        worst = 0;
+        for (int c = 0; c < ncols; ++c)
+            if (bnorm2[c] > 0) worst = std::max(worst, std::sqrt(std::max(rz[c], 0.0) / bnorm2[c]));
+        return RVE_OK;
+    }
+
+    int run(int precision, SolveOut& out) {
+        const rve_options& o = m->ctx->opt;
+        const bool mixed = precision == RVE_PREC_MIXED;
+        RVE_TRY(alloc(mixed));
+        const size_t nv = (size_t)n_rows * ncols;
+        double* x64 = m->x64.as<double>();
+        double* r64 = m->r64.as<double>();
+        double* b64 = m->b64.as<double>();
+        RVE_CUDA(cudaMemsetAsync(x64, 0, nv * 8, s));
+        RVE_TRY(residual64(x64, b64));   // b = -(K 0 + macro)
+        RVE_CUDA(cudaMemcpyAsync(r64, b64, nv * 8, cudaMemcpyDeviceToDevice, s));
+        // reference norms (b, P b)
+        std::vector<double> bn(ncols, 1.0);
+        {
+            double dummy;
+            std::vector<double> ones(ncols, 1.0);
+            RVE_TRY(rel_residual(b64, ones, dummy));
+            RVE_CUDA(cudaMemcpyAsync(bn.data(), cs64.rz0, sizeof(double) * ncols, cudaMemcpyDeviceToHost, s));
+            RVE_CUDA(cudaStreamSynchronize(s));
+        }
+        out.iterations = 0;
+        out.sweeps = 0;
+        out.converged = false;
+        if (!mixed) {
+            int its = 0;
+            bool conv = false;
+            RVE_TRY(pcg<double>(x64, r64, m->p64.as<double>(), m->q64.as<double>(), m->scale64,
+                                o.rtol, o.max_iter, its, conv));
+            out.iterations = its;
+            RVE_TRY(residual64(x64, r64));
+            RVE_TRY(rel_residual(r64, bn, out.rel_res));
+            out.converged = conv || out.rel_res <= o.rtol * 10;
+        } else {
+            float* x32 = m->x32.as<float>();
+            float* r32 = m->r32.as<float>();
+            int total = 0;
+            for (int sw = 0; sw < std::max(1, o.max_refine); ++sw) {
+                launch_cast_d2f((int64_t)nv, r64, r32, s);
+                RVE_CUDA(cudaMemsetAsync(x32, 0, nv * 4, s));
+                *launches += 1;
+                int its = 0;
+                bool conv = false;
+                RVE_TRY(pcg<float>(x32, r32, m->p32.as<float>(), m->q32.as<float>(), m->scale32,
+                                   o.inner_rtol, o.max_iter, its, conv));
+                total += its;
+                launch_axpy_f2d((int64_t)nv, x32, x64, s);
+                *launches += 1;
+                RVE_TRY(residual64(x64, r64));
+                RVE_TRY(rel_residual(r64, bn, out.rel_res));
+                out.sweeps = sw + 1;
+                if (out.rel_res <= o.rtol) {
+                    out.converged = true;
+                    break;
+                }
+            }
+            out.iterations = total;
+        }
+        // reductions for the tensors
+        launch_gram(n_rows, b64, x64, r64, m->gpart.as<double>(), L);
+        launch_reduce_partials(L.nby, ncols * 12, m->gpart.as<double>(), m->gsum.as<double>(), s);
+        launch_mean_stress<double>(m->p, f.nc, ev<double>(m->scale64), x64, m->mpart.as<double>(), L);
+        launch_reduce_partials(L.nby, ncols * 12, m->mpart.as<double>(), m->msum.as<double>(), s);
+        *launches += 4;
+        std::vector<double> Gs(ncols * 12), Ms(ncols * 12);
+        int32_t flags = 0;
+        RVE_CUDA(cudaMemcpyAsync(Gs.data(), m->gsum.p, Gs.size() * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaMemcpyAsync(Ms.data(), m->msum.p, Ms.size() * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaMemcpyAsync(&flags, cs64.flags, 4, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaStreamSynchronize(s));
+        out.numeric = flags != 0;
+        const double V = m->volume;
+        out.tensor.assign((size_t)B * 36, 0.0);
+        out.sig.assign((size_t)B * 36, 0.0);
+        for (int b = 0; b < B; ++b)
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                    const int ci = 6 * b + i, cj = 6 * b + j;
+                    // V C_ij = V <D>_ij - b_i . u_j - u_i . r_j
+                    const double e = Ms[cj * 12 + 6 + i] - Gs[ci * 12 + j] - Gs[ci * 12 + 6 + j];
+                    out.tensor[b * 36 + i * 6 + j] = e / V;
+                    out.sig[b * 36 + i * 6 + j] = Ms[cj * 12 + (f.nc == 3 ? i : i % 3)] / V;
+                }
+        return RVE_OK;
+    }
+};
+
+double rel_fro(const double* a, const double* b, int n) {
+    double num = 0, den = 0;
+    for (int i = 0; i < n; ++i) {
+        num += (a[i] - b[i]) * (a[i] - b[i]);
+        den += b[i] * b[i];
+    }
+    return den > 0 ? std::sqrt(num / den) : std::sqrt(num);
+}
+
+// Solve B RVEs of one mesh whose degradation factors are in d_w (device).
+int homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D,
+                     rve_stats* st) {
+    cudaStream_t s = m->ctx->stream;
+    const int ncols = 6 * B;
+    RVE_TRY(m->scale64.ensure((size_t)ncols * 2 * 8));
+    RVE_TRY(m->scale32.ensure((size_t)ncols * 2 * 4));
+    const int prec = m->ctx->opt.precision;
+    // mechanics
+    launch_column_scales<double>(B, d_w, m->deg.apply_to_yarn, true, m->scale64.as<double>(), s);
+    launch_column_scales<float>(B, d_w, m->deg.apply_to_yarn, true, m->scale32.as<float>(), s);
+    m->ctx->launches += 2;
+    SolveOut om, osc;
+    {
+        Solver sv(m, m->mech, B);
+        RVE_TRY(sv.run(prec, om));
+    }
+    launch_column_scales<double>(B, d_w, 0, false, m->scale64.as<double>(), s);
+    launch_column_scales<float>(B, d_w, 0, false, m->scale32.as<float>(), s);
+    m->ctx->launches += 2;
+    {
+        Solver sv(m, m->scal, B);
+        RVE_TRY(sv.run(prec, osc));
+    }
+    double hm_m = 0, hm_s = 0;
+    for (int b = 0; b < B; ++b) {
+        double c[36], cs[36];
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                const double* T = &om.tensor[b * 36];
+                c[i * 6 + j] = 0.5 * (T[i * 6 + j] + T[j * 6 + i]) * m->mc.ref_mech;
+                cs[i * 6 + j] = om.sig[b * 36 + i * 6 + j] * m->mc.ref_mech;
+            }
+        hm_m = std::max(hm_m, rel_fro(cs, c, 36));
+        if (C) std::memcpy(C + 36 * b, c, sizeof(c));
+        double k[9], d[9], ks[9];
+        const double* T = &osc.tensor[b * 36];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                k[i * 3 + j] = 0.5 * (T[i * 6 + j] + T[j * 6 + i]) * m->mc.ref_k;
+                d[i * 3 + j] = 0.5 * (T[(3 + i) * 6 + 3 + j] + T[(3 + j) * 6 + 3 + i]) * m->mc.ref_d;
+                ks[i * 3 + j] = osc.sig[b * 36 + i * 6 + j] * m->mc.ref_k;
+            }
+        hm_s = std::max(hm_s, rel_fro(ks, k, 9));
+        if (K) std::memcpy(K + 9 * b, k, sizeof(k));
+        if (D) std::memcpy(D + 9 * b, d, sizeof(d));
+    }
+    if (st) {
+        st->iterations_mech = std::max(st->iterations_mech, om.iterations);
+        st->iterations_scalar = std::max(st->iterations_scalar, osc.iterations);
+        st->refine_sweeps = std::max(st->refine_sweeps, std::max(om.sweeps, osc.sweeps));
+        st->converged = st->converged && om.converged && osc.converged;
+        st->rel_residual_mech = std::max(st->rel_residual_mech, om.rel_res);
+        st->rel_residual_scalar = std::max(st->rel_residual_scalar, osc.rel_res);
+        st->hill_mandel_mech = std::max(st->hill_mandel_mech, hm_m);
+        st->hill_mandel_scalar = std::max(st->hill_mandel_scalar, hm_s);
+    }
+    if (om.numeric || osc.numeric) {
+        set_error("non-finite or non-positive value in a PCG reduction");
+        return RVE_ERR_NUMERIC;
+    }
+    if (!(om.converged && osc.converged)) {
+        set_error("PCG did not reach rtol within max_iter");
+        return RVE_ERR_NOT_CONVERGED;
+    }
+    return RVE_OK;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* rve_strerror(int code) {
+    switch (code) {
+        case RVE_OK: return "ok";
+        case RVE_ERR_INVALID_ARGUMENT: return "invalid argument";
+        case RVE_ERR_BAD_MESH: return "bad mesh";
+        case RVE_ERR_NOT_SPD: return "material not positive definite";
+        case RVE_ERR_NOT_CONVERGED: return "not converged";
+        case RVE_ERR_NUMERIC: return "numeric error (NaN/Inf)";
+        case RVE_ERR_CUDA: return "CUDA error";
+        case RVE_ERR_NO_DEVICE: return "no suitable CUDA device";
+        case RVE_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case RVE_ERR_STATE: return "call order violated";
+        case RVE_ERR_TIMEOUT: return "bounded device wait timed out";
+        default: return "unknown error";
+    }
+}
+
+const char* rve_last_error(void) { return g_last_error.c_str(); }
+
+void rve_default_options(rve_options* o) {
+    if (!o) return;
+    o->device = 0;
+    o->precision = RVE_PREC_FP64;
+    o->rtol = 1e-10;
+    o->max_iter = 20000;
+    o->inner_rtol = 1e-6;
+    o->max_refine = 4;
+    o->check_every = 16;
+    o->batch = 0;
+    o->stream = nullptr;
+}
+
+int rve_create(rve_ctx* out, const rve_options* opts) {
+    if (!out) {
+        set_error("null output handle");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    *out = nullptr;
+    rve_options o;
+    rve_default_options(&o);
+    if (opts) o = *opts;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        set_error("no CUDA device visible");
+        return RVE_ERR_NO_DEVICE;
+    }
+    if (o.device < 0 || o.device >= n) {
+        set_error("device ordinal out of range");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    cudaDeviceProp prop;
+    RVE_CUDA(cudaGetDeviceProperties(&prop, o.device));
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        set_error("librve is built for sm_103a (GB300); found compute capability " +
+                  std::to_string(prop.major) + "." + std::to_string(prop.minor));
+        return RVE_ERR_NO_DEVICE;
+    }
+    RVE_CUDA(cudaSetDevice(o.device));
+    auto* c = new rve_ctx_s();
+    c->opt = o;
+    c->device = o.device;
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            set_error("cudaStreamCreate failed");
+            return RVE_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    upload_basis_tables();
+    if (cudaGetLastError() != cudaSuccess) {
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        set_error("uploading basis tables failed");
+        return RVE_ERR_CUDA;
+    }
+    *out = c;
+    return RVE_OK;
+}
+
+int rve_destroy(rve_ctx c) {
+    if (!c) return RVE_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return RVE_OK;
+}
+
+int rve_set_options(rve_ctx c, const rve_options* o) {
+    RVE_TRY(check_ctx(c));
+    if (!o || !(o->rtol > 0) || o->max_iter <= 0 || (o->precision != RVE_PREC_FP64 && o->precision != RVE_PREC_MIXED)) {
+        set_error("invalid options");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    const void* keep_stream = c->opt.stream;
+    const int keep_dev = c->opt.device;
+    c->opt = *o;
+    c->opt.stream = const_cast<void*>(keep_stream);
+    c->opt.device = keep_dev;
+    return RVE_OK;
+}
+
+int rve_get_options(rve_ctx c, rve_options* o) {
+    RVE_TRY(check_ctx(c));
+    if (!o) return RVE_ERR_INVALID_ARGUMENT;
+    *o = c->opt;
+    o->stream = c->stream;
+    return RVE_OK;
+}
+
+int rve_mesh_load(rve_ctx c, const double* xyz, int64_t nv, const int32_t* tets, int64_t nt,
+                  const uint8_t* phase, const double* fibre_dir, int p, rve_mesh* out) {
+    RVE_TRY(check_ctx(c));
+    if (!out || !xyz || !tets || nv < 4 || nt < 1 || p < 1 || p > 3 || nt > (int64_t)INT32_MAX / 20) {
+        set_error("rve_mesh_load: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    *out = nullptr;
+    auto m = std::make_unique<rve_mesh_s>();
+    m->ctx = c;
+    m->p = p;
+    m->bc = RVE_BC_DIRICHLET;
+    m->nv = nv;
+    m->nt = nt;
+    m->xyz.assign(xyz, xyz + 3 * nv);
+    m->tets.assign(tets, tets + 4 * nt);
+    m->phase.assign(nt, 0);
+    if (phase)
+        for (int64_t e = 0; e < nt; ++e) {
+            if (phase[e] > 1) {
+                set_error("phase must be 0 (matrix) or 1 (yarn)");
+                return RVE_ERR_INVALID_ARGUMENT;
+            }
+            m->phase[e] = phase[e];
+        }
+    m->tangent.assign(3 * nt, 0.0);
+    for (int64_t e = 0; e < nt; ++e) m->tangent[3 * e] = 1.0;
+    if (fibre_dir) m->tangent.assign(fibre_dir, fibre_dir + 3 * nt);
+    cudaStream_t s = c->stream;
+    RVE_TRY(upload(m->d_xyz, m->xyz.data(), m->xyz.size(), s));
+    RVE_TRY(upload(m->d_phase, m->phase.data(), m->phase.size(), s));
+    RVE_TRY(upload(m->d_tangent, m->tangent.data(), m->tangent.size(), s));
+    RVE_TRY(rebuild_map(m.get()));
+    RVE_TRY(build_field_data(m.get()));
+    *out = m.release();
+    return RVE_OK;
+}
+
+int rve_mesh_free(rve_ctx c, rve_mesh m) {
+    if (!m) return RVE_OK;
+    if (c) cudaSetDevice(c->device);
+    if (m->ctx) cudaStreamSynchronize(m->ctx->stream);
+    delete m;
+    return RVE_OK;
+}
+
+int rve_mesh_info(rve_ctx c, rve_mesh m, rve_mesh_stats* o) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !o) return RVE_ERR_INVALID_ARGUMENT;
+    o->n_vertices = m->map.V;
+    o->n_edges = m->map.E;
+    o->n_faces = m->map.F;
+    o->n_tets = m->nt;
+    o->n_scalar_dofs = m->map.N;
+    int64_t nb = 0;
+    if (m->bc == RVE_BC_DIRICHLET)
+        for (auto b : m->map.boundary) nb += b;
+    o->n_constrained = nb;
+    o->p = m->p;
+    o->bc = m->bc;
+    o->volume = m->volume;
+    return RVE_OK;
+}
+
+int rve_set_materials(rve_ctx c, rve_mesh m, const rve_matrix_props* mp, const rve_yarn_props* yp,
+                      double T_C, double c_wt, double t_h, const rve_degradation* deg) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !mp || !yp) {
+        set_error("rve_set_materials: null argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    rve_degradation dg{-0.001682, 126.0, 1.5, 0};
+    if (deg) dg = *deg;
+    if (!std::isfinite(T_C) || !std::isfinite(c_wt) || !std::isfinite(t_h) || t_h < 0 ||
+        !(T_C < dg.Tg_C) || T_C <= -273.15 || !finite_pos(dg.c_sat_wt) || !std::isfinite(dg.beta)) {
+        set_error("degradation state out of range (need -273.15 < T < Tg, t >= 0)");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    // positive definiteness of the constituents
+    bool ok = finite_pos(mp->E) && mp->nu > -1 && mp->nu < 0.5 && finite_pos(mp->k) && finite_pos(mp->d);
+    ok = ok && finite_pos(yp->E1) && finite_pos(yp->E2) && finite_pos(yp->G12) && yp->nu23 > -1 &&
+         yp->nu23 < 1 && finite_pos(yp->k1) && finite_pos(yp->k2) && finite_pos(yp->d1) &&
+         finite_pos(yp->d2);
+    // TI normal block: 1 - nu23 - 2 nu12^2 E2/E1 > 0 (with 1 + nu23 > 0)
+    ok = ok && (1 - yp->nu23 - 2 * yp->nu12 * yp->nu12 * yp->E2 / yp->E1) > 0;
+    if (!ok) {
+        set_error("constituent properties are not positive definite");
+        return RVE_ERR_NOT_SPD;
+    }
+    cudaStream_t s = c->stream;
+    MaterialConsts mc;
+    mc.Em = mp->E; mc.num = mp->nu; mc.km = mp->k; mc.dm = mp->d;
+    mc.E1 = yp->E1; mc.E2 = yp->E2; mc.G12 = yp->G12; mc.nu12 = yp->nu12; mc.nu23 = yp->nu23;
+    mc.k1 = yp->k1; mc.k2 = yp->k2; mc.d1 = yp->d1; mc.d2 = yp->d2;
+    mc.ref_mech = mp->E;
+    mc.ref_k = mp->k;
+    mc.ref_d = mp->d;
+    const int64_t nt = m->nt;
+    RVE_TRY(m->d_matm64.ensure(nt * 21 * 8));
+    RVE_TRY(m->d_matm32.ensure(nt * 21 * 4));
+    RVE_TRY(m->d_mats64.ensure(nt * 12 * 8));
+    RVE_TRY(m->d_mats32.ensure(nt * 12 * 4));
+    RVE_CUDA(cudaMemsetAsync(m->d_flag.p, 0, sizeof(int32_t), s));
+    launch_materials(nt, m->d_phase.as<uint8_t>(), m->d_tangent.as<double>(), mc,
+                     m->d_matm64.as<double>(), m->d_matm32.as<float>(), m->d_mats64.as<double>(),
+                     m->d_mats32.as<float>(), m->d_flag.as<int32_t>(), s);
+    c->launches++;
+    int32_t bad = 0;
+    RVE_CUDA(cudaMemcpyAsync(&bad, m->d_flag.p, 4, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    if (bad) {
+        set_error("yarn tangent is zero or TI tensor not invertible");
+        return RVE_ERR_NOT_SPD;
+    }
+    m->mc = mc;
+    m->deg = dg;
+    m->T_C = T_C;
+    m->c_wt = c_wt;
+    m->t_h = t_h;
+    m->have_materials = true;
+    RVE_TRY(build_diagonals(m));
+    return RVE_OK;
+}
+
+int rve_set_bc(rve_ctx c, rve_mesh m, int bc) {
+    RVE_TRY(check_ctx(c));
+    if (!m || (bc != RVE_BC_DIRICHLET && bc != RVE_BC_PERIODIC && bc != RVE_BC_NEUMANN)) {
+        set_error("rve_set_bc: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    const bool fold_changes = (bc == RVE_BC_PERIODIC) != (m->bc == RVE_BC_PERIODIC);
+    const int old = m->bc;
+    m->bc = bc;
+    if (fold_changes) {
+        int rc = rebuild_map(m);
+        if (rc != RVE_OK) {
+            m->bc = old;
+            std::string keep = g_last_error;
+            rebuild_map(m);
+            build_field_data(m);
+            if (m->have_materials) build_diagonals(m);
+            set_error(keep);
+            return rc;
+        }
+    }
+    RVE_TRY(build_field_data(m));
+    if (m->have_materials) RVE_TRY(build_diagonals(m));
+    return RVE_OK;
+}
+
+int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (!m) return RVE_ERR_INVALID_ARGUMENT;
+    if (!m->have_materials) {
+        set_error("rve_set_materials must be called before rve_homogenise");
+        return RVE_ERR_STATE;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t l0 = c->launches;
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->converged = 1;
+    }
+    cudaStream_t s = c->stream;
+    double Th[1] = {m->T_C}, ch[1] = {m->c_wt}, th[1] = {m->t_h};
+    DevBuf tmp;
+    RVE_TRY(tmp.ensure(4 * 8));
+    double* d = tmp.as<double>();
+    RVE_CUDA(cudaMemcpyAsync(d, Th, 8, cudaMemcpyHostToDevice, s));
+    RVE_CUDA(cudaMemcpyAsync(d + 1, ch, 8, cudaMemcpyHostToDevice, s));
+    RVE_CUDA(cudaMemcpyAsync(d + 2, th, 8, cudaMemcpyHostToDevice, s));
+    launch_degradation(1, d, d + 1, d + 2, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, d + 3, s);
+    c->launches++;
+    int rc = homogenise_batch(m, 1, d + 3, C, K, D, st);
+    RVE_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        st->kernel_launches = c->launches - l0;
+    }
+    return rc;
+}
+
+static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, int64_t G,
+                             const double* T_dev, const double* c_dev, const double* t_dev,
+                             const int32_t* mesh_id, double* C_dev, double* K_dev, double* D_dev,
+                             int32_t* status_dev, rve_stats* st) {
+    cudaStream_t s = c->stream;
+    // group points by mesh
+    std::vector<std::vector<int64_t>> groups(n_meshes);
+    for (int64_t g = 0; g < G; ++g) {
+        if (mesh_id[g] < 0 || mesh_id[g] >= n_meshes) {
+            set_error("mesh_id out of range");
+            return RVE_ERR_INVALID_ARGUMENT;
+        }
+        groups[mesh_id[g]].push_back(g);
+    }
+    int rc_all = RVE_OK;
+    DevBuf d_idx, d_tmp;
+    std::vector<double> hC, hK, hD;
+    for (int mi = 0; mi < n_meshes; ++mi) {
+        auto& grp = groups[mi];
+        if (grp.empty()) continue;
+        rve_mesh m = meshes[mi];
+        if (!m || !m->have_materials) {
+            set_error("mesh without materials in macro_update_gauss_points");
+            return RVE_ERR_STATE;
+        }
+        int Bmax = c->opt.batch > 0 ? c->opt.batch : 16;
+        for (size_t off = 0; off < grp.size(); off += Bmax) {
+            const int B = (int)std::min<size_t>(Bmax, grp.size() - off);
+            // gather states of this batch on the device
+            RVE_TRY(d_tmp.ensure((size_t)B * 4 * 8));
+            double* dT = d_tmp.as<double>();
+            double* dc = dT + B;
+            double* dt = dT + 2 * B;
+            double* dw = dT + 3 * B;
+            for (int b = 0; b < B; ++b) {
+                const int64_t g = grp[off + b];
+                RVE_CUDA(cudaMemcpyAsync(dT + b, T_dev + g, 8, cudaMemcpyDeviceToDevice, s));
+                RVE_CUDA(cudaMemcpyAsync(dc + b, c_dev + g, 8, cudaMemcpyDeviceToDevice, s));
+                RVE_CUDA(cudaMemcpyAsync(dt + b, t_dev + g, 8, cudaMemcpyDeviceToDevice, s));
+            }
+            launch_degradation(B, dT, dc, dt, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, dw, s);
+            c->launches++;
+            hC.assign((size_t)B * 36, 0);
+            hK.assign((size_t)B * 9, 0);
+            hD.assign((size_t)B * 9, 0);
+            int rc = homogenise_batch(m, B, dw, hC.data(), hK.data(), hD.data(), st);
+            if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return rc;
+            if (rc != RVE_OK) rc_all = rc;
+            for (int b = 0; b < B; ++b) {
+                const int64_t g = grp[off + b];
+                RVE_CUDA(cudaMemcpyAsync(C_dev + 36 * g, &hC[36 * b], 36 * 8, cudaMemcpyHostToDevice, s));
+                RVE_CUDA(cudaMemcpyAsync(K_dev + 9 * g, &hK[9 * b], 9 * 8, cudaMemcpyHostToDevice, s));
+                RVE_CUDA(cudaMemcpyAsync(D_dev + 9 * g, &hD[9 * b], 9 * 8, cudaMemcpyHostToDevice, s));
+                int32_t sv = rc;
+                RVE_CUDA(cudaMemcpyAsync(status_dev + g, &sv, 4, cudaMemcpyHostToDevice, s));
+                RVE_CUDA(cudaStreamSynchronize(s));
+            }
+        }
+    }
+    return rc_all;
+}
+
+int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshes, int64_t G,
+                                  const double* T_dev, const double* c_dev, const double* t_dev,
+                                  const int32_t* mesh_id_host, double* C_dev, double* K_dev,
+                                  double* D_dev, int32_t* status_dev, int mode, rve_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (!meshes || n_meshes <= 0 || G < 0 || (G > 0 && (!T_dev || !c_dev || !t_dev || !mesh_id_host || !C_dev ||
+        !K_dev || !D_dev || !status_dev)) || mode != RVE_MODE_PCG) {
+        set_error("macro_update_gauss_points_dev: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t l0 = c->launches;
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->converged = 1;
+    }
+    int rc = macro_update_impl(c, meshes, n_meshes, G, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev,
+                               D_dev, status_dev, st);
+    if (st) {
+        cudaStreamSynchronize(c->stream);
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        st->kernel_launches = c->launches - l0;
+    }
+    return rc;
+}
+
+int macro_update_gauss_points(rve_ctx c, const rve_mesh* meshes, int n_meshes, int64_t G,
+                              const double* T_C, const double* c_wt, const double* t_h,
+                              const int32_t* mesh_id, double* C, double* K, double* D,
+                              int32_t* status, int mode, rve_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (G < 0 || (G > 0 && (!T_C || !c_wt || !t_h || !mesh_id || !C || !K || !D || !status))) {
+        set_error("macro_update_gauss_points: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (G == 0) return RVE_OK;
+    cudaStream_t s = c->stream;
+    DevBuf in, outb;
+    RVE_TRY(in.ensure((size_t)G * 3 * 8));
+    RVE_TRY(outb.ensure((size_t)G * (36 + 9 + 9) * 8 + (size_t)G * 4));
+    double* dT = in.as<double>();
+    RVE_CUDA(cudaMemcpyAsync(dT, T_C, G * 8, cudaMemcpyHostToDevice, s));
+    RVE_CUDA(cudaMemcpyAsync(dT + G, c_wt, G * 8, cudaMemcpyHostToDevice, s));
+    RVE_CUDA(cudaMemcpyAsync(dT + 2 * G, t_h, G * 8, cudaMemcpyHostToDevice, s));
+    double* dC = outb.as<double>();
+    double* dK = dC + 36 * G;
+    double* dD = dK + 9 * G;
+    int32_t* dS = reinterpret_cast<int32_t*>(dD + 9 * G);
+    int rc = macro_update_gauss_points_dev(c, meshes, n_meshes, G, dT, dT + G, dT + 2 * G, mesh_id,
+                                           dC, dK, dD, dS, mode, st);
+    if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return rc;
+    RVE_CUDA(cudaMemcpyAsync(C, dC, G * 36 * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(K, dK, G * 9 * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(D, dD, G * 9 * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(status, dS, G * 4, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
+int rve_degradation_factor(rve_ctx c, int64_t n, const double* T_C, const double* c_wt,
+                           const double* t_h, const rve_degradation* deg, double* out) {
+    RVE_TRY(check_ctx(c));
+    if (n < 0 || (n > 0 && (!T_C || !c_wt || !t_h || !out))) return RVE_ERR_INVALID_ARGUMENT;
+    if (n == 0) return RVE_OK;
+    rve_degradation dg{-0.001682, 126.0, 1.5, 0};
+    if (deg) dg = *deg;
+    cudaStream_t s = c->stream;
+    DevBuf b;
+    RVE_TRY(b.ensure((size_t)n * 4 * 8));
+    double* d = b.as<double>();
+    RVE_CUDA(cudaMemcpyAsync(d, T_C, n * 8, cudaMemcpyHostToDevice, s));
+    RVE_CUDA(cudaMemcpyAsync(d + n, c_wt, n * 8, cudaMemcpyHostToDevice, s));
+    RVE_CUDA(cudaMemcpyAsync(d + 2 * n, t_h, n * 8, cudaMemcpyHostToDevice, s));
+    launch_degradation(n, d, d + n, d + 2 * n, dg.beta, dg.Tg_C, dg.c_sat_wt, d + 3 * n, s);
+    c->launches++;
+    RVE_CUDA(cudaGetLastError());
+    RVE_CUDA(cudaMemcpyAsync(out, d + 3 * n, n * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    return RVE_OK;
+}
+
+int rve_mesh_get_tensors(rve_ctx c, rve_mesh m, double* stiff, double* cond, double* diff) {
+    RVE_TRY(check_ctx(c));
+    if (!m) return RVE_ERR_INVALID_ARGUMENT;
+    if (!m->have_materials) return RVE_ERR_STATE;
+    cudaStream_t s = c->stream;
+    const int64_t nt = m->nt;
+    std::vector<double> a(nt * 21), b(nt * 12);
+    RVE_CUDA(cudaMemcpyAsync(a.data(), m->d_matm64.p, a.size() * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(b.data(), m->d_mats64.p, b.size() * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    auto u6 = [](int i, int j) {
+        if (i > j) std::swap(i, j);
+        return i * 6 - i * (i - 1) / 2 + (j - i);
+    };
+    auto sym3 = [](int i, int j) { return i == j ? i : ((i + j == 1) ? 3 : ((i + j == 3) ? 4 : 5)); };
+    for (int64_t e = 0; e < nt; ++e) {
+        if (stiff)
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) stiff[e * 36 + i * 6 + j] = a[e * 21 + u6(i, j)] * m->mc.ref_mech;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                if (cond) cond[e * 9 + i * 3 + j] = b[e * 12 + sym3(i, j)] * m->mc.ref_k;
+                if (diff) diff[e * 9 + i * 3 + j] = b[e * 12 + 6 + sym3(i, j)] * m->mc.ref_d;
+            }
+    }
+    return RVE_OK;
+}
+
+int rve_apply_operator(rve_ctx c, rve_mesh m, int field, int ncols, const double* x, double* y) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !x || !y || field < 0 || field > 2 || ncols <= 0) return RVE_ERR_INVALID_ARGUMENT;
+    if (!m->have_materials) return RVE_ERR_STATE;
+    cudaStream_t s = c->stream;
+    FieldDev& f = field == 0 ? m->mech : m->scal;
+    // pad columns to a multiple of 6; select the scalar field through the column index
+    const int cpad = 6 * ((ncols + 5) / 6);
+    const int64_t n_rows = f.n_rows;
+    std::vector<double> xp((size_t)n_rows * cpad, 0.0), yp((size_t)n_rows * cpad, 0.0);
+    // scalar: thermal uses columns 0..2 of each group, moisture 3..5
+    std::vector<int> colmap(ncols);
+    for (int j = 0; j < ncols; ++j) colmap[j] = j;
+    int cpad2 = cpad;
+    if (field != 0) {
+        cpad2 = 6 * ncols;   // one group per column, place it at 0 (thermal) or 3 (moisture)
+        xp.assign((size_t)n_rows * cpad2, 0.0);
+        yp.assign((size_t)n_rows * cpad2, 0.0);
+        for (int j = 0; j < ncols; ++j) colmap[j] = 6 * j + (field == 2 ? 3 : 0);
+    }
+    for (int64_t r = 0; r < n_rows; ++r)
+        for (int j = 0; j < ncols; ++j) xp[r * cpad2 + colmap[j]] = x[r * ncols + j];
+    DevBuf dx, dy, sc;
+    RVE_TRY(upload(dx, xp.data(), xp.size(), s));
+    RVE_TRY(dy.ensure(yp.size() * 8));
+    RVE_CUDA(cudaMemsetAsync(dy.p, 0, yp.size() * 8, s));
+    std::vector<double> ones((size_t)cpad2 * 2, 1.0);
+    RVE_TRY(upload(sc, ones.data(), ones.size(), s));
+    ElemView<double> ev;
+    ev.nt = m->nt;
+    ev.edofs = m->d_edofs.as<int32_t>();
+    ev.geo = m->d_geo64.as<double>();
+    ev.mat = (f.nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
+    ev.phase = m->d_phase.as<uint8_t>();
+    ev.scale = sc.as<double>();
+    Launch L = make_launch(cpad2, m->nt, s);
+    launch_operator<double>(m->p, f.nc, false, ev, dx.as<double>(), dy.as<double>(), nullptr, L);
+    c->launches++;
+    RVE_CUDA(cudaGetLastError());
+    RVE_CUDA(cudaMemcpyAsync(yp.data(), dy.p, yp.size() * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    const double ref = field == 0 ? m->mc.ref_mech : (field == 1 ? m->mc.ref_k : m->mc.ref_d);
+    for (int64_t r = 0; r < n_rows; ++r)
+        for (int j = 0; j < ncols; ++j) y[r * ncols + j] = yp[r * cpad2 + colmap[j]] * ref;
+    return RVE_OK;
+}
+
+int rve_mesh_get_dofmap(rve_ctx c, rve_mesh m, int32_t* edofs, int32_t* lverts) {
+    RVE_TRY(check_ctx(c));
+    if (!m) return RVE_ERR_INVALID_ARGUMENT;
+    if (edofs) std::memcpy(edofs, m->map.edofs.data(), m->map.edofs.size() * 4);
+    if (lverts) std::memcpy(lverts, m->map.lverts.data(), m->map.lverts.size() * 4);
+    return RVE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,937 @@
+// Device kernels of librve (sm_103a).
+//
+// Vector layout (all vector kernels): v[row * ncols + col], row = dof * NC + comp.
+// 2-D launches: grid = (ncols / cpb, nby), block = cpb * rows_per_block threads;
+// thread (cl, r) owns column blockIdx.x * cpb + cl and strides over rows
+// (or elements) starting at blockIdx.y * rows_per_block + r.  Every reduction
+// writes one FP64 partial per (blockIdx.y, column), summed by a finalize kernel.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "kernels.h"
+#include "rve_internal.h"
+
+namespace rve {
+
+// ------------------------------------------------------------ basis tables
+// A[k][m][j] of the hierarchic basis (see rve_internal.h), per order p.
+__constant__ double cA64[3][3 * 10 * 20];
+__constant__ float cA32[3][3 * 10 * 20];
+
+void upload_basis_tables() {
+    static double h64[3][3 * 10 * 20];
+    static float h32[3][3 * 10 * 20];
+    for (int p = 1; p <= 3; ++p) {
+        const Basis& B = basis(p);
+        for (size_t i = 0; i < B.A.size(); ++i) {
+            h64[p - 1][i] = B.A[i];
+            h32[p - 1][i] = (float)B.A[i];
+        }
+    }
+    cudaMemcpyToSymbol(cA64, h64, sizeof(h64));
+    cudaMemcpyToSymbol(cA32, h32, sizeof(h32));
+}
+
+template <typename T>
+struct Tab;
+template <>
+struct Tab<double> {
+    __device__ __forceinline__ static double a(int p, int i) { return cA64[p - 1][i]; }
+};
+template <>
+struct Tab<float> {
+    __device__ __forceinline__ static float a(int p, int i) { return cA32[p - 1][i]; }
+};
+
+template <int P>
+struct Order {
+    static constexpr int NE = P == 1 ? 4 : (P == 2 ? 10 : 20);
+    static constexpr int NM = P == 1 ? 1 : (P == 2 ? 4 : 10);
+};
+
+// Upper-triangular index of a symmetric 6x6 stored row by row.
+__host__ __device__ constexpr int ut6(int i, int j) {
+    return i <= j ? (i * 6 - i * (i - 1) / 2 + (j - i)) : (j * 6 - j * (j - 1) / 2 + (i - j));
+}
+// Symmetric 3x3 stored as (xx, yy, zz, xy, yz, zx).
+__host__ __device__ constexpr int s3(int i, int j) {
+    return i == j ? i : ((i + j == 1) ? 3 : ((i + j == 3) ? 4 : 5));
+}
+
+// ---------------------------------------------------- block column reduction
+// Reduce `nacc` per-thread values over the rows of the block for each column
+// and store them to out[(blockIdx.y * ncols + col) * nacc + a].
+template <int NACC>
+__device__ __forceinline__ void block_column_reduce(const double (&acc)[NACC], double* out,
+                                                    int ncols, int cpb, int col) {
+    __shared__ double buf[256];
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, r = threadIdx.x / cpb;
+#pragma unroll 1
+    for (int a = 0; a < NACC; ++a) {
+        buf[threadIdx.x] = acc[a];
+        __syncthreads();
+        if (r == 0) {
+            double s = 0.0;
+            for (int q = 0; q < rows; ++q) s += buf[q * cpb + cl];
+            out[((int64_t)blockIdx.y * ncols + col) * NACC + a] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------- the operator
+// y += sum_e A_e^T K_e A_e x  for every column, matrix-free (Eq. RVE_Eq_var_final):
+// per element, the reference gradient of the field is expanded on the
+// orthonormal modes of P_{p-1}; each mode is mapped to the physical gradient
+// by J^{-1}, turned into a stress (s * D : eps) or flux (s * k grad), mapped
+// back and contracted with the same table, then scatter-added.  With MACRO
+// the unit macro strain / gradient of the column is added to the constant mode,
+// so -y is the fluctuation problem's residual b - K x.
+template <int P, int NC, typename T, bool MACRO>
+__global__ void __launch_bounds__(256) k_operator(ElemView<T> ev, const T* __restrict__ x,
+                                                  T* __restrict__ y, double* __restrict__ epart,
+                                                  int ncols, int cpb) {
+    constexpr int NE = Order<P>::NE;
+    constexpr int NM = Order<P>::NM;
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    const int field = (col % 6) >= 3 ? 1 : 0;   // scalar solve: thermal / moisture
+    const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
+    double energy = 0.0;
+
+    for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < ev.nt; e += (int64_t)gridDim.y * rows) {
+        int dof[NE];
+#pragma unroll
+        for (int j = 0; j < NE; ++j) dof[j] = __ldg(ev.edofs + e * NE + j);
+        T G[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) G[i] = __ldg(ev.geo + e * 10 + i);
+        const T vol = __ldg(ev.geo + e * 10 + 9);
+        const T s = __ldg(ev.scale + col * 2 + __ldg(ev.phase + e));
+        constexpr int NMAT = NC == 3 ? 21 : 6;
+        T Dm[NMAT];
+#pragma unroll
+        for (int i = 0; i < NMAT; ++i)
+            Dm[i] = s * __ldg(ev.mat + e * (NC == 3 ? 21 : 12) + (NC == 3 ? 0 : 6 * field) + i);
+
+        T xv[NE][NC];
+#pragma unroll
+        for (int j = 0; j < NE; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) xv[j][c] = x[((int64_t)dof[j] * NC + c) * ncols + col];
+        T yv[NE][NC];
+#pragma unroll
+        for (int j = 0; j < NE; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) yv[j][c] = T(0);
+
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            // reference gradient mode m: V[k][c] = d u_c / d xi_k
+            T V[3][NC];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) V[k][c] = (m == 0) ? (xv[k + 1][c] - xv[0][c]) : T(0);
+#pragma unroll
+            for (int j = 4; j < NE; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const T a = Tab<T>::a(P, (k * NM + m) * NE + j);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) V[k][c] = fma(a, xv[j][c], V[k][c]);
+                }
+            // physical gradient H[c][l] = sum_k V[k][c] Jinv[k][l]
+            T H[NC][3];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+                    H[c][l] = V[0][c] * G[l] + V[1][c] * G[3 + l] + V[2][c] * G[6 + l];
+            if (MACRO && m == 0) {
+                if (NC == 3) {
+                    if (macro_id < 3) {
+                        H[macro_id % NC][macro_id] += T(1);
+                    } else {
+                        const int a = macro_id == 3 ? 0 : (macro_id == 4 ? 1 : 2);
+                        const int b = macro_id == 3 ? 1 : (macro_id == 4 ? 2 : 0);
+                        H[a % NC][b] += T(0.5);
+                        H[b % NC][a] += T(0.5);
+                    }
+                } else {
+                    H[0][macro_id] += T(1);
+                }
+            }
+            // stress / flux S[c][l]
+            T S[NC][3];
+            if (NC == 3) {
+                T ev6[6] = {H[0][0], H[1 % NC][1], H[2 % NC][2], H[0][1] + H[1 % NC][0],
+                            H[1 % NC][2] + H[2 % NC][1], H[2 % NC][0] + H[0][2]};
+                T sg[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    T t = T(0);
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) t = fma(Dm[ut6(i, j)], ev6[j], t);
+                    sg[i] = t;
+                }
+                S[0][0] = sg[0];
+                S[0][1] = sg[3];
+                S[0][2] = sg[5];
+                S[1 % NC][0] = sg[3];
+                S[1 % NC][1] = sg[1];
+                S[1 % NC][2] = sg[4];
+                S[2 % NC][0] = sg[5];
+                S[2 % NC][1] = sg[4];
+                S[2 % NC][2] = sg[2];
+            } else {
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+                    S[0][l] = Dm[s3(l, 0)] * H[0][0] + Dm[s3(l, 1)] * H[0][1] + Dm[s3(l, 2)] * H[0][2];
+            }
+            // W[k][c] = |T| sum_l Jinv[k][l] S[c][l]
+            T W[3][NC];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    W[k][c] = vol * (G[3 * k] * S[c][0] + G[3 * k + 1] * S[c][1] + G[3 * k + 2] * S[c][2]);
+            if (m == 0) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    yv[0][c] -= W[0][c] + W[1][c] + W[2][c];
+                    yv[1][c] += W[0][c];
+                    yv[2][c] += W[1][c];
+                    yv[3][c] += W[2][c];
+                }
+            }
+#pragma unroll
+            for (int j = 4; j < NE; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const T a = Tab<T>::a(P, (k * NM + m) * NE + j);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) yv[j][c] = fma(a, W[k][c], yv[j][c]);
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < NE; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                atomicAdd(y + ((int64_t)dof[j] * NC + c) * ncols + col, yv[j][c]);
+                if (epart) energy += (double)xv[j][c] * (double)yv[j][c];
+            }
+    }
+    if (epart) {
+        double acc[1] = {energy};
+        block_column_reduce<1>(acc, epart, ncols, cpb, col);
+    }
+}
+
+template <typename T>
+void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
+                     double* energy_partial, const Launch& L) {
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+#define RVE_OP_CASE(PP, NCC, MM)                                                                \
+    if (p == PP && nc == NCC && macro == MM) {                                                  \
+        k_operator<PP, NCC, T, MM><<<grid, block, 0, L.stream>>>(ev, x, y, energy_partial,      \
+                                                                 L.ncols, L.cpb);              \
+        return;                                                                                 \
+    }
+    RVE_OP_CASE(1, 3, false) RVE_OP_CASE(2, 3, false) RVE_OP_CASE(3, 3, false)
+    RVE_OP_CASE(1, 1, false) RVE_OP_CASE(2, 1, false) RVE_OP_CASE(3, 1, false)
+    RVE_OP_CASE(1, 3, true) RVE_OP_CASE(2, 3, true) RVE_OP_CASE(3, 3, true)
+    RVE_OP_CASE(1, 1, true) RVE_OP_CASE(2, 1, true) RVE_OP_CASE(3, 1, true)
+#undef RVE_OP_CASE
+}
+template void launch_operator<float>(int, int, bool, const ElemView<float>&, const float*, float*,
+                                     double*, const Launch&);
+template void launch_operator<double>(int, int, bool, const ElemView<double>&, const double*,
+                                      double*, double*, const Launch&);
+
+// ------------------------------------------------------ Jacobi diagonal (K6)
+// diag[field][phase][row] = unscaled diagonal of K restricted to one phase.
+template <int P, int NC, typename T>
+__global__ void k_diag(ElemView<T> ev, int64_t n_rows, T* __restrict__ diag) {
+    constexpr int NE = Order<P>::NE;
+    constexpr int NM = Order<P>::NM;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ev.nt) return;
+    double G[9];
+    for (int i = 0; i < 9; ++i) G[i] = ev.geo[e * 10 + i];
+    const double vol = ev.geo[e * 10 + 9];
+    const int ph = ev.phase[e];
+    const int nfield = NC == 3 ? 1 : 2;
+    for (int f = 0; f < nfield; ++f) {
+        double Dm[21];
+        const int nmat = NC == 3 ? 21 : 6;
+        for (int i = 0; i < nmat; ++i) Dm[i] = ev.mat[e * (NC == 3 ? 21 : 12) + 6 * f + i];
+        for (int j = 0; j < NE; ++j) {
+            const int dof = ev.edofs[e * NE + j];
+            double d[NC];
+            for (int c = 0; c < NC; ++c) d[c] = 0.0;
+            for (int m = 0; m < NM; ++m) {
+                double a[3];
+                for (int k = 0; k < 3; ++k) {
+                    if (j < 4)
+                        a[k] = (m == 0) ? ((j == k + 1) ? 1.0 : (j == 0 ? -1.0 : 0.0)) : 0.0;
+                    else
+                        a[k] = Tab<double>::a(P, (k * NM + m) * NE + j);
+                }
+                double g[3];
+                for (int l = 0; l < 3; ++l) g[l] = a[0] * G[l] + a[1] * G[3 + l] + a[2] * G[6 + l];
+                if (NC == 3) {
+                    for (int c = 0; c < 3; ++c) {
+                        // Voigt strain of e_c (x) g
+                        double ev6[6] = {0, 0, 0, 0, 0, 0};
+                        ev6[c] = g[c];
+                        if (c == 0) { ev6[3] = g[1]; ev6[5] = g[2]; }
+                        if (c == 1) { ev6[3] = g[0]; ev6[4] = g[2]; }
+                        if (c == 2) { ev6[4] = g[1]; ev6[5] = g[0]; }
+                        double en = 0;
+                        for (int i = 0; i < 6; ++i)
+                            for (int jj = 0; jj < 6; ++jj) en += ev6[i] * Dm[ut6(i, jj)] * ev6[jj];
+                        d[c % NC] += vol * en;
+                    }
+                } else {
+                    double en = 0;
+                    for (int l = 0; l < 3; ++l)
+                        for (int l2 = 0; l2 < 3; ++l2) en += g[l] * Dm[s3(l, l2)] * g[l2];
+                    d[0] += vol * en;
+                }
+            }
+            for (int c = 0; c < NC; ++c)
+                atomicAdd(diag + ((int64_t)(f * 2 + ph)) * n_rows + (int64_t)dof * NC + c, (T)d[c]);
+        }
+    }
+}
+
+template <typename T>
+void launch_diag(int p, int nc, int64_t n_rows, const ElemView<T>& ev, T* diag, cudaStream_t s) {
+    const int bs = 128;
+    const int64_t nb = (ev.nt + bs - 1) / bs;
+#define RVE_DG_CASE(PP, NCC)                                                                  \
+    if (p == PP && nc == NCC) {                                                               \
+        k_diag<PP, NCC, T><<<(unsigned)nb, bs, 0, s>>>(ev, n_rows, diag);                     \
+        return;                                                                               \
+    }
+    RVE_DG_CASE(1, 3) RVE_DG_CASE(2, 3) RVE_DG_CASE(3, 3)
+    RVE_DG_CASE(1, 1) RVE_DG_CASE(2, 1) RVE_DG_CASE(3, 1)
+#undef RVE_DG_CASE
+}
+template void launch_diag<double>(int, int, int64_t, const ElemView<double>&, double*, cudaStream_t);
+
+// ------------------------------------------------------------ geometry (K2)
+__global__ void k_geometry(int64_t nt, const double* __restrict__ xyz,
+                           const int32_t* __restrict__ lverts, double* __restrict__ geo64,
+                           float* __restrict__ geo32, int32_t* bad) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nt) return;
+    double v[4][3];
+    for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < 3; ++i) v[a][i] = xyz[3 * (int64_t)lverts[4 * e + a] + i];
+    double a[3], b[3], c[3];
+    for (int i = 0; i < 3; ++i) {
+        a[i] = v[1][i] - v[0][i];
+        b[i] = v[2][i] - v[0][i];
+        c[i] = v[3][i] - v[0][i];
+    }
+    double bc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+    double ca[3] = {c[1] * a[2] - c[2] * a[1], c[2] * a[0] - c[0] * a[2], c[0] * a[1] - c[1] * a[0]};
+    double ab[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    const double det = a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2];
+    const double scale = fmax(fmax(fabs(a[0]) + fabs(a[1]) + fabs(a[2]), fabs(b[0]) + fabs(b[1]) + fabs(b[2])),
+                              fabs(c[0]) + fabs(c[1]) + fabs(c[2]));
+    if (!(fabs(det) > 1e-12 * scale * scale * scale)) {
+        atomicExch(bad, 1);
+        return;
+    }
+    double g[10];
+    for (int i = 0; i < 3; ++i) {
+        g[i] = bc[i] / det;       // grad xi_1
+        g[3 + i] = ca[i] / det;   // grad xi_2
+        g[6 + i] = ab[i] / det;   // grad xi_3
+    }
+    g[9] = fabs(det) / 6.0;
+    for (int i = 0; i < 10; ++i) {
+        geo64[e * 10 + i] = g[i];
+        geo32[e * 10 + i] = (float)g[i];
+    }
+}
+
+void launch_geometry(int64_t nt, const double* xyz, const int32_t* lverts, double* geo64,
+                     float* geo32, int32_t* bad, cudaStream_t s) {
+    const int bs = 128;
+    k_geometry<<<(unsigned)((nt + bs - 1) / bs), bs, 0, s>>>(nt, xyz, lverts, geo64, geo32, bad);
+}
+
+// ----------------------------------------------------------- materials (K1)
+// Isotropic matrix; transversely isotropic yarn built in the fibre frame and
+// rotated with the Bond stress matrix M: D_global = M D_local M^T (Sec. 6).
+__global__ void k_materials(int64_t nt, const uint8_t* __restrict__ phase,
+                            const double* __restrict__ tangent, MaterialConsts mc,
+                            double* __restrict__ m64, float* __restrict__ m32,
+                            double* __restrict__ s64, float* __restrict__ s32, int32_t* bad) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nt) return;
+    double D[6][6] = {};
+    double kt[3][3] = {}, dt[3][3] = {};
+    if (phase[e] == 0) {
+        const double E = mc.Em, nu = mc.num;
+        const double lam = E * nu / ((1 + nu) * (1 - 2 * nu)), mu = E / (2 * (1 + nu));
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) D[i][j] = lam;
+            D[i][i] += 2 * mu;
+            D[3 + i][3 + i] = mu;
+            kt[i][i] = mc.km;
+            dt[i][i] = mc.dm;
+        }
+    } else {
+        double t[3] = {tangent[3 * e], tangent[3 * e + 1], tangent[3 * e + 2]};
+        const double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        if (!(tn > 0)) {
+            atomicExch(bad, 1);
+            return;
+        }
+        for (int i = 0; i < 3; ++i) t[i] /= tn;
+        double h[3] = {0, 0, 1};
+        if (fabs(t[2]) >= 0.9) { h[0] = 1; h[2] = 0; }
+        const double th = t[0] * h[0] + t[1] * h[1] + t[2] * h[2];
+        double a[3] = {h[0] - th * t[0], h[1] - th * t[1], h[2] - th * t[2]};
+        const double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        for (int i = 0; i < 3; ++i) a[i] /= an;
+        double b[3] = {t[1] * a[2] - t[2] * a[1], t[2] * a[0] - t[0] * a[2], t[0] * a[1] - t[1] * a[0]};
+        double R[3][3];   // columns = local axes (fibre, a, b) in global coordinates
+        for (int i = 0; i < 3; ++i) {
+            R[i][0] = t[i];
+            R[i][1] = a[i];
+            R[i][2] = b[i];
+        }
+        // local stiffness: invert the normal compliance block, shear moduli direct
+        const double S11 = 1 / mc.E1, S22 = 1 / mc.E2, S12 = -mc.nu12 / mc.E1, S23 = -mc.nu23 / mc.E2;
+        double Sn[3][3] = {{S11, S12, S12}, {S12, S22, S23}, {S12, S23, S22}};
+        double cof[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+                cof[i][j] = Sn[i1][j1] * Sn[i2][j2] - Sn[i1][j2] * Sn[i2][j1];
+            }
+        const double det = Sn[0][0] * cof[0][0] + Sn[0][1] * cof[0][1] + Sn[0][2] * cof[0][2];
+        if (!(det > 0)) {
+            atomicExch(bad, 1);
+            return;
+        }
+        double Dl[6][6] = {};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Dl[i][j] = cof[j][i] / det;
+        Dl[3][3] = mc.G12;                          // 12
+        Dl[5][5] = mc.G12;                          // 31
+        Dl[4][4] = mc.E2 / (2 * (1 + mc.nu23));     // 23
+        static const int VI[6] = {0, 1, 2, 0, 1, 2}, VJ[6] = {0, 1, 2, 1, 2, 0};
+        double M[6][6];
+        for (int I = 0; I < 6; ++I)
+            for (int J = 0; J < 6; ++J) {
+                const int i = VI[I], j = VJ[I], p = VI[J], q = VJ[J];
+                M[I][J] = (J < 3) ? R[i][p] * R[j][p] : R[i][p] * R[j][q] + R[i][q] * R[j][p];
+            }
+        double MD[6][6];
+        for (int I = 0; I < 6; ++I)
+            for (int J = 0; J < 6; ++J) {
+                double sacc = 0;
+                for (int K = 0; K < 6; ++K) sacc += M[I][K] * Dl[K][J];
+                MD[I][J] = sacc;
+            }
+        for (int I = 0; I < 6; ++I)
+            for (int J = 0; J < 6; ++J) {
+                double sacc = 0;
+                for (int K = 0; K < 6; ++K) sacc += MD[I][K] * M[J][K];
+                D[I][J] = sacc;
+            }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                kt[i][j] = (i == j ? mc.k2 : 0.0) + (mc.k1 - mc.k2) * t[i] * t[j];
+                dt[i][j] = (i == j ? mc.d2 : 0.0) + (mc.d1 - mc.d2) * t[i] * t[j];
+            }
+    }
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) {
+            const double v = 0.5 * (D[i][j] + D[j][i]) / mc.ref_mech;
+            m64[e * 21 + ut6(i, j)] = v;
+            m32[e * 21 + ut6(i, j)] = (float)v;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+            const double vk = kt[i][j] / mc.ref_k, vd = dt[i][j] / mc.ref_d;
+            s64[e * 12 + s3(i, j)] = vk;
+            s32[e * 12 + s3(i, j)] = (float)vk;
+            s64[e * 12 + 6 + s3(i, j)] = vd;
+            s32[e * 12 + 6 + s3(i, j)] = (float)vd;
+        }
+}
+
+void launch_materials(int64_t nt, const uint8_t* phase, const double* tangent,
+                      const MaterialConsts& mc, double* matm64, float* matm32, double* mats64,
+                      float* mats32, int32_t* bad, cudaStream_t s) {
+    const int bs = 128;
+    k_materials<<<(unsigned)((nt + bs - 1) / bs), bs, 0, s>>>(nt, phase, tangent, mc, matm64,
+                                                              matm32, mats64, mats32, bad);
+}
+
+// --------------------------------------------------------- degradation (K1)
+// 1 - omega = exp(-c alpha(T) t), alpha(T) = beta ln(1 - T/Tg) in kelvin,
+// c = clamp(c_wt / c_sat), t in days (Sec. 4, Eqs. alphaT and Model_final1).
+__global__ void k_degradation(int64_t n, const double* __restrict__ T_C,
+                              const double* __restrict__ c_wt, const double* __restrict__ t_h,
+                              double beta, double Tg_C, double c_sat, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c = fmin(fmax(c_wt[i] / c_sat, 0.0), 1.0);
+    const double alpha = beta * log(1.0 - (T_C[i] + 273.15) / (Tg_C + 273.15));
+    out[i] = exp(-c * alpha * (t_h[i] / 24.0));
+}
+
+void launch_degradation(int64_t n, const double* T_C, const double* c_wt, const double* t_h,
+                        double beta, double Tg_C, double c_sat, double* out, cudaStream_t s) {
+    if (n <= 0) return;
+    const int bs = 128;
+    k_degradation<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(n, T_C, c_wt, t_h, beta, Tg_C,
+                                                               c_sat, out);
+}
+
+template <typename T>
+__global__ void k_column_scales(int nrve, const double* __restrict__ w, int apply_to_yarn,
+                                int mech, T* __restrict__ scale) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= nrve * 6) return;
+    const double f = mech ? w[col / 6] : 1.0;
+    scale[2 * col + 0] = (T)f;
+    scale[2 * col + 1] = (T)((mech && apply_to_yarn) ? f : 1.0);
+}
+
+template <typename T>
+void launch_column_scales(int nrve, const double* w, int apply_to_yarn, bool mech, T* scale,
+                          cudaStream_t s) {
+    const int bs = 128;
+    k_column_scales<T><<<(nrve * 6 + bs - 1) / bs, bs, 0, s>>>(nrve, w, apply_to_yarn, mech ? 1 : 0,
+                                                               scale);
+}
+template void launch_column_scales<float>(int, const double*, int, bool, float*, cudaStream_t);
+template void launch_column_scales<double>(int, const double*, int, bool, double*, cudaStream_t);
+
+// ------------------------------------------------------------- PCG pieces
+template <typename T>
+__device__ __forceinline__ T inv_diag(const RowView<T>& rv, int64_t row, int col, int ncols) {
+    const int64_t dof = row / rv.nc;
+    if (rv.mask && rv.mask[dof]) return T(0);
+    const int f = (rv.nfield == 2 && (col % 6) >= 3) ? 1 : 0;
+    const T d = rv.scale[2 * col] * rv.diag[(int64_t)(2 * f) * rv.n_rows + row] +
+                rv.scale[2 * col + 1] * rv.diag[(int64_t)(2 * f + 1) * rv.n_rows + row];
+    return d > T(0) ? T(1) / d : T(0);
+}
+
+__global__ void k_finalize_alpha(const double* __restrict__ ep, int nby, int ncols, ColState cs) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    if (!cs.active[col]) {
+        cs.alpha[col] = 0.0;
+        return;
+    }
+    double pq = 0.0;
+    for (int b = 0; b < nby; ++b) pq += ep[(int64_t)b * ncols + col];
+    double a = cs.rz[col] / pq;
+    if (!(pq > 0.0) || !isfinite(a)) {
+        atomicOr(cs.flags, 1);
+        a = 0.0;
+        cs.active[col] = 0;
+    }
+    cs.alpha[col] = a;
+    cs.iters[col] += 1;
+}
+
+template <typename T>
+void launch_finalize_alpha(const double* energy_partial, ColState cs, const Launch& L) {
+    k_finalize_alpha<<<(L.ncols + 127) / 128, 128, 0, L.stream>>>(energy_partial, L.nby, L.ncols, cs);
+}
+template void launch_finalize_alpha<float>(const double*, ColState, const Launch&);
+template void launch_finalize_alpha<double>(const double*, ColState, const Launch&);
+
+// x += alpha p, r -= alpha q (when apply), partial (r, M^-1 r) per column.
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x, T* __restrict__ r,
+                                                const T* __restrict__ p, const T* __restrict__ q,
+                                                ColState cs, double* __restrict__ rzp, int ncols,
+                                                int cpb, int apply) {
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    const T a = apply ? (T)cs.alpha[col] : T(0);
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < rv.n_rows; i += (int64_t)gridDim.y * rows) {
+        const int64_t idx = i * ncols + col;
+        T rv_ = r[idx];
+        if (a != T(0)) {
+            x[idx] = fma(a, p[idx], x[idx]);
+            rv_ = fma(-a, q[idx], rv_);
+            r[idx] = rv_;
+        }
+        const T w = inv_diag(rv, i, col, ncols) * rv_;
+        acc += (double)rv_ * (double)w;
+    }
+    double accs[1] = {acc};
+    block_column_reduce<1>(accs, rzp, ncols, cpb, col);
+}
+
+template <typename T>
+void launch_update(const RowView<T>& rv, T* x, T* r, const T* p, const T* q, ColState cs,
+                   double* rz_partial, bool apply_update, const Launch& L) {
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+    k_update<T><<<grid, block, 0, L.stream>>>(rv, x, r, p, q, cs, rz_partial, L.ncols, L.cpb,
+                                               apply_update ? 1 : 0);
+}
+template void launch_update<float>(const RowView<float>&, float*, float*, const float*, const float*,
+                                   ColState, double*, bool, const Launch&);
+template void launch_update<double>(const RowView<double>&, double*, double*, const double*,
+                                    const double*, ColState, double*, bool, const Launch&);
+
+// partial C M^-1 r over the constraint support (m <= 12 rows)
+template <typename T>
+__global__ void __launch_bounds__(256) k_constraint_dot(RowView<T> rv, const T* __restrict__ r,
+                                                        double* __restrict__ cp, int ncols, int cpb) {
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+    const int m = rv.m;
+    for (int64_t s = (int64_t)blockIdx.y * rows + rr; s < rv.n_sup; s += (int64_t)gridDim.y * rows) {
+        const int64_t row = rv.sup_row[s];
+        const double w = (double)(inv_diag(rv, row, col, ncols) * r[row * ncols + col]);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            if (k < m) acc[k] += rv.sup_coef[s * m + k] * w;
+    }
+    __shared__ double buf[256];
+    for (int k = 0; k < m; ++k) {
+        buf[threadIdx.x] = acc[k];
+        __syncthreads();
+        if (rr == 0) {
+            double sacc = 0.0;
+            for (int q = 0; q < rows; ++q) sacc += buf[q * cpb + cl];
+            cp[((int64_t)blockIdx.y * m + k) * ncols + col] = sacc;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+void launch_constraint_dot(const RowView<T>& rv, const T* r, double* c_partial, const Launch& L) {
+    if (rv.m == 0) return;
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+    k_constraint_dot<T><<<grid, block, 0, L.stream>>>(rv, r, c_partial, L.ncols, L.cpb);
+}
+template void launch_constraint_dot<float>(const RowView<float>&, const float*, double*, const Launch&);
+template void launch_constraint_dot<double>(const RowView<double>&, const double*, double*,
+                                            const Launch&);
+
+// mu = S^-1 w, rz = (r, M^-1 r) - w . mu, beta, convergence.
+__global__ void k_finalize_beta(int m, const double* __restrict__ rzp, const double* __restrict__ cp,
+                                int nby, int ncols, ColState cs, int first) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    if (!first && !cs.active[col]) return;
+    double rz = 0.0;
+    for (int b = 0; b < nby; ++b) rz += rzp[(int64_t)b * ncols + col];
+    double w[12], mu[12];
+    for (int k = 0; k < m; ++k) {
+        double s = 0.0;
+        for (int b = 0; b < nby; ++b) s += cp[((int64_t)b * m + k) * ncols + col];
+        w[k] = s;
+    }
+    if (m > 0) {
+        const double* Lc = cs.schur + (int64_t)col * m * m;
+        for (int i = 0; i < m; ++i) {   // forward
+            double t = w[i];
+            for (int j = 0; j < i; ++j) t -= Lc[i * m + j] * mu[j];
+            mu[i] = t / Lc[i * m + i];
+        }
+        for (int i = m - 1; i >= 0; --i) {   // backward
+            double t = mu[i];
+            for (int j = i + 1; j < m; ++j) t -= Lc[j * m + i] * mu[j];
+            mu[i] = t / Lc[i * m + i];
+        }
+        for (int k = 0; k < m; ++k) {
+            rz -= w[k] * mu[k];
+            cs.mu[(int64_t)k * ncols + col] = mu[k];
+        }
+    }
+    if (!isfinite(rz)) {
+        atomicOr(cs.flags, 1);
+        cs.active[col] = 0;
+        return;
+    }
+    if (first) {
+        cs.rz0[col] = rz;
+        cs.rz[col] = rz;
+        cs.beta[col] = 0.0;
+        cs.iters[col] = 0;
+        cs.active[col] = rz > 0.0 ? 1 : 0;
+        return;
+    }
+    cs.beta[col] = rz / cs.rz[col];
+    cs.rz[col] = rz;
+    if (rz <= cs.tol * cs.tol * cs.rz0[col]) cs.active[col] = 0;
+}
+
+void launch_finalize_beta(int m, const double* rz_partial, const double* c_partial, ColState cs,
+                          bool first, const Launch& L) {
+    k_finalize_beta<<<(L.ncols + 127) / 128, 128, 0, L.stream>>>(m, rz_partial, c_partial, L.nby,
+                                                                  L.ncols, cs, first ? 1 : 0);
+}
+
+// p = M^-1 (r - C^T mu) + beta p ; q = 0
+template <typename T>
+__global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, const T* __restrict__ r,
+                                                 T* __restrict__ p, T* __restrict__ q, ColState cs,
+                                                 int ncols, int cpb, int first) {
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    const bool act = cs.active[col] != 0;
+    const T beta = first ? T(0) : (T)cs.beta[col];
+    const int m = rv.m;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < rv.n_rows; i += (int64_t)gridDim.y * rows) {
+        const int64_t idx = i * ncols + col;
+        q[idx] = T(0);
+        if (!act) continue;
+        T rr_ = r[idx];
+        if (m > 0) {
+            const int32_t s = rv.sup_of_row[i];
+            if (s >= 0) {
+                double corr = 0.0;
+                for (int k = 0; k < m; ++k) corr += rv.sup_coef[(int64_t)s * m + k] * cs.mu[(int64_t)k * ncols + col];
+                rr_ = (T)((double)rr_ - corr);
+            }
+        }
+        const T z = inv_diag(rv, i, col, ncols) * rr_;
+        p[idx] = first ? z : fma(beta, p[idx], z);
+    }
+}
+
+template <typename T>
+void launch_pupdate(const RowView<T>& rv, const T* r, T* p, T* q, ColState cs, bool first,
+                    const Launch& L) {
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+    k_pupdate<T><<<grid, block, 0, L.stream>>>(rv, r, p, q, cs, L.ncols, L.cpb, first ? 1 : 0);
+}
+template void launch_pupdate<float>(const RowView<float>&, const float*, float*, float*, ColState,
+                                    bool, const Launch&);
+template void launch_pupdate<double>(const RowView<double>&, const double*, double*, double*,
+                                     ColState, bool, const Launch&);
+
+// S = C M^-1 C^T per column (one block per (column, row k)), then Cholesky.
+template <typename T>
+__global__ void k_schur_rows(RowView<T> rv, double* __restrict__ S, int ncols) {
+    const int col = blockIdx.x, k = blockIdx.y, m = rv.m;
+    double acc[12];
+    for (int l = 0; l < 12; ++l) acc[l] = 0.0;
+    for (int64_t s = threadIdx.x; s < rv.n_sup; s += blockDim.x) {
+        const int64_t row = rv.sup_row[s];
+        const double w = (double)inv_diag(rv, row, col, ncols) * rv.sup_coef[s * m + k];
+        for (int l = 0; l < m; ++l) acc[l] += w * rv.sup_coef[s * m + l];
+    }
+    __shared__ double buf[256];
+    for (int l = 0; l < m; ++l) {
+        buf[threadIdx.x] = acc[l];
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) buf[threadIdx.x] += buf[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) S[((int64_t)col * m + k) * m + l] = buf[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_cholesky(int m, int ncols, double* __restrict__ S, int32_t* flags) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    double* A = S + (int64_t)col * m * m;
+    for (int j = 0; j < m; ++j) {
+        double s = A[j * m + j];
+        for (int k = 0; k < j; ++k) s -= A[j * m + k] * A[j * m + k];
+        if (!(s > 0)) {
+            atomicOr(flags, 2);
+            s = 1e-300;
+        }
+        const double d = sqrt(s);
+        A[j * m + j] = d;
+        for (int i = j + 1; i < m; ++i) {
+            double t = A[i * m + j];
+            for (int k = 0; k < j; ++k) t -= A[i * m + k] * A[j * m + k];
+            A[i * m + j] = t / d;
+        }
+        for (int i = 0; i < j; ++i) A[i * m + j] = 0.0;
+    }
+}
+
+template <typename T>
+void launch_schur(const RowView<T>& rv, ColState cs, const Launch& L) {
+    if (rv.m == 0) return;
+    dim3 grid(L.ncols, rv.m);
+    k_schur_rows<T><<<grid, 256, 0, L.stream>>>(rv, cs.schur, L.ncols);
+    k_cholesky<<<(L.ncols + 127) / 128, 128, 0, L.stream>>>(rv.m, L.ncols, cs.schur, cs.flags);
+}
+template void launch_schur<float>(const RowView<float>&, ColState, const Launch&);
+template void launch_schur<double>(const RowView<double>&, ColState, const Launch&);
+
+// ------------------------------------------------- homogenisation reductions
+// Per column i of RVE b: sum_rows b_i u_j and u_i r_j, j over the RVE's six
+// columns (FP64).  Used for the energy form
+//   V C_ij = V <D>_ij - b_i . u_j - u_i . r_j      (r = b - K u).
+__global__ void __launch_bounds__(256) k_gram(int64_t n_rows, const double* __restrict__ b,
+                                              const double* __restrict__ u,
+                                              const double* __restrict__ r,
+                                              double* __restrict__ part, int ncols, int cpb) {
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    const int base = (col / 6) * 6;
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < n_rows; i += (int64_t)gridDim.y * rows) {
+        const double bi = b[i * ncols + col], ui = u[i * ncols + col];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            acc[j] += bi * u[i * ncols + base + j];
+            acc[6 + j] += ui * r[i * ncols + base + j];
+        }
+    }
+    block_column_reduce<12>(acc, part, ncols, cpb, col);
+}
+
+void launch_gram(int64_t n_rows, const double* b, const double* u, const double* r,
+                 double* partial, const Launch& L) {
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+    k_gram<<<grid, block, 0, L.stream>>>(n_rows, b, u, r, partial, L.ncols, L.cpb);
+}
+
+// Volume integrals per column: int sigma(eps_bar + eps(u)) (Eq. macro_stress)
+// and int sigma(eps_bar) (the Voigt term), 6 + 6 values (3 + 3 for scalars).
+template <int P, int NC, typename T>
+__global__ void __launch_bounds__(256) k_mean_stress(ElemView<T> ev, const T* __restrict__ u,
+                                                     double* __restrict__ part, int ncols, int cpb) {
+    constexpr int NE = Order<P>::NE;
+    constexpr int NM = Order<P>::NM;
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    const int field = (col % 6) >= 3 ? 1 : 0;
+    const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+    for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < ev.nt; e += (int64_t)gridDim.y * rows) {
+        double G[9];
+        for (int i = 0; i < 9; ++i) G[i] = (double)ev.geo[e * 10 + i];
+        const double vol = (double)ev.geo[e * 10 + 9];
+        const double s = (double)ev.scale[col * 2 + ev.phase[e]];
+        double V[3][NC];
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < NC; ++c) {
+                double v = (double)u[((int64_t)ev.edofs[e * NE + k + 1] * NC + c) * ncols + col] -
+                           (double)u[((int64_t)ev.edofs[e * NE] * NC + c) * ncols + col];
+                for (int j = 4; j < NE; ++j)
+                    v += Tab<double>::a(P, (k * NM + 0) * NE + j) *
+                         (double)u[((int64_t)ev.edofs[e * NE + j] * NC + c) * ncols + col];
+                V[k][c] = v;
+            }
+        double H[NC][3];
+        for (int c = 0; c < NC; ++c)
+            for (int l = 0; l < 3; ++l) H[c][l] = V[0][c] * G[l] + V[1][c] * G[3 + l] + V[2][c] * G[6 + l];
+        if (NC == 3) {
+            double Dm[21];
+            for (int i = 0; i < 21; ++i) Dm[i] = s * (double)ev.mat[e * 21 + i];
+            double ev6[6] = {H[0][0], H[1 % NC][1], H[2 % NC][2], H[0][1] + H[1 % NC][0],
+                             H[1 % NC][2] + H[2 % NC][1], H[2 % NC][0] + H[0][2]};
+            ev6[macro_id] += 1.0;   // unit engineering macro strain of this column
+            for (int i = 0; i < 6; ++i) {
+                double t = 0.0;
+                for (int j = 0; j < 6; ++j) t += Dm[ut6(i, j)] * ev6[j];
+                acc[i] += vol * t;
+                acc[6 + i] += vol * Dm[ut6(i, macro_id)];
+            }
+        } else {
+            double Km[6];
+            for (int i = 0; i < 6; ++i) Km[i] = s * (double)ev.mat[e * 12 + 6 * field + i];
+            double g[3] = {H[0][0], H[0][1], H[0][2]};
+            g[macro_id] += 1.0;
+            for (int l = 0; l < 3; ++l) {
+                acc[l] += vol * (Km[s3(l, 0)] * g[0] + Km[s3(l, 1)] * g[1] + Km[s3(l, 2)] * g[2]);
+                acc[6 + l] += vol * Km[s3(l, macro_id)];
+            }
+        }
+    }
+    block_column_reduce<12>(acc, part, ncols, cpb, col);
+}
+
+template <typename T>
+void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const T* u, double* partial,
+                        const Launch& L) {
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+#define RVE_MS_CASE(PP, NCC)                                                                  \
+    if (p == PP && nc == NCC) {                                                               \
+        k_mean_stress<PP, NCC, T><<<grid, block, 0, L.stream>>>(ev, u, partial, L.ncols, L.cpb); \
+        return;                                                                               \
+    }
+    RVE_MS_CASE(1, 3) RVE_MS_CASE(2, 3) RVE_MS_CASE(3, 3)
+    RVE_MS_CASE(1, 1) RVE_MS_CASE(2, 1) RVE_MS_CASE(3, 1)
+#undef RVE_MS_CASE
+}
+template void launch_mean_stress<double>(int, int, const ElemView<double>&, const double*, double*,
+                                         const Launch&);
+
+__global__ void k_reduce_partials(int nby, int width, const double* __restrict__ part,
+                                  double* __restrict__ out) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= width) return;
+    double s = 0.0;
+    for (int b = 0; b < nby; ++b) s += part[(int64_t)b * width + w];
+    out[w] = s;
+}
+
+void launch_reduce_partials(int nby, int width, const double* partial, double* out, cudaStream_t s) {
+    k_reduce_partials<<<(width + 127) / 128, 128, 0, s>>>(nby, width, partial, out);
+}
+
+// ---------------------------------------------------------- elementwise
+__global__ void k_cast_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+__global__ void k_axpy_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] += (double)a[i];
+}
+__global__ void k_neg(int64_t n, double* __restrict__ a) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = -a[i];
+}
+static unsigned ew_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s) {
+    k_cast_d2f<<<ew_blocks(n), 256, 0, s>>>(n, a, b);
+}
+void launch_axpy_f2d(int64_t n, const float* a, double* b, cudaStream_t s) {
+    k_axpy_f2d<<<ew_blocks(n), 256, 0, s>>>(n, a, b);
+}
+void launch_neg(int64_t n, double* a, cudaStream_t s) { k_neg<<<ew_blocks(n), 256, 0, s>>>(n, a); }
+
+}  // namespace rve

@@ -1,0 +1,124 @@
+// Launch wrappers for the librve device kernels (defined in kernels.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rve {
+
+// Column layout shared by every vector kernel.  A vector of one field holds
+// n_rows = n_scalar_dofs * NC rows (NC = 3 for mechanics, 1 for the scalar
+// fields) and ncols right-hand sides, stored row-major: v[row * ncols + col].
+// Columns are grouped by RVE: RVE b owns columns [6b, 6b+6).  Mechanics uses
+// the six unit strains; the scalar solve uses columns 0..2 for the thermal and
+// 3..5 for the moisture unit gradients.
+struct Launch {
+    int ncols = 6;
+    int cpb = 6;          // columns per block (divides ncols)
+    int rows_per_block = 42;
+    int nby = 1;          // grid.y of the 2-D launches (partials are [nby][ncols][...])
+    cudaStream_t stream = 0;
+};
+
+template <typename T>
+struct ElemView {
+    int64_t nt = 0;
+    const int32_t* edofs = nullptr;   // [nt][ne]
+    const T* geo = nullptr;           // [nt][10]: Jinv (row k = grad xi_k), |T|
+    const T* mat = nullptr;           // mech [nt][21] upper-triangular Voigt D; scalar [nt][12] k(6), d(6)
+    const uint8_t* phase = nullptr;   // [nt]
+    const T* scale = nullptr;         // [ncols][2] factor per column and phase
+};
+
+// Per-row preconditioner / constraint data of one field.
+template <typename T>
+struct RowView {
+    int64_t n_rows = 0;
+    const T* diag = nullptr;          // [nfield][2 phases][n_rows], nfield = 1 (mech) or 2 (scalar)
+    const uint8_t* mask = nullptr;    // [n_scalar_dofs] 1 = Dirichlet-constrained (or nullptr)
+    const T* scale = nullptr;         // [ncols][2]
+    int nfield = 1;
+    int nc = 3;
+    // constraint rows (periodic / Neumann), FP64
+    int m = 0;                        // number of rows
+    int64_t n_sup = 0;                // support entries (rows of the vector touched by C)
+    const int64_t* sup_row = nullptr; // [n_sup] vector row
+    const double* sup_coef = nullptr; // [n_sup][m]
+    const int32_t* sup_of_row = nullptr;  // [n_rows] index into support or -1
+};
+
+// Per-column PCG state, FP64, each array [ncols] unless noted.
+struct ColState {
+    double* rz;       // current (r, z)
+    double* rz0;      // initial (r, z)
+    double* alpha;
+    double* beta;
+    double* mu;       // [m][ncols] constraint multipliers of the current residual
+    double* schur;    // [ncols][m*m] Cholesky factor of C M^-1 C^T
+    int32_t* active;  // 1 while the column iterates
+    int32_t* iters;   // iterations taken
+    int32_t* flags;   // [1] bit0: numeric error
+    double tol;       // relative tolerance on sqrt(rz / rz0)
+};
+
+void upload_basis_tables();
+
+// y += K x (+ macro load when macro != 0); energy partials x.Kx per column.
+template <typename T>
+void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
+                     double* energy_partial, const Launch& L);
+
+template <typename T>
+void launch_diag(int p, int nc, int64_t n_rows, const ElemView<T>& ev, T* diag, cudaStream_t s);
+
+void launch_geometry(int64_t nt, const double* xyz, const int32_t* lverts, double* geo64,
+                     float* geo32, int32_t* bad, cudaStream_t s);
+
+struct MaterialConsts {
+    double Em, num, km, dm;
+    double E1, E2, G12, nu12, nu23, k1, k2, d1, d2;
+    double ref_mech, ref_k, ref_d;   // internal scaling (outputs multiplied back)
+};
+void launch_materials(int64_t nt, const uint8_t* phase, const double* tangent,
+                      const MaterialConsts& mc, double* matm64, float* matm32, double* mats64,
+                      float* mats32, int32_t* bad, cudaStream_t s);
+
+void launch_degradation(int64_t n, const double* T_C, const double* c_wt, const double* t_h,
+                        double beta, double Tg_C, double c_sat, double* out, cudaStream_t s);
+
+// column scales from per-RVE degradation factors
+template <typename T>
+void launch_column_scales(int nrve, const double* w, int apply_to_yarn, bool mech, T* scale,
+                          cudaStream_t s);
+
+// PCG pieces
+template <typename T>
+void launch_finalize_alpha(const double* energy_partial, ColState cs, const Launch& L);
+template <typename T>
+void launch_update(const RowView<T>& rv, T* x, T* r, const T* p, const T* q, ColState cs,
+                   double* rz_partial, bool apply_update, const Launch& L);
+template <typename T>
+void launch_constraint_dot(const RowView<T>& rv, const T* r, double* c_partial, const Launch& L);
+void launch_finalize_beta(int m, const double* rz_partial, const double* c_partial, ColState cs,
+                          bool first, const Launch& L);
+template <typename T>
+void launch_pupdate(const RowView<T>& rv, const T* r, T* p, T* q, ColState cs, bool first,
+                    const Launch& L);
+template <typename T>
+void launch_schur(const RowView<T>& rv, ColState cs, const Launch& L);
+
+// reductions for the homogenised tensors
+void launch_gram(int64_t n_rows, const double* b, const double* u, const double* r,
+                 double* partial, const Launch& L);
+template <typename T>
+void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const T* u, double* partial,
+                        const Launch& L);
+void launch_reduce_partials(int nby, int width, const double* partial, double* out,
+                            cudaStream_t s);
+
+// elementwise helpers
+void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
+void launch_axpy_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
+void launch_neg(int64_t n, double* a, cudaStream_t s);
+
+}  // namespace rve
