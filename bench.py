@@ -1,0 +1,347 @@
+"""Benchmark: batched RVE homogenisation throughput on one GB300 (or N, weak scaling).
+
+Workload (one step): the batched FE^2 evaluation of 4096 macro Gauss points,
+each with its own degradation state (T ~ U(20,60) C, moisture ~ U(0,1.5) wt%,
+time = 10^U(0,4) h, seed 2 + rank), RVE plain-weave grids 16x16x6 / 24x24x8 /
+32x32x10 and order p in {1,2} drawn uniformly, periodic BC; each point solves
+6 mechanical + 3 thermal + 3 moisture cell problems and returns C, K, D.
+Mixed precision: FP32 operator and vectors, FP64 scalars / reductions and
+FP64 residual refinement.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import rve_inputs as ri  # noqa: E402
+
+METRIC = "RVE homogenisations/s on 1 GB300: batched PCG vs surrogate at ≤1e-2 rel err"
+UNIT = "homogenisations/s"
+G_POINTS = 4096
+SEED = 2
+WORKLOAD = ("batched FE2 evaluation: 4096 macro Gauss points per GPU, plain-weave RVEs on "
+            "16x16x6 / 24x24x8 / 32x32x10 Kuhn grids, p in {1,2}, periodic BC, 12 load cases "
+            "per RVE (6 mech + 3 thermal + 3 moisture), degradation state per point from the "
+            "Sec. 4 law, FP32 operator + FP64 reductions/refinement, tensors to 1e-6")
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--points", type=int, default=G_POINTS)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for i, n in enumerate(names):
+                    if r[5 + i].strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+def build_meshes(ctx, rve):
+    """The six mesh classes (3 grids x 2 orders), periodic BC, nominal constituents."""
+    meshes, classes = [], []
+    for si, grid in enumerate(ri.SIZE_CLASSES):
+        xyz, tets, phase, tangent = ri.weave_rve(*grid)
+        for p in ri.P_CLASSES:
+            m = ctx.mesh_load(xyz, tets, p, phase, tangent)
+            m.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+            m.set_bc(rve.BC_PERIODIC)
+            meshes.append(m)
+            classes.append((si, p))
+    return meshes, classes
+
+
+def mesh_ids(size, p, classes):
+    lut = {c: i for i, c in enumerate(classes)}
+    return np.array([lut[(int(s), int(q))] for s, q in zip(size, p)], np.int32)
+
+
+def operator_bytes_per_unit(classes, meshes):
+    """Algorithmic bytes of one operator launch per RVE column group:
+    x read + y written (n_rows * 6 * 4 B each) + element data once per launch."""
+    out = {}
+    for (si, p), m in zip(classes, meshes):
+        info = m.info()
+        N = info["n_scalar_dofs"]
+        nt = info["n_tets"]
+        ne = {1: 4, 2: 10, 3: 20}[p]
+        out[(si, p)] = {"mech_rows": 3 * N, "scal_rows": N, "nt": nt,
+                        "elem_bytes_mech": nt * (4 * ne + 4 * 10 + 4 * 21 + 1),
+                        "elem_bytes_scal": nt * (4 * ne + 4 * 10 + 4 * 12 + 1)}
+    return out
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1610_03484_gb300 as rve
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = rve.Context(precision=rve.PREC_MIXED, rtol=1e-8, inner_rtol=1e-5, max_refine=4,
+                      batch=args.batch, stream=stream.cuda_stream, device=local)
+    meshes, classes = build_meshes(ctx, rve)
+    G = args.points
+    T, c, t, size, p = ri.gauss_point_states(G, SEED + rank)
+    mid = mesh_ids(size, p, classes)
+    # device-resident inputs / outputs for `value`
+    Td = torch.tensor(T, dtype=torch.float64, device=dev)
+    cd = torch.tensor(c, dtype=torch.float64, device=dev)
+    td = torch.tensor(t, dtype=torch.float64, device=dev)
+    Cd = torch.zeros((G, 36), dtype=torch.float64, device=dev)
+    Kd = torch.zeros((G, 9), dtype=torch.float64, device=dev)
+    Dd = torch.zeros((G, 9), dtype=torch.float64, device=dev)
+    Sd = torch.zeros(G, dtype=torch.int32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        st, rc = ctx.macro_update_dev(meshes, Td.data_ptr(), cd.data_ptr(), td.data_ptr(), mid,
+                                      Cd.data_ptr(), Kd.data_ptr(), Dd.data_ptr(), Sd.data_ptr())
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    launches = 0
+    op_ms, op_n = 0.0, 0
+    times = []
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        launches += st["kernel_launches"]
+        op_ms += st["op_ms"]
+        op_n += st["op_launches"]
+    barrier(world)
+    clk = clocks.stop()
+    status = Sd.cpu().numpy()
+    local_s = sum(times) / 1000.0
+    job_s = max_over_ranks(local_s, world)
+    units = sum_over_ranks(G * args.steps, world)
+    value = units / job_s
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    Th = torch.tensor(T).pin_memory()
+    ch = torch.tensor(c).pin_memory()
+    th = torch.tensor(t).pin_memory()
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Cc, Kk, Ddd, stt, _, _ = ctx.macro_update(meshes, Th.numpy(), ch.numpy(), th.numpy(), mid,
+                                                  allow_not_converged=True)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(sum(e2e_times), world)
+    e2e_value = sum_over_ranks(G * len(e2e_times), world) / e2e_s
+
+    pk, pk_kind = peaks()
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": job_s * 1000.0 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points_per_gpu": G, "seed": SEED, "bc": "periodic",
+                   "precision": "FP32 operator, FP64 reductions + refinement", "rtol": 1e-8,
+                   "l2": "256 MB buffer written between timed steps; per-step working set >> 129 MB L2",
+                   "status_ok": int((status == 0).sum())},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": G * 3 * 8,
+                "d2h_bytes_per_step": G * (36 + 9 + 9) * 8 + G * 4},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": None,
+        "cpu_baseline": None,
+    }
+    if op_n > 0:
+        result["roofline"] = {"kernel": "k_operator", "op_ms_total": op_ms, "launches": op_n}
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        result["cpu_baseline"] = cpu_baseline(budget_s=20.0)
+    for m in meshes:
+        m.free()
+    ctx.close()
+    return result
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_one(grid, p, T, c, t):
+    from oracle import fem
+    from oracle import materials as mt
+    xyz, tets, phase, tangent = ri.weave_rve(*grid)
+    w = float(mt.one_minus_omega(T, c, t))
+    m0 = ri.NOMINAL_MATRIX
+    mat = ri.MatrixProps(E=m0.E * w, nu=m0.nu, k=m0.k, d=m0.d)
+    D, K, Dd = mt.element_tensors(phase, tangent, mat, ri.NOMINAL_YARN)
+    return fem.homogenise(xyz, tets, grid, p, fem.BC_PERIODIC, D, K, Dd)
+
+
+def cpu_baseline(budget_s=20.0):
+    """Times the FP64 oracle on the cheapest RVE class of the workload (16x16x6,
+    p = 1), repeating whole homogenisations (12 load cases) until the budget."""
+    T, c, t, _, _ = ri.gauss_point_states(64, SEED)
+    grid, p = ri.SIZE_CLASSES[0], 1
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle_one(grid, p, T[n], c[n], t[n])
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 64:
+            break
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} homogenisations (12 load cases each) of the 16x16x6 p=1 class, the cheapest "
+                      f"class of the workload, single-threaded FP64 oracle; larger classes are slower, so "
+                      f"this overstates the CPU rate on the full mix"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    T, c, t, _, _ = ri.gauss_point_states(64, SEED)
+    grid, p = ri.SIZE_CLASSES[0], 1
+    for i in range(args.warmup):
+        oracle_one(grid, p, T[i % 64], c[i % 64], t[i % 64])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle_one(grid, p, T[i % 64], c[i % 64], t[i % 64])
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    sample = ("one homogenisation (12 load cases) per step of the 16x16x6 p=1 class (the cheapest class of "
+              "the workload), FP64 CPU oracle, single thread")
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1000 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        res = run_reference(args, world, rank)
+    else:
+        res = run_ours(args, world, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

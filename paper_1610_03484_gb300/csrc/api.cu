@@ -478,22 +478,29 @@ struct Solver {
         return RVE_OK;
     }
 
-    // relative projected residual sqrt((r, P r) / (b, P b)) per column
-    int rel_residual(const double* r, const std::vector<double>& bnorm2, double& worst) {
+    // Projects r in place (r <- r - C^T mu, the constraint-force part removed)
+    // and returns per column rz = (r, M^-1 r) of the projected residual and the
+    // worst relative value sqrt(rz / bnorm2).
+    int rel_residual(double* r, const std::vector<double>& bnorm2, double& worst,
+                     std::vector<double>* rz_out = nullptr) {
         ColState cs = cs64;
-        cs.tol = 0;
         RowView<double> rvw = rv<double>(m->scale64);
-        launch_update<double>(rvw, nullptr, const_cast<double*>(r), nullptr, nullptr, cs,
-                              m->rzp.as<double>(), false, L);
-        launch_constraint_dot<double>(rvw, r, m->cpart.as<double>(), L);
-        launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, true, L);
-        *launches += 3;
+        if (f.m > 0) {
+            launch_schur<double>(rvw, cs, L);
+            launch_constraint_dot<double>(rvw, r, m->cpart.as<double>(), L);
+            launch_constraint_multipliers(f.m, m->cpart.as<double>(), cs, L);
+            *launches += 4;
+        }
+        launch_project_residual<double>(rvw, r, cs, m->rzp.as<double>(), L);
+        launch_reduce_partials(L.nby, ncols, m->rzp.as<double>(), m->gsum.as<double>(), s);
+        *launches += 2;
         std::vector<double> rz(ncols);
-        RVE_CUDA(cudaMemcpyAsync(rz.data(), cs.rz0, sizeof(double) * ncols, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaMemcpyAsync(rz.data(), m->gsum.p, sizeof(double) * ncols, cudaMemcpyDeviceToHost, s));
         RVE_CUDA(cudaStreamSynchronize(s));
         worst = 0;
         for (int c = 0; c < ncols; ++c)
             if (bnorm2[c] > 0) worst = std::max(worst, std::sqrt(std::max(rz[c], 0.0) / bnorm2[c]));
+        if (rz_out) *rz_out = rz;
         return RVE_OK;
     }
 
@@ -508,14 +515,12 @@ struct Solver {
         RVE_CUDA(cudaMemsetAsync(x64, 0, nv * 8, s));
         RVE_TRY(residual64(x64, b64));   // b = -(K 0 + macro)
         RVE_CUDA(cudaMemcpyAsync(r64, b64, nv * 8, cudaMemcpyDeviceToDevice, s));
-        // reference norms (b, P b)
+        // reference norms (b, P b); r64 becomes the projected right-hand side
         std::vector<double> bn(ncols, 1.0);
         {
             double dummy;
             std::vector<double> ones(ncols, 1.0);
-            RVE_TRY(rel_residual(b64, ones, dummy));
-            RVE_CUDA(cudaMemcpyAsync(bn.data(), cs64.rz0, sizeof(double) * ncols, cudaMemcpyDeviceToHost, s));
-            RVE_CUDA(cudaStreamSynchronize(s));
+            RVE_TRY(rel_residual(r64, ones, dummy, &bn));
         }
         out.iterations = 0;
         out.sweeps = 0;
@@ -575,7 +580,8 @@ struct Solver {
                 for (int j = 0; j < 6; ++j) {
                     const int ci = 6 * b + i, cj = 6 * b + j;
                     // V C_ij = V <D>_ij - b_i . u_j - u_i . r_j
-                    const double e = Ms[cj * 12 + 6 + i] - Gs[ci * 12 + j] - Gs[ci * 12 + 6 + j];
+                    const int irow = f.nc == 3 ? i : i % 3;   // flux component of the scalar fields
+                    const double e = Ms[cj * 12 + 6 + irow] - Gs[ci * 12 + j] - Gs[ci * 12 + 6 + j];
                     out.tensor[b * 36 + i * 6 + j] = e / V;
                     out.sig[b * 36 + i * 6 + j] = Ms[cj * 12 + (f.nc == 3 ? i : i % 3)] / V;
                 }

@@ -639,11 +639,12 @@ template void launch_constraint_dot<double>(const RowView<double>&, const double
                                             const Launch&);
 
 // mu = S^-1 w, rz = (r, M^-1 r) - w . mu, beta, convergence.
+// first: 0 = iteration, 1 = initial residual, 2 = multipliers only (no state change)
 __global__ void k_finalize_beta(int m, const double* __restrict__ rzp, const double* __restrict__ cp,
                                 int nby, int ncols, ColState cs, int first) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncols) return;
-    if (!first && !cs.active[col]) return;
+    if (first == 0 && !cs.active[col]) return;
     double rz = 0.0;
     for (int b = 0; b < nby; ++b) rz += rzp[(int64_t)b * ncols + col];
     double w[12], mu[12];
@@ -669,6 +670,7 @@ __global__ void k_finalize_beta(int m, const double* __restrict__ rzp, const dou
             cs.mu[(int64_t)k * ncols + col] = mu[k];
         }
     }
+    if (first == 2) return;
     if (!isfinite(rz)) {
         atomicOr(cs.flags, 1);
         cs.active[col] = 0;
@@ -693,9 +695,53 @@ void launch_finalize_beta(int m, const double* rz_partial, const double* c_parti
                                                                   L.ncols, cs, first ? 1 : 0);
 }
 
+void launch_constraint_multipliers(int m, const double* c_partial, ColState cs, const Launch& L) {
+    if (m == 0) return;
+    k_finalize_beta<<<(L.ncols + 127) / 128, 128, 0, L.stream>>>(m, c_partial, c_partial, L.nby,
+                                                                  L.ncols, cs, 2);
+}
+
+// Residual reset r <- r - C^T mu on the constraint support (the part of the
+// residual that the constraint forces carry), and partial (r, M^-1 r) of the
+// projected residual, computed without cancellation.
+template <typename T>
+__global__ void __launch_bounds__(256) k_project_residual(RowView<T> rv, T* __restrict__ r, ColState cs,
+                                                          double* __restrict__ rzp, int ncols, int cpb) {
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    const int m = rv.m;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < rv.n_rows; i += (int64_t)gridDim.y * rows) {
+        const int64_t idx = i * ncols + col;
+        T v = r[idx];
+        if (m > 0) {
+            const int32_t sidx = rv.sup_of_row[i];
+            if (sidx >= 0) {
+                double corr = 0.0;
+                for (int k = 0; k < m; ++k)
+                    corr += rv.sup_coef[(int64_t)sidx * m + k] * cs.mu[(int64_t)k * ncols + col];
+                v = (T)((double)v - corr);
+                r[idx] = v;
+            }
+        }
+        acc += (double)v * (double)(inv_diag(rv, i, col, ncols) * v);
+    }
+    double accs[1] = {acc};
+    block_column_reduce<1>(accs, rzp, ncols, cpb, col);
+}
+
+template <typename T>
+void launch_project_residual(const RowView<T>& rv, T* r, ColState cs, double* rz_partial, const Launch& L) {
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+    k_project_residual<T><<<grid, block, 0, L.stream>>>(rv, r, cs, rz_partial, L.ncols, L.cpb);
+}
+template void launch_project_residual<double>(const RowView<double>&, double*, ColState, double*,
+                                              const Launch&);
+
 // p = M^-1 (r - C^T mu) + beta p ; q = 0
 template <typename T>
-__global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, const T* __restrict__ r,
+__global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, T* __restrict__ r,
                                                  T* __restrict__ p, T* __restrict__ q, ColState cs,
                                                  int ncols, int cpb, int first) {
     const int rows = blockDim.x / cpb;
@@ -707,7 +753,10 @@ __global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, const T* __restr
     for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < rv.n_rows; i += (int64_t)gridDim.y * rows) {
         const int64_t idx = i * ncols + col;
         q[idx] = T(0);
-        if (!act) continue;
+        if (!act) {
+            if (first) p[idx] = T(0);
+            continue;
+        }
         T rr_ = r[idx];
         if (m > 0) {
             const int32_t s = rv.sup_of_row[i];
@@ -715,6 +764,7 @@ __global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, const T* __restr
                 double corr = 0.0;
                 for (int k = 0; k < m; ++k) corr += rv.sup_coef[(int64_t)s * m + k] * cs.mu[(int64_t)k * ncols + col];
                 rr_ = (T)((double)rr_ - corr);
+                r[idx] = rr_;   // residual reset: keeps r in the projected space
             }
         }
         const T z = inv_diag(rv, i, col, ncols) * rr_;
@@ -723,15 +773,15 @@ __global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, const T* __restr
 }
 
 template <typename T>
-void launch_pupdate(const RowView<T>& rv, const T* r, T* p, T* q, ColState cs, bool first,
+void launch_pupdate(const RowView<T>& rv, T* r, T* p, T* q, ColState cs, bool first,
                     const Launch& L) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
     k_pupdate<T><<<grid, block, 0, L.stream>>>(rv, r, p, q, cs, L.ncols, L.cpb, first ? 1 : 0);
 }
-template void launch_pupdate<float>(const RowView<float>&, const float*, float*, float*, ColState,
-                                    bool, const Launch&);
-template void launch_pupdate<double>(const RowView<double>&, const double*, double*, double*,
-                                     ColState, bool, const Launch&);
+template void launch_pupdate<float>(const RowView<float>&, float*, float*, float*, ColState, bool,
+                                    const Launch&);
+template void launch_pupdate<double>(const RowView<double>&, double*, double*, double*, ColState,
+                                     bool, const Launch&);
 
 // S = C M^-1 C^T per column (one block per (column, row k)), then Cholesky.
 template <typename T>

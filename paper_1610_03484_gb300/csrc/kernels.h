@@ -102,8 +102,12 @@ void launch_constraint_dot(const RowView<T>& rv, const T* r, double* c_partial, 
 void launch_finalize_beta(int m, const double* rz_partial, const double* c_partial, ColState cs,
                           bool first, const Launch& L);
 template <typename T>
-void launch_pupdate(const RowView<T>& rv, const T* r, T* p, T* q, ColState cs, bool first,
+void launch_pupdate(const RowView<T>& rv, T* r, T* p, T* q, ColState cs, bool first,
                     const Launch& L);
+void launch_constraint_multipliers(int m, const double* c_partial, ColState cs, const Launch& L);
+template <typename T>
+void launch_project_residual(const RowView<T>& rv, T* r, ColState cs, double* rz_partial,
+                             const Launch& L);
 template <typename T>
 void launch_schur(const RowView<T>& rv, ColState cs, const Launch& L);
 

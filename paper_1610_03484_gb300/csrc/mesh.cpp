@@ -115,9 +115,26 @@ int build_dofmap(const double* xyz, int64_t nv, const int32_t* tets, int64_t nt,
             out.lverts[4 * t + a] = s[a].second;
         }
     }
-    // ---- edges and faces on folded ids
+    // ---- edges and faces
+    // Without folding an edge (face) is identified by its sorted vertex ids.
+    // With the periodic fold two different edges of the torus can join the
+    // same pair of folded vertices (a box only two cells thick), so entities
+    // are identified by their midpoint / centroid folded into the box instead.
     static const int EL[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
     static const int FL[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+    const double qpos = 1.0 / (1e-7 * L);
+    auto folded_key = [&](const int32_t* vs, int n) {
+        std::array<int64_t, 3> k;
+        for (int a = 0; a < 3; ++a) {
+            double c = 0;
+            for (int i = 0; i < n; ++i) c += xyz[3 * (int64_t)vs[i] + a];
+            c = c / n - lo[a];
+            const double span = hi[a] - lo[a];
+            if (c >= span - tol) c -= span;
+            k[a] = (int64_t)std::llround(c * qpos);
+        }
+        return k;
+    };
     std::unordered_map<std::array<int64_t, 3>, int64_t, Key3Hash> emap, fmap;
     emap.reserve(nt * 2);
     fmap.reserve(nt * 3);
@@ -127,17 +144,27 @@ int build_dofmap(const double* xyz, int64_t nv, const int32_t* tets, int64_t nt,
     for (int64_t t = 0; t < nt; ++t) {
         for (int e = 0; e < 6; ++e) {
             std::array<int64_t, 3> k{g[4 * t + EL[e][0]], g[4 * t + EL[e][1]], -1};
+            if (periodic) {
+                const int32_t vs[2] = {out.lverts[4 * t + EL[e][0]], out.lverts[4 * t + EL[e][1]]};
+                k = folded_key(vs, 2);
+            }
             auto it = emap.find(k);
             if (it == emap.end()) it = emap.emplace(k, (int64_t)emap.size()).first;
             tedge[6 * t + e] = it->second;
         }
         for (int f = 0; f < 4; ++f) {
             std::array<int64_t, 3> k{g[4 * t + FL[f][0]], g[4 * t + FL[f][1]], g[4 * t + FL[f][2]]};
+            const std::array<int64_t, 3> kv = k;
+            if (periodic) {
+                const int32_t vs[3] = {out.lverts[4 * t + FL[f][0]], out.lverts[4 * t + FL[f][1]],
+                                       out.lverts[4 * t + FL[f][2]]};
+                k = folded_key(vs, 3);
+            }
             auto it = fmap.find(k);
             if (it == fmap.end()) {
                 it = fmap.emplace(k, (int64_t)fmap.size()).first;
                 fcount.push_back(0);
-                fverts.push_back(k);
+                fverts.push_back(kv);
             }
             fcount[it->second]++;
             tface[4 * t + f] = it->second;
