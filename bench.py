@@ -38,6 +38,11 @@ WORKLOAD = ("batched FE2 evaluation: 4096 macro Gauss points per GPU, plain-weav
             "per RVE (6 mech + 3 thermal + 3 moisture), degradation state per point from the "
             "Sec. 4 law, FP32 operator + FP64 reductions/refinement, tensors to 1e-6")
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+RTOL = 1e-8          # FP64 outer (true-residual) tolerance of every cell solve
+INNER_RTOL = 1e-5    # FP32 inner PCG tolerance per refinement sweep
+# dram read + write bytes per operator launch from the ncu capture in profiles/ (None until
+# the kernel's current version has been captured)
+TRAFFIC_PER_LAUNCH = None
 
 
 def parse():
@@ -162,29 +167,14 @@ def mesh_ids(size, p, classes):
     return np.array([lut[(int(s), int(q))] for s, q in zip(size, p)], np.int32)
 
 
-def operator_bytes_per_unit(classes, meshes):
-    """Algorithmic bytes of one operator launch per RVE column group:
-    x read + y written (n_rows * 6 * 4 B each) + element data once per launch."""
-    out = {}
-    for (si, p), m in zip(classes, meshes):
-        info = m.info()
-        N = info["n_scalar_dofs"]
-        nt = info["n_tets"]
-        ne = {1: 4, 2: 10, 3: 20}[p]
-        out[(si, p)] = {"mech_rows": 3 * N, "scal_rows": N, "nt": nt,
-                        "elem_bytes_mech": nt * (4 * ne + 4 * 10 + 4 * 21 + 1),
-                        "elem_bytes_scal": nt * (4 * ne + 4 * 10 + 4 * 12 + 1)}
-    return out
-
-
 def run_ours(args, world, rank, local):
     import torch
     import paper_1610_03484_gb300 as rve
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    ctx = rve.Context(precision=rve.PREC_MIXED, rtol=1e-8, inner_rtol=1e-5, max_refine=4,
-                      batch=args.batch, stream=stream.cuda_stream, device=local)
+    ctx = rve.Context(precision=rve.PREC_MIXED, rtol=RTOL, inner_rtol=INNER_RTOL, max_refine=4,
+                      batch=args.batch, stream=stream.cuda_stream, device=local, profile=True)
     meshes, classes = build_meshes(ctx, rve)
     G = args.points
     T, c, t, size, p = ri.gauss_point_states(G, SEED + rank)
@@ -209,7 +199,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     launches = 0
-    op_ms, op_n = 0.0, 0
+    op_ms, op_n, op_bytes, op_flops = 0.0, 0, 0.0, 0.0
     times = []
     barrier(world)
     torch.cuda.synchronize()
@@ -226,6 +216,8 @@ def run_ours(args, world, rank, local):
         launches += st["kernel_launches"]
         op_ms += st["op_ms"]
         op_n += st["op_launches"]
+        op_bytes += st["op_bytes"]
+        op_flops += st["op_flops"]
     barrier(world)
     clk = clocks.stop()
     status = Sd.cpu().numpy()
@@ -255,7 +247,8 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": job_s * 1000.0 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points_per_gpu": G, "seed": SEED, "bc": "periodic",
-                   "precision": "FP32 operator, FP64 reductions + refinement", "rtol": 1e-8,
+                   "precision": "FP32 operator, FP64 reductions + refinement", "rtol": RTOL,
+                   "inner_rtol": INNER_RTOL,
                    "l2": "256 MB buffer written between timed steps; per-step working set >> 129 MB L2",
                    "status_ok": int((status == 0).sum())},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": G * 3 * 8,
@@ -266,13 +259,38 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": None,
     }
     if op_n > 0:
-        result["roofline"] = {"kernel": "k_operator", "op_ms_total": op_ms, "launches": op_n}
+        result["roofline"] = roofline(op_ms, op_n, op_bytes, op_flops, pk, pk_kind, clk)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_baseline(budget_s=20.0)
     for m in meshes:
         m.free()
     ctx.close()
     return result
+
+
+def roofline(op_ms, op_n, op_bytes, op_flops, pk, pk_kind, clk):
+    """Roofline of the dominant kernel (the matrix-free operator) over every
+    launch in the timed region: algorithmic bytes and flops per launch divided
+    by the mean CUDA-event duration of a launch."""
+    t = op_ms / 1e3 / op_n
+    gbs = op_bytes / op_n / t / 1e9
+    tfs = op_flops / op_n / t / 1e12
+    hbm_peak = pk["hbm_gbs"]
+    mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12      # FP32 CUDA-core FMA peak at the sampled clock
+    hbm_frac, alu_frac = gbs / hbm_peak, tfs / fp32_peak
+    out = {"kernel": "k_operator (all classes, FP32 inner solves)", "launches": op_n,
+           "mean_launch_ms": t * 1e3, "traffic": TRAFFIC_PER_LAUNCH,
+           "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                   "peak_kind": f"{pk_kind} (MEASURED_PEAKS.json copy bandwidth)"},
+           "alu": {"achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu_frac,
+                   "peak_kind": f"derived: 152 SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled median)"},
+           "bytes_per_launch": op_bytes / op_n, "flops_per_launch": op_flops / op_n}
+    if alu_frac >= hbm_frac:
+        out.update({"bound": "alu", "achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu_frac})
+    else:
+        out.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac})
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle

@@ -74,6 +74,7 @@ typedef struct rve_options {
     int     check_every;     /* iterations between host convergence checks (default 16) */
     int     batch;           /* RVEs solved together in macro_update_gauss_points, 0 = auto */
     void*   stream;          /* cudaStream_t to run on; NULL = library-created stream */
+    int     profile;         /* 1: time every operator launch with CUDA events (rve_stats.op_*) */
 } rve_options;
 
 /* Isotropic matrix phase (Sec. 1, Sec. 7). */
@@ -124,6 +125,9 @@ typedef struct rve_stats {
     int64_t kernel_launches;      /* device kernels launched by the call */
     double  op_ms;                /* summed device time of operator launches (profile mode) */
     int64_t op_launches;          /* operator launches counted in op_ms */
+    double  op_bytes;             /* algorithmic bytes of those launches: x read + y written
+                                     (2 n_rows ncols sizeof(real)) + element data once */
+    double  op_flops;             /* algorithmic flops of those launches (FMA = 2) */
 } rve_stats;
 
 /* ------------------------------------------------------------------ calls */

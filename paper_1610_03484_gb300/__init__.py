@@ -35,7 +35,7 @@ class RveError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_iter", C.c_int), ("inner_rtol", C.c_double), ("max_refine", C.c_int),
-                ("check_every", C.c_int), ("batch", C.c_int), ("stream", C.c_void_p)]
+                ("check_every", C.c_int), ("batch", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int)]
 
 
 class MatrixProps(C.Structure):
@@ -63,7 +63,7 @@ class Stats(C.Structure):
                 ("rel_residual_mech", C.c_double), ("rel_residual_scalar", C.c_double),
                 ("hill_mandel_mech", C.c_double), ("hill_mandel_scalar", C.c_double),
                 ("seconds", C.c_double), ("kernel_launches", C.c_int64), ("op_ms", C.c_double),
-                ("op_launches", C.c_int64)]
+                ("op_launches", C.c_int64), ("op_bytes", C.c_double), ("op_flops", C.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -155,12 +155,13 @@ class Context:
     """One librve context (device + stream).  Use as a context manager."""
 
     def __init__(self, precision=PREC_FP64, rtol=1e-10, max_iter=20000, inner_rtol=1e-6,
-                 max_refine=4, check_every=16, batch=0, stream=None, device=0):
+                 max_refine=4, check_every=16, batch=0, stream=None, device=0, profile=False):
         lib = load_library()
         o = default_options()
         o.device, o.precision, o.rtol, o.max_iter = device, precision, rtol, max_iter
         o.inner_rtol, o.max_refine, o.check_every, o.batch = inner_rtol, max_refine, check_every, batch
         o.stream = stream
+        o.profile = int(profile)
         h = C.c_void_p()
         _check(lib.rve_create(C.byref(h), C.byref(o)), "rve_create")
         self.h = h

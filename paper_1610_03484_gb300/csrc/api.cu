@@ -88,9 +88,18 @@ using namespace rve;
 struct rve_ctx_s {
     rve_options opt;
     cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;   // private stream used only to capture graphs
     bool own_stream = false;
     int device = 0;
     int64_t launches = 0;
+    // profile mode: event pairs around every operator launch of a captured body
+    std::vector<cudaEvent_t> ev;
+    double op_ms = 0;
+    int64_t op_launches = 0;
+    double op_bytes = 0, op_flops = 0;
+    ~rve_ctx_s() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
 };
 
 struct rve_mesh_s {
@@ -449,20 +458,71 @@ struct Solver {
         std::vector<int32_t> act(ncols);
         int it = 0;
         conv = false;
-        while (it < max_iter) {
-            for (int k = 0; k < check && it < max_iter; ++k, ++it) {
-                launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), L);
-                launch_finalize_alpha<T>(m->epart.as<double>(), cs, L);
-                launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, L);
-                launch_constraint_dot<T>(rvw, r, m->cpart.as<double>(), L);
-                launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, L);
-                launch_pupdate<T>(rvw, r, p, q, cs, false, L);
-                *launches += f.m > 0 ? 6 : 5;
+        // `check` iterations are captured once into a CUDA graph (on the private
+        // capture stream) and replayed on the context stream until every column
+        // has converged; the host reads the convergence flags between replays.
+        const bool prof = m->ctx->opt.profile != 0;
+        if (prof && (int)m->ctx->ev.size() < 2 * check) {
+            for (int k = (int)m->ctx->ev.size(); k < 2 * check; ++k) {
+                cudaEvent_t e;
+                RVE_CUDA(cudaEventCreate(&e));
+                m->ctx->ev.push_back(e);
             }
+        }
+        auto body = [&](const Launch& Lx) {
+            for (int k = 0; k < check; ++k) {
+                if (prof) cudaEventRecord(m->ctx->ev[2 * k], Lx.stream);
+                launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active);
+                if (prof) cudaEventRecord(m->ctx->ev[2 * k + 1], Lx.stream);
+                launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
+                launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx);
+                launch_constraint_dot<T>(rvw, r, m->cpart.as<double>(), Lx);
+                launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, Lx);
+                launch_pupdate<T>(rvw, r, p, q, cs, false, Lx);
+            }
+        };
+        cudaGraphExec_t exec = nullptr;
+        {
+            Launch Lc = L;
+            Lc.stream = m->ctx->capture;
+            cudaGraph_t graph = nullptr;
+            RVE_CUDA(cudaStreamBeginCapture(Lc.stream, cudaStreamCaptureModeThreadLocal));
+            body(Lc);
+            RVE_CUDA(cudaStreamEndCapture(Lc.stream, &graph));
+            cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            RVE_CUDA(ge);
+        }
+        struct ExecGuard {
+            cudaGraphExec_t e;
+            ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+        } guard{exec};
+        while (it < max_iter) {
+            RVE_CUDA(cudaGraphLaunch(exec, s));
+            it += check;
+            *launches += (int64_t)check * (f.m > 0 ? 6 : 5);
             RVE_CUDA(cudaGetLastError());
             RVE_CUDA(cudaMemcpyAsync(act.data(), cs.active, sizeof(int32_t) * ncols,
                                      cudaMemcpyDeviceToHost, s));
             RVE_CUDA(cudaStreamSynchronize(s));
+            if (prof) {
+                // algorithmic bytes / flops of one operator launch of this solve
+                const int ne = n_local(m->p), nmod = n_modes(m->p), nc = f.nc;
+                const double sz = sizeof(T);
+                const double bytes = 2.0 * n_rows * ncols * sz +
+                                     (double)m->nt * (4.0 * ne + 10 * sz + (nc == 3 ? 21 : 6) * sz + 1);
+                const double fma = 2.0 * (ne - 4) * nmod * 3 * nc + nmod * (18.0 * nc + (nc == 3 ? 36 : 9));
+                const double flops = 2.0 * fma * (double)m->nt * ncols;
+                for (int k = 0; k < check; ++k) {
+                    float ms = 0;
+                    if (cudaEventElapsedTime(&ms, m->ctx->ev[2 * k], m->ctx->ev[2 * k + 1]) == cudaSuccess) {
+                        m->ctx->op_ms += ms;
+                        m->ctx->op_launches++;
+                        m->ctx->op_bytes += bytes;
+                        m->ctx->op_flops += flops;
+                    }
+                }
+            }
             bool any = false;
             for (int c = 0; c < ncols; ++c) any |= act[c] != 0;
             if (!any) {
@@ -703,6 +763,7 @@ void rve_default_options(rve_options* o) {
     o->check_every = 16;
     o->batch = 0;
     o->stream = nullptr;
+    o->profile = 0;
 }
 
 int rve_create(rve_ctx* out, const rve_options* opts) {
@@ -745,6 +806,12 @@ int rve_create(rve_ctx* out, const rve_options* opts) {
         }
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        set_error("cudaStreamCreate failed");
+        return RVE_ERR_CUDA;
+    }
     upload_basis_tables();
     if (cudaGetLastError() != cudaSuccess) {
         if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -761,6 +828,7 @@ int rve_destroy(rve_ctx c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     if (c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->capture) cudaStreamDestroy(c->capture);
     delete c;
     return RVE_OK;
 }
@@ -960,11 +1028,17 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
     RVE_CUDA(cudaMemcpyAsync(d + 2, th, 8, cudaMemcpyHostToDevice, s));
     launch_degradation(1, d, d + 1, d + 2, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, d + 3, s);
     c->launches++;
+    const double op0 = c->op_ms, ob0 = c->op_bytes, of0 = c->op_flops;
+    const int64_t on0 = c->op_launches;
     int rc = homogenise_batch(m, 1, d + 3, C, K, D, st);
     RVE_CUDA(cudaStreamSynchronize(s));
     if (st) {
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st->kernel_launches = c->launches - l0;
+        st->op_ms = c->op_ms - op0;
+        st->op_launches = c->op_launches - on0;
+        st->op_bytes = c->op_bytes - ob0;
+        st->op_flops = c->op_flops - of0;
     }
     return rc;
 }
@@ -1047,12 +1121,18 @@ int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshe
         std::memset(st, 0, sizeof(*st));
         st->converged = 1;
     }
+    const double op0 = c->op_ms, ob0 = c->op_bytes, of0 = c->op_flops;
+    const int64_t on0 = c->op_launches;
     int rc = macro_update_impl(c, meshes, n_meshes, G, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev,
                                D_dev, status_dev, st);
     if (st) {
         cudaStreamSynchronize(c->stream);
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st->kernel_launches = c->launches - l0;
+        st->op_ms = c->op_ms - op0;
+        st->op_launches = c->op_launches - on0;
+        st->op_bytes = c->op_bytes - ob0;
+        st->op_flops = c->op_flops - of0;
     }
     return rc;
 }

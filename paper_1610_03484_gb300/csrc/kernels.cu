@@ -91,9 +91,10 @@ __device__ __forceinline__ void block_column_reduce(const double (&acc)[NACC], d
 // the unit macro strain / gradient of the column is added to the constant mode,
 // so -y is the fluctuation problem's residual b - K x.
 template <int P, int NC, typename T, bool MACRO>
-__global__ void __launch_bounds__(256) k_operator(ElemView<T> ev, const T* __restrict__ x,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_operator(ElemView<T> ev, const T* __restrict__ x,
                                                   T* __restrict__ y, double* __restrict__ epart,
-                                                  int ncols, int cpb) {
+                                                  const int32_t* __restrict__ active, int ncols,
+                                                  int cpb) {
     constexpr int NE = Order<P>::NE;
     constexpr int NM = Order<P>::NM;
     const int rows = blockDim.x / cpb;
@@ -102,129 +103,135 @@ __global__ void __launch_bounds__(256) k_operator(ElemView<T> ev, const T* __res
     const int field = (col % 6) >= 3 ? 1 : 0;   // scalar solve: thermal / moisture
     const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
     double energy = 0.0;
+    // converged columns skip the element loop (their step length is zero)
+    const int64_t e_end = (active && !active[col]) ? 0 : ev.nt;
 
-    for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < ev.nt; e += (int64_t)gridDim.y * rows) {
-        int dof[NE];
+    for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < e_end; e += (int64_t)gridDim.y * rows) {
+        const int32_t* ed = ev.edofs + e * NE;
+        // ---- forward: reference-gradient modes V[m][k][c] = sum_j A[k][m][j] x_j,c.
+        // Each gathered value is used for every mode at once and then dropped.
+        T V[NM][3][NC];
+        {
+            const int d0 = __ldg(ed);
+            T x0[NC];
 #pragma unroll
-        for (int j = 0; j < NE; ++j) dof[j] = __ldg(ev.edofs + e * NE + j);
-        T G[9];
+            for (int c = 0; c < NC; ++c) x0[c] = x[((int64_t)d0 * NC + c) * ncols + col];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) G[i] = __ldg(ev.geo + e * 10 + i);
-        const T vol = __ldg(ev.geo + e * 10 + 9);
-        const T s = __ldg(ev.scale + col * 2 + __ldg(ev.phase + e));
-        constexpr int NMAT = NC == 3 ? 21 : 6;
-        T Dm[NMAT];
+            for (int k = 0; k < 3; ++k) {
+                const int dk = __ldg(ed + k + 1);
 #pragma unroll
-        for (int i = 0; i < NMAT; ++i)
-            Dm[i] = s * __ldg(ev.mat + e * (NC == 3 ? 21 : 12) + (NC == 3 ? 0 : 6 * field) + i);
-
-        T xv[NE][NC];
+                for (int c = 0; c < NC; ++c) V[0][k][c] = x[((int64_t)dk * NC + c) * ncols + col] - x0[c];
+            }
 #pragma unroll
-        for (int j = 0; j < NE; ++j)
+            for (int m = 1; m < NM; ++m)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) xv[j][c] = x[((int64_t)dof[j] * NC + c) * ncols + col];
-        T yv[NE][NC];
+                for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int j = 0; j < NE; ++j)
+                    for (int c = 0; c < NC; ++c) V[m][k][c] = T(0);
+        }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) yv[j][c] = T(0);
-
+        for (int j = 4; j < NE; ++j) {
+            const int dj = __ldg(ed + j);
+            T xj[NC];
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            // reference gradient mode m: V[k][c] = d u_c / d xi_k
-            T V[3][NC];
+            for (int c = 0; c < NC; ++c) xj[c] = x[((int64_t)dj * NC + c) * ncols + col];
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) V[k][c] = (m == 0) ? (xv[k + 1][c] - xv[0][c]) : T(0);
-#pragma unroll
-            for (int j = 4; j < NE; ++j)
+            for (int m = 0; m < NM; ++m)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const T a = Tab<T>::a(P, (k * NM + m) * NE + j);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) V[k][c] = fma(a, xv[j][c], V[k][c]);
+                    for (int c = 0; c < NC; ++c) V[m][k][c] = fma(a, xj[c], V[m][k][c]);
                 }
-            // physical gradient H[c][l] = sum_k V[k][c] Jinv[k][l]
+        }
+        // ---- element data; s * |T| folded into the material
+        T G[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) G[i] = __ldg(ev.geo + e * 10 + i);
+        const T sv = __ldg(ev.scale + col * 2 + __ldg(ev.phase + e)) * __ldg(ev.geo + e * 10 + 9);
+        constexpr int NMAT = NC == 3 ? 21 : 6;
+        T Dm[NMAT];
+#pragma unroll
+        for (int i = 0; i < NMAT; ++i)
+            Dm[i] = sv * __ldg(ev.mat + e * (NC == 3 ? 21 : 12) + (NC == 3 ? 0 : 6 * field) + i);
+        // ---- per mode: gradient -> stress/flux -> W = J^-1 S, overwriting V
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
             T H[NC][3];
 #pragma unroll
             for (int c = 0; c < NC; ++c)
 #pragma unroll
                 for (int l = 0; l < 3; ++l)
-                    H[c][l] = V[0][c] * G[l] + V[1][c] * G[3 + l] + V[2][c] * G[6 + l];
+                    H[c][l] = V[m][0][c] * G[l] + V[m][1][c] * G[3 + l] + V[m][2][c] * G[6 + l];
             if (MACRO && m == 0) {
-                if (NC == 3) {
+                if constexpr (NC == 3) {
                     if (macro_id < 3) {
-                        H[macro_id % NC][macro_id] += T(1);
+                        H[macro_id][macro_id] += T(1);
                     } else {
                         const int a = macro_id == 3 ? 0 : (macro_id == 4 ? 1 : 2);
                         const int b = macro_id == 3 ? 1 : (macro_id == 4 ? 2 : 0);
-                        H[a % NC][b] += T(0.5);
-                        H[b % NC][a] += T(0.5);
+                        H[a][b] += T(0.5);
+                        H[b][a] += T(0.5);
                     }
                 } else {
                     H[0][macro_id] += T(1);
                 }
             }
-            // stress / flux S[c][l]
             T S[NC][3];
-            if (NC == 3) {
-                T ev6[6] = {H[0][0], H[1 % NC][1], H[2 % NC][2], H[0][1] + H[1 % NC][0],
-                            H[1 % NC][2] + H[2 % NC][1], H[2 % NC][0] + H[0][2]};
+            if constexpr (NC == 3) {
+                const T ev6[6] = {H[0][0], H[1][1], H[2][2], H[0][1] + H[1][0], H[1][2] + H[2][1],
+                                  H[2][0] + H[0][2]};
                 T sg[6];
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
                     T t = T(0);
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) t = fma(Dm[ut6(i, j)], ev6[j], t);
+                    for (int jj = 0; jj < 6; ++jj) t = fma(Dm[ut6(i, jj)], ev6[jj], t);
                     sg[i] = t;
                 }
-                S[0][0] = sg[0];
-                S[0][1] = sg[3];
-                S[0][2] = sg[5];
-                S[1 % NC][0] = sg[3];
-                S[1 % NC][1] = sg[1];
-                S[1 % NC][2] = sg[4];
-                S[2 % NC][0] = sg[5];
-                S[2 % NC][1] = sg[4];
-                S[2 % NC][2] = sg[2];
+                S[0][0] = sg[0]; S[0][1] = sg[3]; S[0][2] = sg[5];
+                S[1][0] = sg[3]; S[1][1] = sg[1]; S[1][2] = sg[4];
+                S[2][0] = sg[5]; S[2][1] = sg[4]; S[2][2] = sg[2];
             } else {
 #pragma unroll
                 for (int l = 0; l < 3; ++l)
                     S[0][l] = Dm[s3(l, 0)] * H[0][0] + Dm[s3(l, 1)] * H[0][1] + Dm[s3(l, 2)] * H[0][2];
             }
-            // W[k][c] = |T| sum_l Jinv[k][l] S[c][l]
-            T W[3][NC];
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    W[k][c] = vol * (G[3 * k] * S[c][0] + G[3 * k + 1] * S[c][1] + G[3 * k + 2] * S[c][2]);
-            if (m == 0) {
-#pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    yv[0][c] -= W[0][c] + W[1][c] + W[2][c];
-                    yv[1][c] += W[0][c];
-                    yv[2][c] += W[1][c];
-                    yv[3][c] += W[2][c];
+                    const T w = G[3 * k] * S[c][0] + G[3 * k + 1] * S[c][1] + G[3 * k + 2] * S[c][2];
+                    if (epart && !MACRO) energy += (double)V[m][k][c] * (double)w;   // x.Kx = sum V.W
+                    V[m][k][c] = w;
                 }
-            }
+        }
+        // ---- backward and scatter: y_j,c = sum_m sum_k A[k][m][j] W[m][k][c]
 #pragma unroll
-            for (int j = 4; j < NE; ++j)
+        for (int c = 0; c < NC; ++c) {
+            const T w0 = V[0][0][c], w1 = V[0][1][c], w2 = V[0][2][c];
+            atomicAdd(y + ((int64_t)__ldg(ed) * NC + c) * ncols + col, -(w0 + w1 + w2));
+            atomicAdd(y + ((int64_t)__ldg(ed + 1) * NC + c) * ncols + col, w0);
+            atomicAdd(y + ((int64_t)__ldg(ed + 2) * NC + c) * ncols + col, w1);
+            atomicAdd(y + ((int64_t)__ldg(ed + 3) * NC + c) * ncols + col, w2);
+        }
+#pragma unroll
+        for (int j = 4; j < NE; ++j) {
+            T yj[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) yj[c] = T(0);
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const T a = Tab<T>::a(P, (k * NM + m) * NE + j);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) yv[j][c] = fma(a, W[k][c], yv[j][c]);
+                    for (int c = 0; c < NC; ++c) yj[c] = fma(a, V[m][k][c], yj[c]);
                 }
+            const int dj = __ldg(ed + j);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) atomicAdd(y + ((int64_t)dj * NC + c) * ncols + col, yj[c]);
         }
-#pragma unroll
-        for (int j = 0; j < NE; ++j)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                atomicAdd(y + ((int64_t)dof[j] * NC + c) * ncols + col, yv[j][c]);
-                if (epart) energy += (double)xv[j][c] * (double)yv[j][c];
-            }
     }
     if (epart) {
         double acc[1] = {energy};
@@ -234,12 +241,12 @@ __global__ void __launch_bounds__(256) k_operator(ElemView<T> ev, const T* __res
 
 template <typename T>
 void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
-                     double* energy_partial, const Launch& L) {
+                     double* energy_partial, const Launch& L, const int32_t* active) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
 #define RVE_OP_CASE(PP, NCC, MM)                                                                \
     if (p == PP && nc == NCC && macro == MM) {                                                  \
         k_operator<PP, NCC, T, MM><<<grid, block, 0, L.stream>>>(ev, x, y, energy_partial,      \
-                                                                 L.ncols, L.cpb);              \
+                                                                 active, L.ncols, L.cpb);      \
         return;                                                                                 \
     }
     RVE_OP_CASE(1, 3, false) RVE_OP_CASE(2, 3, false) RVE_OP_CASE(3, 3, false)
@@ -249,9 +256,9 @@ void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* 
 #undef RVE_OP_CASE
 }
 template void launch_operator<float>(int, int, bool, const ElemView<float>&, const float*, float*,
-                                     double*, const Launch&);
+                                     double*, const Launch&, const int32_t*);
 template void launch_operator<double>(int, int, bool, const ElemView<double>&, const double*,
-                                      double*, double*, const Launch&);
+                                      double*, double*, const Launch&, const int32_t*);
 
 // ------------------------------------------------------ Jacobi diagonal (K6)
 // diag[field][phase][row] = unscaled diagonal of K restricted to one phase.
@@ -570,7 +577,9 @@ __global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x
     const int col = blockIdx.x * cpb + cl;
     const T a = apply ? (T)cs.alpha[col] : T(0);
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < rv.n_rows; i += (int64_t)gridDim.y * rows) {
+    // a converged column keeps x and r; its partial stays zero
+    const int64_t i_end = (apply && !cs.active[col]) ? 0 : rv.n_rows;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += (int64_t)gridDim.y * rows) {
         const int64_t idx = i * ncols + col;
         T rv_ = r[idx];
         if (a != T(0)) {
@@ -750,11 +759,14 @@ __global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, T* __restrict__ 
     const bool act = cs.active[col] != 0;
     const T beta = first ? T(0) : (T)cs.beta[col];
     const int m = rv.m;
-    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < rv.n_rows; i += (int64_t)gridDim.y * rows) {
+    // converged columns are left alone (the operator and update skip them too),
+    // except on the first pass, which clears p and q of columns with b = 0
+    const int64_t i_end = (!act && !first) ? 0 : rv.n_rows;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += (int64_t)gridDim.y * rows) {
         const int64_t idx = i * ncols + col;
         q[idx] = T(0);
         if (!act) {
-            if (first) p[idx] = T(0);
+            p[idx] = T(0);
             continue;
         }
         T rr_ = r[idx];

@@ -64,9 +64,10 @@ struct ColState {
 void upload_basis_tables();
 
 // y += K x (+ macro load when macro != 0); energy partials x.Kx per column.
+// active (optional, [ncols]): columns with active == 0 are skipped.
 template <typename T>
 void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
-                     double* energy_partial, const Launch& L);
+                     double* energy_partial, const Launch& L, const int32_t* active = nullptr);
 
 template <typename T>
 void launch_diag(int p, int nc, int64_t n_rows, const ElemView<T>& ev, T* diag, cudaStream_t s);
