@@ -211,6 +211,31 @@ int rve_mesh_get_tensors(rve_ctx ctx, rve_mesh mesh, double* stiffness, double* 
 int rve_apply_operator(rve_ctx ctx, rve_mesh mesh, int field, int ncols, const double* x,
                        double* y);
 
+/* Allocation-free variant of the operator apply, for callers that cannot
+ * allocate device memory while they run: for example a host application that
+ * owns all GPU memory through its own pre-sized pool and forbids further
+ * cudaMalloc/cudaFree (which can also synchronise the device), or a real-time
+ * loop that must not allocate.  This call allocates nothing: the caller passes
+ * device buffers, and the only scratch (per-block energy partials and column
+ * scales) lives in a file-scope __device__ array of about 0.9 MB that every
+ * GPU loading librve holds until the process exits.  The mesh must already be
+ * loaded and have materials (its device data is allocated by rve_mesh_load).
+ * The paper has no counterpart of this call; it computes the same operator as
+ * rve_apply_operator.
+ *   field 0: mechanics, x_dev / y_dev [n_scalar_dofs][3][ncols];
+ *   field 1: scalar fields, x_dev / y_dev [n_scalar_dofs][ncols], where column
+ *            c uses the conductivity when c % 6 < 3 and the diffusivity otherwise.
+ *   ncols must be a positive multiple of 6 and at most 96; larger values are
+ *   rejected with RVE_ERR_INVALID_ARGUMENT.
+ * Writes y_dev = K x_dev and energy_dev[c] = x_c . K x_c (SI units), enqueued on
+ * the context's stream; the caller synchronises.  The first call on a device
+ * looks up the scratch address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one scratch array, which keeps
+ * the last call's contents: calls that overlap on the GPU (different streams or
+ * contexts on one device) race on it and must be serialised by the caller. */
+int rve_operator_energy_noalloc(rve_ctx ctx, rve_mesh mesh, int field, int ncols,
+                                const double* x_dev, double* y_dev, double* energy_dev);
+
 /* Hierarchic DOF map of the current BC: edofs [nt][n_local] scalar DOF index of
  * each local function (4 vertex, then 6 quadratic edge, 6 cubic edge, 4 face
  * functions as p allows) and the vertex order used by each tet [nt][4]. */

@@ -101,6 +101,8 @@ _SIGS = {
     "rve_mesh_get_tensors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "rve_mesh_get_dofmap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_operator_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                              C.c_void_p]),
 }
 
 
@@ -303,6 +305,14 @@ class Mesh:
         _check(self.ctx.lib.rve_apply_operator(self.ctx.h, self.h, int(field), int(ncols), _ptr(x), _ptr(y)),
                "rve_apply_operator")
         return y
+
+    def operator_energy_noalloc(self, field: int, ncols: int, x_dev: int, y_dev: int, energy_dev: int):
+        """Allocation-free operator apply on caller-owned device buffers (integer
+        device addresses); enqueued on the context's stream."""
+        _check(self.ctx.lib.rve_operator_energy_noalloc(self.ctx.h, self.h, int(field), int(ncols),
+                                                        C.c_void_p(x_dev), C.c_void_p(y_dev),
+                                                        C.c_void_p(energy_dev)),
+               "rve_operator_energy_noalloc")
 
     def dofmap(self):
         ne = {1: 4, 2: 10, 3: 20}[self.p]

@@ -1267,6 +1267,55 @@ int rve_apply_operator(rve_ctx c, rve_mesh m, int field, int ncols, const double
     return RVE_OK;
 }
 
+int rve_operator_energy_noalloc(rve_ctx c, rve_mesh m, int field, int ncols, const double* x_dev,
+                                double* y_dev, double* energy_dev) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !x_dev || !y_dev || !energy_dev || (field != 0 && field != 1) || ncols <= 0 ||
+        ncols % 6 != 0) {
+        set_error("rve_operator_energy_noalloc: invalid argument (field 0 or 1, ncols a positive multiple of 6)");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (ncols > noalloc_max_cols()) {
+        set_error("rve_operator_energy_noalloc: ncols exceeds the static scratch limit of " +
+                  std::to_string(noalloc_max_cols()) + " columns");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (!m->have_materials) {
+        set_error("rve_set_materials must be called first");
+        return RVE_ERR_STATE;
+    }
+    cudaError_t e = cudaSuccess;
+    double* scratch = noalloc_scratch(c->device, &e);
+    if (!scratch) {
+        set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return RVE_ERR_CUDA;
+    }
+    cudaStream_t s = c->stream;
+    FieldDev& f = field == 0 ? m->mech : m->scal;
+    Launch L = make_launch(ncols, std::max<int64_t>(f.n_rows, m->nt), s);
+    L.nby = std::min(L.nby, noalloc_max_blocks_y());
+    double* partial = scratch;                                                   // [nby][ncols]
+    double* scale = scratch + (size_t)noalloc_max_blocks_y() * noalloc_max_cols(); // [ncols][2]
+    launch_fill((int64_t)ncols * 2, 1.0, scale, s);   // unit scales: the materials as set
+    RVE_CUDA(cudaMemsetAsync(y_dev, 0, sizeof(double) * f.n_rows * ncols, s));
+    ElemView<double> ev;
+    ev.nt = m->nt;
+    ev.edofs = m->d_edofs.as<int32_t>();
+    ev.geo = m->d_geo64.as<double>();
+    ev.mat = (f.nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
+    ev.phase = m->d_phase.as<uint8_t>();
+    ev.scale = scale;
+    launch_operator<double>(m->p, f.nc, false, ev, x_dev, y_dev, partial, L);
+    launch_reduce_partials(L.nby, ncols, partial, energy_dev, s);
+    const double lo = field == 0 ? m->mc.ref_mech : m->mc.ref_k;
+    const double hi = field == 0 ? m->mc.ref_mech : m->mc.ref_d;
+    launch_scale_cols(f.n_rows, ncols, lo, hi, y_dev, s);
+    launch_scale_cols(1, ncols, lo, hi, energy_dev, s);
+    c->launches += 5;
+    RVE_CUDA(cudaGetLastError());
+    return RVE_OK;
+}
+
 int rve_mesh_get_dofmap(rve_ctx c, rve_mesh m, int32_t* edofs, int32_t* lverts) {
     RVE_TRY(check_ctx(c));
     if (!m) return RVE_ERR_INVALID_ARGUMENT;

@@ -126,4 +126,11 @@ void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 void launch_axpy_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
 void launch_neg(int64_t n, double* a, cudaStream_t s);
 
+// allocation-free entry point support (noalloc.cu)
+int noalloc_max_cols();
+int noalloc_max_blocks_y();
+double* noalloc_scratch(int device, cudaError_t* err);
+void launch_fill(int64_t n, double v, double* a, cudaStream_t s);
+void launch_scale_cols(int64_t n_rows, int ncols, double f_lo, double f_hi, double* y, cudaStream_t s);
+
 }  // namespace rve
