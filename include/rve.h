@@ -189,6 +189,64 @@ int macro_update_gauss_points_dev(rve_ctx ctx, const rve_mesh* meshes, int n_mes
                                   double* C_dev, double* K_dev, double* D_dev,
                                   int32_t* status_dev, int mode, rve_stats* stats);
 
+/* ------------------------------------------------------- learned surrogate
+ * No counterpart in the paper: an ensemble of MLPs (8 features -> 4 x 256
+ * SiLU -> 33 Cholesky-factor entries of the normalised C, K, D, diagonals
+ * through softplus, so every prediction is SPD), trained on the GPU from
+ * cell solves of this library, BF16 weights and activations with FP32
+ * accumulation on the tensor cores, FP32 master weights and Adam.  The
+ * ensemble spread max_e |T_e - mean| / |mean| decides when a point falls back
+ * to the plain batched PCG. */
+typedef struct rve_surrogate_s* rve_surrogate;
+
+/* Ensemble of `members` (1..16) randomly initialised networks (seeded). */
+int rve_surrogate_create(rve_ctx ctx, int members, uint64_t seed, rve_surrogate* out);
+int rve_surrogate_free(rve_ctx ctx, rve_surrogate s);
+
+/* The 8 features of G macro points on a mesh with materials set: (T, c_wt,
+ * log10 t_h, matrix E (1-omega), yarn E1, E2, G12 (degraded if apply_to_yarn),
+ * matrix k); the degradation factor runs on the device (Sec. 4).  Host arrays,
+ * feat [G][8]. */
+int rve_gauss_point_features(rve_ctx ctx, rve_mesh mesh, int64_t G, const double* T_C,
+                             const double* c_wt, const double* t_h, double* feat);
+
+/* Train every member on n samples (features [n][8], tensors C [n][36], K, D
+ * [n][9], host) for `epochs` epochs of minibatch Adam (batch a multiple of 64,
+ * n >= 64); normalisation is fitted to the data.  loss_history [epochs] may be
+ * NULL. */
+int rve_surrogate_train(rve_ctx ctx, rve_surrogate s, int64_t n, const double* feat,
+                        const double* C, const double* K, const double* D, int epochs, int batch,
+                        double lr, uint64_t seed, double* loss_history);
+
+/* One forward/backward pass of one member on n rows (multiple of 64) without
+ * updating it: target_factors [n][33] are factor entries in the network's
+ * normalised units; grads receives the parameter gradient in the layout of
+ * rve_surrogate_get_params (after its header); loss the mean squared error. */
+int rve_surrogate_gradients(rve_ctx ctx, rve_surrogate s, int member, int n, const double* feat,
+                            const float* target_factors, float* grads, double* loss);
+
+/* Ensemble mean tensors (SI units) and spread for n feature rows (host). */
+int rve_surrogate_predict(rve_ctx ctx, rve_surrogate s, int64_t n, const double* feat, double* C,
+                          double* K, double* D, double* spread);
+
+/* Save / load: a float array [52 + members * n_params] (feature mean and std,
+ * output scales, reference tensor scales, then each member's FP32 weights and
+ * biases layer by layer, weights [in][out]).  With buf NULL, get_params writes
+ * the required length. */
+int rve_surrogate_get_params(rve_ctx ctx, rve_surrogate s, float* buf, int64_t* len);
+int rve_surrogate_set_params(rve_ctx ctx, rve_surrogate s, const float* buf, int64_t len);
+
+/* Batched FE^2 evaluation with the surrogate: points whose ensemble spread is
+ * at most tau take the surrogate's mean tensors (fallback[g] = 0); the others,
+ * and every point of a mesh whose surrogate is NULL, are solved by the plain
+ * batched PCG of macro_update_gauss_points (fallback[g] = 1).  Host arrays. */
+int macro_update_gauss_points_surrogate(rve_ctx ctx, const rve_mesh* meshes,
+                                        const rve_surrogate* surrogates, int n_meshes, double tau,
+                                        int64_t G, const double* T_C, const double* c_wt,
+                                        const double* t_h, const int32_t* mesh_id, double* C,
+                                        double* K, double* D, int32_t* status, uint8_t* fallback,
+                                        rve_stats* stats);
+
 /* ---------------------------------------------------- inspection entry points
  * These expose single steps of the path for parity tests. */
 

@@ -103,6 +103,22 @@ _SIGS = {
     "rve_mesh_get_dofmap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_operator_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                               C.c_void_p]),
+    "rve_surrogate_create": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "rve_surrogate_free": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rve_gauss_point_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p]),
+    "rve_surrogate_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_void_p]),
+    "rve_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.POINTER(C.c_double)]),
+    "rve_surrogate_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]),
+    "rve_surrogate_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
+    "rve_surrogate_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "macro_update_gauss_points_surrogate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                                      C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                      C.POINTER(Stats)]),
 }
 
 
@@ -233,6 +249,33 @@ class Context:
                     "macro_update_gauss_points", allow)
         return Cc, Kk, Dd, st, s.as_dict(), rc
 
+    def features(self, mesh, T_C, c_wt, t_h):
+        T = np.ascontiguousarray(T_C, np.float64)
+        c = np.ascontiguousarray(c_wt, np.float64)
+        t = np.ascontiguousarray(t_h, np.float64)
+        f = np.zeros((len(T), 8))
+        _check(self.lib.rve_gauss_point_features(self.h, mesh.h, len(T), _ptr(T), _ptr(c), _ptr(t), _ptr(f)),
+               "rve_gauss_point_features")
+        return f
+
+    def macro_update_surrogate(self, meshes, surrogates, tau, T_C, c_wt, t_h, mesh_id):
+        G = len(T_C)
+        arr = (C.c_void_p * len(meshes))(*[m.h for m in meshes])
+        sarr = (C.c_void_p * len(meshes))(*[(s.h if s is not None else None) for s in surrogates])
+        T = np.ascontiguousarray(T_C, np.float64)
+        c = np.ascontiguousarray(c_wt, np.float64)
+        t = np.ascontiguousarray(t_h, np.float64)
+        mid = np.ascontiguousarray(mesh_id, np.int32)
+        Cc, Kk, Dd = np.zeros((G, 6, 6)), np.zeros((G, 3, 3)), np.zeros((G, 3, 3))
+        st = np.zeros(G, np.int32)
+        fb = np.zeros(G, np.uint8)
+        s = Stats()
+        rc = _check(self.lib.macro_update_gauss_points_surrogate(self.h, arr, sarr, len(meshes), float(tau), G,
+                                                                 _ptr(T), _ptr(c), _ptr(t), _ptr(mid), _ptr(Cc),
+                                                                 _ptr(Kk), _ptr(Dd), _ptr(st), _ptr(fb), C.byref(s)),
+                    "macro_update_gauss_points_surrogate", (-4,))
+        return Cc, Kk, Dd, st, fb, s.as_dict(), rc
+
     def macro_update_dev(self, meshes, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev, D_dev, status_dev):
         """Device-pointer variant: every *_dev argument is an integer device address."""
         G = len(mesh_id_host)
@@ -246,6 +289,76 @@ class Context:
                                                            MODE_PCG, C.byref(s)),
                     "macro_update_gauss_points_dev", (-4,))
         return s.as_dict(), rc
+
+
+class Surrogate:
+    """Ensemble MLP surrogate (see include/rve.h); training and inference on the GPU."""
+
+    N_OUT = 33
+
+    def __init__(self, ctx: "Context", members=4, seed=0):
+        h = C.c_void_p()
+        _check(ctx.lib.rve_surrogate_create(ctx.h, int(members), int(seed), C.byref(h)), "rve_surrogate_create")
+        self.ctx, self.h, self.members = ctx, h, members
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.rve_surrogate_free(self.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            if self.ctx.h:
+                self.free()
+        except Exception:
+            pass
+
+    def train(self, feat, Cc, Kk, Dd, epochs=100, batch=256, lr=1e-3, seed=0):
+        feat = np.ascontiguousarray(feat, np.float64)
+        Cc = np.ascontiguousarray(Cc, np.float64).reshape(-1, 36)
+        Kk = np.ascontiguousarray(Kk, np.float64).reshape(-1, 9)
+        Dd = np.ascontiguousarray(Dd, np.float64).reshape(-1, 9)
+        hist = np.zeros(epochs)
+        _check(self.ctx.lib.rve_surrogate_train(self.ctx.h, self.h, len(feat), _ptr(feat), _ptr(Cc), _ptr(Kk),
+                                                _ptr(Dd), int(epochs), int(batch), float(lr), int(seed), _ptr(hist)),
+               "rve_surrogate_train")
+        return hist
+
+    def gradients(self, member, feat, target_factors):
+        feat = np.ascontiguousarray(feat, np.float64)
+        tf = np.ascontiguousarray(target_factors, np.float32)
+        n = len(feat)
+        g = np.zeros(self.param_count(), np.float32)
+        loss = C.c_double()
+        _check(self.ctx.lib.rve_surrogate_gradients(self.ctx.h, self.h, int(member), n, _ptr(feat), _ptr(tf),
+                                                    _ptr(g), C.byref(loss)), "rve_surrogate_gradients")
+        return g, loss.value
+
+    def predict(self, feat):
+        feat = np.ascontiguousarray(feat, np.float64)
+        n = len(feat)
+        Cc, Kk, Dd, sp = np.zeros((n, 6, 6)), np.zeros((n, 3, 3)), np.zeros((n, 3, 3)), np.zeros(n)
+        _check(self.ctx.lib.rve_surrogate_predict(self.ctx.h, self.h, n, _ptr(feat), _ptr(Cc), _ptr(Kk), _ptr(Dd),
+                                                  _ptr(sp)), "rve_surrogate_predict")
+        return Cc, Kk, Dd, sp
+
+    def get_params(self) -> np.ndarray:
+        n = C.c_int64()
+        _check(self.ctx.lib.rve_surrogate_get_params(self.ctx.h, self.h, None, C.byref(n)), "rve_surrogate_get_params")
+        buf = np.zeros(n.value, np.float32)
+        _check(self.ctx.lib.rve_surrogate_get_params(self.ctx.h, self.h, _ptr(buf), C.byref(n)),
+               "rve_surrogate_get_params")
+        return buf
+
+    def set_params(self, buf):
+        buf = np.ascontiguousarray(buf, np.float32)
+        _check(self.ctx.lib.rve_surrogate_set_params(self.ctx.h, self.h, _ptr(buf), len(buf)),
+               "rve_surrogate_set_params")
+
+    HEADER = 52
+
+    def param_count(self):
+        return (len(self.get_params()) - self.HEADER) // self.members
 
 
 class Mesh:
@@ -322,5 +435,5 @@ class Mesh:
         return ed, lv
 
 
-__all__ = ["Context", "Mesh", "RveError", "load_library", "exported_symbols", "BC_DIRICHLET", "BC_PERIODIC",
+__all__ = ["Context", "Mesh", "Surrogate", "RveError", "load_library", "exported_symbols", "BC_DIRICHLET", "BC_PERIODIC",
            "BC_NEUMANN", "PREC_FP64", "PREC_MIXED", "Options", "Stats"]

@@ -13,124 +13,19 @@
 #include <string>
 #include <vector>
 
-#include "kernels.h"
-#include "rve_internal.h"
+#include "api_internal.h"
 
 namespace rve {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& s) { g_last_error = s; }
-
-#define RVE_CUDA(call)                                                                   \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess) {                                                         \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
-            return e_ == cudaErrorMemoryAllocation ? RVE_ERR_OUT_OF_MEMORY : RVE_ERR_CUDA; \
-        }                                                                                \
-    } while (0)
-
-#define RVE_TRY(call)          \
-    do {                       \
-        int rc_ = (call);      \
-        if (rc_ != RVE_OK) return rc_; \
-    } while (0)
-
-// ------------------------------------------------------------ device buffer
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    ~DevBuf() { release(); }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    int ensure(size_t b) {
-        if (b <= bytes && p) return RVE_OK;
-        release();
-        if (b == 0) b = 16;
-        cudaError_t e = cudaMalloc(&p, b);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-            return RVE_ERR_OUT_OF_MEMORY;
-        }
-        bytes = b;
-        return RVE_OK;
-    }
-    template <typename T>
-    T* as() const { return static_cast<T*>(p); }
-};
-
-template <typename T>
-static int upload(DevBuf& d, const T* h, size_t n, cudaStream_t s) {
-    RVE_TRY(d.ensure(n * sizeof(T)));
-    if (n) RVE_CUDA(cudaMemcpyAsync(d.p, h, n * sizeof(T), cudaMemcpyHostToDevice, s));
-    return RVE_OK;
-}
-
-// Constraint rows and preconditioner data of one field on the current BC.
-struct FieldDev {
-    int nc = 3;
-    int nfield = 1;
-    int64_t n_rows = 0;
-    DevBuf diag64, diag32, mask;
-    int m = 0;
-    int64_t n_sup = 0;
-    DevBuf sup_row, sup_coef, sup_of_row;
-};
+const std::string& last_error() { return g_last_error; }
 
 }  // namespace rve
 
 using namespace rve;
 
-struct rve_ctx_s {
-    rve_options opt;
-    cudaStream_t stream = nullptr;
-    cudaStream_t capture = nullptr;   // private stream used only to capture graphs
-    bool own_stream = false;
-    int device = 0;
-    int64_t launches = 0;
-    // profile mode: event pairs around every operator launch of a captured body
-    std::vector<cudaEvent_t> ev;
-    double op_ms = 0;
-    int64_t op_launches = 0;
-    double op_bytes = 0, op_flops = 0;
-    ~rve_ctx_s() {
-        for (auto e : ev) cudaEventDestroy(e);
-    }
-};
-
-struct rve_mesh_s {
-    rve_ctx ctx = nullptr;
-    int p = 1;
-    int bc = RVE_BC_DIRICHLET;
-    int64_t nv = 0, nt = 0;
-    std::vector<double> xyz;
-    std::vector<int32_t> tets;
-    std::vector<uint8_t> phase;
-    std::vector<double> tangent;
-    DofMap map;
-    double volume = 0;
-    // device mesh
-    DevBuf d_xyz, d_edofs, d_lverts, d_geo64, d_geo32, d_phase, d_tangent, d_flag;
-    DevBuf d_matm64, d_matm32, d_mats64, d_mats32;
-    FieldDev mech, scal;
-    bool have_materials = false;
-    MaterialConsts mc{};
-    rve_degradation deg{};
-    double T_C = 20, c_wt = 0, t_h = 0;
-    // solve workspace
-    DevBuf x64, r64, b64, p64, q64, x32, r32, p32, q32;
-    DevBuf epart, rzp, cpart, gpart, mpart, gsum, msum;
-    DevBuf colstate, scale64, scale32, wdev;
-    int64_t ws_rows = 0;
-    int ws_cols = 0;
-};
-
-namespace {
-
+namespace rve {
 int check_ctx(rve_ctx c) {
     if (!c) {
         set_error("null context");
@@ -139,6 +34,9 @@ int check_ctx(rve_ctx c) {
     cudaSetDevice(c->device);
     return RVE_OK;
 }
+}  // namespace rve
+
+namespace {
 
 // ------------------------------------------------------------ geometry + map
 int rebuild_map(rve_mesh m) {
@@ -481,8 +379,10 @@ struct Solver {
                 launch_pupdate<T>(rvw, r, p, q, cs, false, Lx);
             }
         };
+        // Profile mode launches the body directly on the context stream so that
+        // the event pairs around each operator launch can be timed.
         cudaGraphExec_t exec = nullptr;
-        {
+        if (!prof) {
             Launch Lc = L;
             Lc.stream = m->ctx->capture;
             cudaGraph_t graph = nullptr;
@@ -498,7 +398,10 @@ struct Solver {
             ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
         } guard{exec};
         while (it < max_iter) {
-            RVE_CUDA(cudaGraphLaunch(exec, s));
+            if (prof)
+                body(L);
+            else
+                RVE_CUDA(cudaGraphLaunch(exec, s));
             it += check;
             *launches += (int64_t)check * (f.m > 0 ? 6 : 5);
             RVE_CUDA(cudaGetLastError());
@@ -658,9 +561,11 @@ double rel_fro(const double* a, const double* b, int n) {
     return den > 0 ? std::sqrt(num / den) : std::sqrt(num);
 }
 
+}  // namespace
+
 // Solve B RVEs of one mesh whose degradation factors are in d_w (device).
-int homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D,
-                     rve_stats* st) {
+int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D,
+                          rve_stats* st) {
     cudaStream_t s = m->ctx->stream;
     const int ncols = 6 * B;
     RVE_TRY(m->scale64.ensure((size_t)ncols * 2 * 8));
@@ -726,8 +631,8 @@ int homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K,
     return RVE_OK;
 }
 
+namespace {
 bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
-
 }  // namespace
 
 // =================================================================== C ABI
@@ -1043,6 +948,15 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
     return rc;
 }
 
+// RVEs per device pass for one mesh: enough columns to fill the GPU (about 16M
+// vector entries per field), a multiple of 8, between 8 and 256.
+static int auto_batch(rve_mesh m) {
+    const double rows = (double)m->mech.n_rows;
+    int B = (int)(16.0e6 / (rows * 6.0));
+    B = std::max(8, std::min(256, B));
+    return (B / 8) * 8;
+}
+
 static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, int64_t G,
                              const double* T_dev, const double* c_dev, const double* t_dev,
                              const int32_t* mesh_id, double* C_dev, double* K_dev, double* D_dev,
@@ -1058,8 +972,8 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
         groups[mesh_id[g]].push_back(g);
     }
     int rc_all = RVE_OK;
-    DevBuf d_idx, d_tmp;
-    std::vector<double> hC, hK, hD;
+    DevBuf d_idx, d_tmp, d_res;
+    std::vector<double> res;
     for (int mi = 0; mi < n_meshes; ++mi) {
         auto& grp = groups[mi];
         if (grp.empty()) continue;
@@ -1068,38 +982,33 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
             set_error("mesh without materials in macro_update_gauss_points");
             return RVE_ERR_STATE;
         }
-        int Bmax = c->opt.batch > 0 ? c->opt.batch : 16;
+        const int Bmax = c->opt.batch > 0 ? c->opt.batch : auto_batch(m);
+        RVE_TRY(upload(d_idx, grp.data(), grp.size(), s));
         for (size_t off = 0; off < grp.size(); off += Bmax) {
             const int B = (int)std::min<size_t>(Bmax, grp.size() - off);
-            // gather states of this batch on the device
+            const int64_t* idx = d_idx.as<int64_t>() + off;
             RVE_TRY(d_tmp.ensure((size_t)B * 4 * 8));
-            double* dT = d_tmp.as<double>();
-            double* dc = dT + B;
-            double* dt = dT + 2 * B;
-            double* dw = dT + 3 * B;
-            for (int b = 0; b < B; ++b) {
-                const int64_t g = grp[off + b];
-                RVE_CUDA(cudaMemcpyAsync(dT + b, T_dev + g, 8, cudaMemcpyDeviceToDevice, s));
-                RVE_CUDA(cudaMemcpyAsync(dc + b, c_dev + g, 8, cudaMemcpyDeviceToDevice, s));
-                RVE_CUDA(cudaMemcpyAsync(dt + b, t_dev + g, 8, cudaMemcpyDeviceToDevice, s));
-            }
-            launch_degradation(B, dT, dc, dt, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, dw, s);
-            c->launches++;
-            hC.assign((size_t)B * 36, 0);
-            hK.assign((size_t)B * 9, 0);
-            hD.assign((size_t)B * 9, 0);
+            double* st3 = d_tmp.as<double>();
+            double* dw = st3 + 3 * B;
+            launch_gather_states(B, idx, T_dev, c_dev, t_dev, st3, s);
+            launch_degradation(B, st3, st3 + B, st3 + 2 * B, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, dw, s);
+            c->launches += 2;
+            res.assign((size_t)B * 55, 0.0);
+            std::vector<double> hC((size_t)B * 36), hK((size_t)B * 9), hD((size_t)B * 9);
             int rc = homogenise_batch(m, B, dw, hC.data(), hK.data(), hD.data(), st);
             if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return rc;
             if (rc != RVE_OK) rc_all = rc;
             for (int b = 0; b < B; ++b) {
-                const int64_t g = grp[off + b];
-                RVE_CUDA(cudaMemcpyAsync(C_dev + 36 * g, &hC[36 * b], 36 * 8, cudaMemcpyHostToDevice, s));
-                RVE_CUDA(cudaMemcpyAsync(K_dev + 9 * g, &hK[9 * b], 9 * 8, cudaMemcpyHostToDevice, s));
-                RVE_CUDA(cudaMemcpyAsync(D_dev + 9 * g, &hD[9 * b], 9 * 8, cudaMemcpyHostToDevice, s));
-                int32_t sv = rc;
-                RVE_CUDA(cudaMemcpyAsync(status_dev + g, &sv, 4, cudaMemcpyHostToDevice, s));
-                RVE_CUDA(cudaStreamSynchronize(s));
+                std::memcpy(&res[(size_t)b * 55], &hC[(size_t)b * 36], 36 * 8);
+                std::memcpy(&res[(size_t)b * 55 + 36], &hK[(size_t)b * 9], 9 * 8);
+                std::memcpy(&res[(size_t)b * 55 + 45], &hD[(size_t)b * 9], 9 * 8);
+                res[(size_t)b * 55 + 54] = rc;
             }
+            RVE_TRY(upload(d_res, res.data(), res.size(), s));
+            launch_scatter_results(B, idx, d_res.as<double>(), C_dev, K_dev, D_dev, status_dev, s);
+            c->launches++;
+            RVE_CUDA(cudaGetLastError());
+            RVE_CUDA(cudaStreamSynchronize(s));   // res is reused by the next batch
         }
     }
     return rc_all;

@@ -1,0 +1,143 @@
+// Internal definitions shared by the host files of the C ABI (api.cu,
+// surrogate_api.cu): device buffers, handles and error macros.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "rve_internal.h"
+
+#define RVE_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::rve::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));        \
+            return e_ == cudaErrorMemoryAllocation ? RVE_ERR_OUT_OF_MEMORY : RVE_ERR_CUDA; \
+        }                                                                                \
+    } while (0)
+
+#define RVE_TRY(call)                  \
+    do {                               \
+        int rc_ = (call);              \
+        if (rc_ != RVE_OK) return rc_; \
+    } while (0)
+
+namespace rve {
+
+const std::string& last_error();
+
+// ------------------------------------------------------------ device buffer
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int ensure(size_t b) {
+        if (b <= bytes && p) return RVE_OK;
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return RVE_ERR_OUT_OF_MEMORY;
+        }
+        bytes = b;
+        return RVE_OK;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+template <typename T>
+inline int upload(DevBuf& d, const T* h, size_t n, cudaStream_t s) {
+    RVE_TRY(d.ensure(n * sizeof(T)));
+    if (n) RVE_CUDA(cudaMemcpyAsync(d.p, h, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return RVE_OK;
+}
+
+// Constraint rows and preconditioner data of one field on the current BC.
+struct FieldDev {
+    int nc = 3;
+    int nfield = 1;
+    int64_t n_rows = 0;
+    DevBuf diag64, diag32, mask;
+    int m = 0;
+    int64_t n_sup = 0;
+    DevBuf sup_row, sup_coef, sup_of_row;
+};
+
+}  // namespace rve
+
+struct rve_ctx_s {
+    rve_options opt;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;   // private stream used only to capture graphs
+    bool own_stream = false;
+    int device = 0;
+    int64_t launches = 0;
+    // profile mode: event pairs around every operator launch of a captured body
+    std::vector<cudaEvent_t> ev;
+    double op_ms = 0;
+    int64_t op_launches = 0;
+    double op_bytes = 0, op_flops = 0;
+    ~rve_ctx_s() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+struct rve_mesh_s {
+    rve_ctx ctx = nullptr;
+    int p = 1;
+    int bc = RVE_BC_DIRICHLET;
+    int64_t nv = 0, nt = 0;
+    std::vector<double> xyz;
+    std::vector<int32_t> tets;
+    std::vector<uint8_t> phase;
+    std::vector<double> tangent;
+    rve::DofMap map;
+    double volume = 0;
+    // device mesh
+    rve::DevBuf d_xyz, d_edofs, d_lverts, d_geo64, d_geo32, d_phase, d_tangent, d_flag;
+    rve::DevBuf d_matm64, d_matm32, d_mats64, d_mats32;
+    rve::FieldDev mech, scal;
+    bool have_materials = false;
+    rve::MaterialConsts mc{};
+    rve_degradation deg{};
+    double T_C = 20, c_wt = 0, t_h = 0;
+    // solve workspace
+    rve::DevBuf x64, r64, b64, p64, q64, x32, r32, p32, q32;
+    rve::DevBuf epart, rzp, cpart, gpart, mpart, gsum, msum;
+    rve::DevBuf colstate, scale64, scale32, wdev;
+};
+
+namespace rve {
+// Batched PCG homogenisation of B RVEs of one mesh (degradation factors d_w on
+// the device); host outputs C [B][36], K [B][9], D [B][9] (any may be null).
+int homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D, rve_stats* st);
+int check_ctx(rve_ctx c);
+}  // namespace rve

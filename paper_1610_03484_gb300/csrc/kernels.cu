@@ -60,6 +60,31 @@ __host__ __device__ constexpr int s3(int i, int j) {
     return i == j ? i : ((i + j == 1) ? 3 : ((i + j == 3) ? 4 : 5));
 }
 
+// ------------------------------------------------------- partial-sum type
+// Per-thread partial sums: FP64 for the FP64 path; for the FP32 path a
+// compensated (Kahan) FP32 sum, because FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this GPU.  Either way the block and grid level
+// reductions that follow are FP64.
+template <typename T>
+struct PartialSum;
+template <>
+struct PartialSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct PartialSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // ---------------------------------------------------- block column reduction
 // Reduce `nacc` per-thread values over the rows of the block for each column
 // and store them to out[(blockIdx.y * ncols + col) * nacc + a].
@@ -82,6 +107,25 @@ __device__ __forceinline__ void block_column_reduce(const double (&acc)[NACC], d
     }
 }
 
+// Sum of one value per thread over the whole block (blockDim a multiple of 32,
+// at most 1024); the result is valid in every thread.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double warp_part[32];
+    __shared__ double total;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) warp_part[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double t = lane < (int)(blockDim.x >> 5) ? warp_part[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) total = t;
+    }
+    __syncthreads();
+    return total;
+}
+
 // ------------------------------------------------------------- the operator
 // y += sum_e A_e^T K_e A_e x  for every column, matrix-free (Eq. RVE_Eq_var_final):
 // per element, the reference gradient of the field is expanded on the
@@ -102,7 +146,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
     const int col = blockIdx.x * cpb + cl;
     const int field = (col % 6) >= 3 ? 1 : 0;   // scalar solve: thermal / moisture
     const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
-    double energy = 0.0;
+    PartialSum<T> energy;
     // converged columns skip the element loop (their step length is zero)
     const int64_t e_end = (active && !active[col]) ? 0 : ev.nt;
 
@@ -155,6 +199,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
         for (int i = 0; i < NMAT; ++i)
             Dm[i] = sv * __ldg(ev.mat + e * (NC == 3 ? 21 : 12) + (NC == 3 ? 0 : 6 * field) + i);
         // ---- per mode: gradient -> stress/flux -> W = J^-1 S, overwriting V
+        T e_elem = T(0);
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
             T H[NC][3];
@@ -202,10 +247,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     const T w = G[3 * k] * S[c][0] + G[3 * k + 1] * S[c][1] + G[3 * k + 2] * S[c][2];
-                    if (epart && !MACRO) energy += (double)V[m][k][c] * (double)w;   // x.Kx = sum V.W
+                    if (!MACRO) e_elem = fma(V[m][k][c], w, e_elem);   // x.Kx = sum V.W
                     V[m][k][c] = w;
                 }
         }
+        if (epart && !MACRO) energy.add(e_elem);
         // ---- backward and scatter: y_j,c = sum_m sum_k A[k][m][j] W[m][k][c]
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -234,7 +280,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
         }
     }
     if (epart) {
-        double acc[1] = {energy};
+        double acc[1] = {energy.value()};
         block_column_reduce<1>(acc, epart, ncols, cpb, col);
     }
 }
@@ -540,15 +586,18 @@ __device__ __forceinline__ T inv_diag(const RowView<T>& rv, int64_t row, int col
     return d > T(0) ? T(1) / d : T(0);
 }
 
-__global__ void k_finalize_alpha(const double* __restrict__ ep, int nby, int ncols, ColState cs) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= ncols) return;
+// One block per column: alpha = (r, z) / (p, K p) with (p, K p) summed in parallel.
+__global__ void __launch_bounds__(256) k_finalize_alpha(const double* __restrict__ ep, int nby, int ncols,
+                                                        ColState cs) {
+    const int col = blockIdx.x;
     if (!cs.active[col]) {
-        cs.alpha[col] = 0.0;
+        if (threadIdx.x == 0) cs.alpha[col] = 0.0;
         return;
     }
-    double pq = 0.0;
-    for (int b = 0; b < nby; ++b) pq += ep[(int64_t)b * ncols + col];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nby; b += blockDim.x) v += ep[(int64_t)b * ncols + col];
+    const double pq = block_sum(v);
+    if (threadIdx.x != 0) return;
     double a = cs.rz[col] / pq;
     if (!(pq > 0.0) || !isfinite(a)) {
         atomicOr(cs.flags, 1);
@@ -561,7 +610,7 @@ __global__ void k_finalize_alpha(const double* __restrict__ ep, int nby, int nco
 
 template <typename T>
 void launch_finalize_alpha(const double* energy_partial, ColState cs, const Launch& L) {
-    k_finalize_alpha<<<(L.ncols + 127) / 128, 128, 0, L.stream>>>(energy_partial, L.nby, L.ncols, cs);
+    k_finalize_alpha<<<L.ncols, 256, 0, L.stream>>>(energy_partial, L.nby, L.ncols, cs);
 }
 template void launch_finalize_alpha<float>(const double*, ColState, const Launch&);
 template void launch_finalize_alpha<double>(const double*, ColState, const Launch&);
@@ -576,7 +625,7 @@ __global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x
     const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
     const int col = blockIdx.x * cpb + cl;
     const T a = apply ? (T)cs.alpha[col] : T(0);
-    double acc = 0.0;
+    PartialSum<T> acc;
     // a converged column keeps x and r; its partial stays zero
     const int64_t i_end = (apply && !cs.active[col]) ? 0 : rv.n_rows;
     for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += (int64_t)gridDim.y * rows) {
@@ -588,9 +637,9 @@ __global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x
             r[idx] = rv_;
         }
         const T w = inv_diag(rv, i, col, ncols) * rv_;
-        acc += (double)rv_ * (double)w;
+        acc.add(rv_ * w);
     }
-    double accs[1] = {acc};
+    double accs[1] = {acc.value()};
     block_column_reduce<1>(accs, rzp, ncols, cpb, col);
 }
 
@@ -648,31 +697,38 @@ template void launch_constraint_dot<double>(const RowView<double>&, const double
                                             const Launch&);
 
 // mu = S^-1 w, rz = (r, M^-1 r) - w . mu, beta, convergence.
-// first: 0 = iteration, 1 = initial residual, 2 = multipliers only (no state change)
-__global__ void k_finalize_beta(int m, const double* __restrict__ rzp, const double* __restrict__ cp,
-                                int nby, int ncols, ColState cs, int first) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= ncols) return;
+// first: 0 = iteration, 1 = initial residual, 2 = multipliers only (no state change).
+// One block per column: the partial sums are reduced in parallel, then thread 0
+// solves the m x m Schur system for mu and updates rz, beta and convergence.
+__global__ void __launch_bounds__(256) k_finalize_beta(int m, const double* __restrict__ rzp,
+                                                       const double* __restrict__ cp, int nby,
+                                                       int ncols, ColState cs, int first) {
+    const int col = blockIdx.x;
     if (first == 0 && !cs.active[col]) return;
-    double rz = 0.0;
-    for (int b = 0; b < nby; ++b) rz += rzp[(int64_t)b * ncols + col];
-    double w[12], mu[12];
+    double v = 0.0;
+    if (first != 2)
+        for (int b = threadIdx.x; b < nby; b += blockDim.x) v += rzp[(int64_t)b * ncols + col];
+    double rz = block_sum(v);
+    __shared__ double w[12];
     for (int k = 0; k < m; ++k) {
-        double s = 0.0;
-        for (int b = 0; b < nby; ++b) s += cp[((int64_t)b * m + k) * ncols + col];
-        w[k] = s;
+        double t = 0.0;
+        for (int b = threadIdx.x; b < nby; b += blockDim.x) t += cp[((int64_t)b * m + k) * ncols + col];
+        t = block_sum(t);
+        if (threadIdx.x == 0) w[k] = t;
     }
+    if (threadIdx.x != 0) return;
+    double mu[12];
     if (m > 0) {
         const double* Lc = cs.schur + (int64_t)col * m * m;
-        for (int i = 0; i < m; ++i) {   // forward
-            double t = w[i];
-            for (int j = 0; j < i; ++j) t -= Lc[i * m + j] * mu[j];
-            mu[i] = t / Lc[i * m + i];
+        for (int i2 = 0; i2 < m; ++i2) {   // forward
+            double t = w[i2];
+            for (int j2 = 0; j2 < i2; ++j2) t -= Lc[i2 * m + j2] * mu[j2];
+            mu[i2] = t / Lc[i2 * m + i2];
         }
-        for (int i = m - 1; i >= 0; --i) {   // backward
-            double t = mu[i];
-            for (int j = i + 1; j < m; ++j) t -= Lc[j * m + i] * mu[j];
-            mu[i] = t / Lc[i * m + i];
+        for (int i2 = m - 1; i2 >= 0; --i2) {   // backward
+            double t = mu[i2];
+            for (int j2 = i2 + 1; j2 < m; ++j2) t -= Lc[j2 * m + i2] * mu[j2];
+            mu[i2] = t / Lc[i2 * m + i2];
         }
         for (int k = 0; k < m; ++k) {
             rz -= w[k] * mu[k];
@@ -700,14 +756,13 @@ __global__ void k_finalize_beta(int m, const double* __restrict__ rzp, const dou
 
 void launch_finalize_beta(int m, const double* rz_partial, const double* c_partial, ColState cs,
                           bool first, const Launch& L) {
-    k_finalize_beta<<<(L.ncols + 127) / 128, 128, 0, L.stream>>>(m, rz_partial, c_partial, L.nby,
-                                                                  L.ncols, cs, first ? 1 : 0);
+    k_finalize_beta<<<L.ncols, 256, 0, L.stream>>>(m, rz_partial, c_partial, L.nby, L.ncols, cs,
+                                                   first ? 1 : 0);
 }
 
 void launch_constraint_multipliers(int m, const double* c_partial, ColState cs, const Launch& L) {
     if (m == 0) return;
-    k_finalize_beta<<<(L.ncols + 127) / 128, 128, 0, L.stream>>>(m, c_partial, c_partial, L.nby,
-                                                                  L.ncols, cs, 2);
+    k_finalize_beta<<<L.ncols, 256, 0, L.stream>>>(m, c_partial, c_partial, L.nby, L.ncols, cs, 2);
 }
 
 // Residual reset r <- r - C^T mu on the constraint support (the part of the
@@ -958,17 +1013,58 @@ void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const T* u, double
 template void launch_mean_stress<double>(int, int, const ElemView<double>&, const double*, double*,
                                          const Launch&);
 
-__global__ void k_reduce_partials(int nby, int width, const double* __restrict__ part,
-                                  double* __restrict__ out) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= width) return;
-    double s = 0.0;
-    for (int b = 0; b < nby; ++b) s += part[(int64_t)b * width + w];
-    out[w] = s;
+// out[w] = sum_b part[b][w]: one block per output value (up to 128 outputs per
+// block row are handled by grid-striding over w).
+__global__ void __launch_bounds__(256) k_reduce_partials(int nby, int width, const double* __restrict__ part,
+                                                         double* __restrict__ out) {
+    for (int w = blockIdx.x; w < width; w += gridDim.x) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nby; b += blockDim.x) v += part[(int64_t)b * width + w];
+        v = block_sum(v);
+        if (threadIdx.x == 0) out[w] = v;
+    }
 }
 
 void launch_reduce_partials(int nby, int width, const double* partial, double* out, cudaStream_t s) {
-    k_reduce_partials<<<(width + 127) / 128, 128, 0, s>>>(nby, width, partial, out);
+    k_reduce_partials<<<width < 4096 ? width : 4096, 256, 0, s>>>(nby, width, partial, out);
+}
+
+// ------------------------------------------------------ batch gather/scatter
+// states of the batch: out[b] = in[idx[b]] for T, c, t
+__global__ void k_gather_states(int B, const int64_t* __restrict__ idx, const double* __restrict__ T,
+                                const double* __restrict__ c, const double* __restrict__ t,
+                                double* __restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int64_t g = idx[b];
+    out[b] = T[g];
+    out[B + b] = c[g];
+    out[2 * B + b] = t[g];
+}
+
+void launch_gather_states(int B, const int64_t* idx, const double* T, const double* c, const double* t,
+                          double* out, cudaStream_t s) {
+    k_gather_states<<<(B + 127) / 128, 128, 0, s>>>(B, idx, T, c, t, out);
+}
+
+// results of the batch [B][36 + 9 + 9 + 1 status] -> per-point outputs
+__global__ void k_scatter_results(int B, const int64_t* __restrict__ idx, const double* __restrict__ res,
+                                  double* __restrict__ C, double* __restrict__ K, double* __restrict__ D,
+                                  int32_t* __restrict__ status) {
+    const int b = blockIdx.x;
+    const int64_t g = idx[b];
+    const double* r = res + (int64_t)b * 55;
+    for (int i = threadIdx.x; i < 54; i += blockDim.x) {
+        if (i < 36) C[g * 36 + i] = r[i];
+        else if (i < 45) K[g * 9 + i - 36] = r[i];
+        else D[g * 9 + i - 45] = r[i];
+    }
+    if (threadIdx.x == 0) status[g] = (int32_t)r[54];
+}
+
+void launch_scatter_results(int B, const int64_t* idx, const double* res, double* C, double* K, double* D,
+                            int32_t* status, cudaStream_t s) {
+    k_scatter_results<<<B, 64, 0, s>>>(B, idx, res, C, K, D, status);
 }
 
 // ---------------------------------------------------------- elementwise

@@ -121,6 +121,12 @@ void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const T* u, double
 void launch_reduce_partials(int nby, int width, const double* partial, double* out,
                             cudaStream_t s);
 
+// batch gather of (T, c, t) and scatter of [B][55] results (C 36, K 9, D 9, status)
+void launch_gather_states(int B, const int64_t* idx, const double* T, const double* c, const double* t,
+                          double* out, cudaStream_t s);
+void launch_scatter_results(int B, const int64_t* idx, const double* res, double* C, double* K, double* D,
+                            int32_t* status, cudaStream_t s);
+
 // elementwise helpers
 void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 void launch_axpy_f2d(int64_t n, const float* a, double* b, cudaStream_t s);

@@ -1,0 +1,27 @@
+// Launch wrappers of the surrogate kernels (surrogate.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace rve {
+
+void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, const float* bias,
+                      int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s);
+void launch_transpose_bf16(int rows, int cols, const __nv_bfloat16* in, __nv_bfloat16* out, cudaStream_t s);
+void launch_silu_backward(int64_t n, const float* dY, const float* Z, __nv_bfloat16* g, cudaStream_t s);
+void launch_head_loss(int M, int m_valid, int noutp, const float* z, const float* target, const float* sigma,
+                      const uint8_t* diag, __nv_bfloat16* dz, float* loss_acc, cudaStream_t s);
+void launch_colsum_bf16(int rows, int cols, const __nv_bfloat16* in, float* out, cudaStream_t s);
+void launch_adam(int K, int N, float* W, const float* Gt, float* m1, float* m2, float lr, int step,
+                 __nv_bfloat16* Wt, __nv_bfloat16* Wn, int n_valid_out, cudaStream_t s);
+void launch_adam_bias(int N, float* b, const float* g, float* m1, float* m2, float lr, int step, int n_valid_out,
+                      cudaStream_t s);
+void launch_features(int n, int M, int kin, const double* feat, const float* mean, const float* inv_std,
+                     __nv_bfloat16* X, cudaStream_t s);
+void launch_head_tensors(int n, int noutp, const float* z, const uint8_t* diag, double* Te, cudaStream_t s);
+void launch_ensemble(int n, int members, const double* T, double* Tm, double* spread, cudaStream_t s);
+
+}  // namespace rve
