@@ -75,6 +75,9 @@ typedef struct rve_options {
     int     batch;           /* RVEs solved together in macro_update_gauss_points, 0 = auto */
     void*   stream;          /* cudaStream_t to run on; NULL = library-created stream */
     int     profile;         /* 1: time every operator launch with CUDA events (rve_stats.op_*) */
+    int     warm_start;      /* macro_update_gauss_points: 1 (default) solves each mesh's points in
+                                order of their degradation factor and starts every batch from the
+                                nearest solutions of the previous batch of the same call */
 } rve_options;
 
 /* Isotropic matrix phase (Sec. 1, Sec. 7). */

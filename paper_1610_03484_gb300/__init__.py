@@ -35,7 +35,8 @@ class RveError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_iter", C.c_int), ("inner_rtol", C.c_double), ("max_refine", C.c_int),
-                ("check_every", C.c_int), ("batch", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int)]
+                ("check_every", C.c_int), ("batch", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
+                ("warm_start", C.c_int)]
 
 
 class MatrixProps(C.Structure):
@@ -173,13 +174,15 @@ class Context:
     """One librve context (device + stream).  Use as a context manager."""
 
     def __init__(self, precision=PREC_FP64, rtol=1e-10, max_iter=20000, inner_rtol=1e-6,
-                 max_refine=4, check_every=16, batch=0, stream=None, device=0, profile=False):
+                 max_refine=4, check_every=16, batch=0, stream=None, device=0, profile=False,
+                 warm_start=True):
         lib = load_library()
         o = default_options()
         o.device, o.precision, o.rtol, o.max_iter = device, precision, rtol, max_iter
         o.inner_rtol, o.max_refine, o.check_every, o.batch = inner_rtol, max_refine, check_every, batch
         o.stream = stream
         o.profile = int(profile)
+        o.warm_start = int(warm_start)
         h = C.c_void_p()
         _check(lib.rve_create(C.byref(h), C.byref(o)), "rve_create")
         self.h = h

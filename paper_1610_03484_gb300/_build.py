@@ -29,7 +29,7 @@ def nvcc() -> str:
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
-           "-I" + CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+           "-I" + CSRC, "-I" + BUILD, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["-x", "cu"]
         if verbose:
@@ -42,9 +42,24 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+def gen_tables() -> None:
+    """Compile and run the host generator of the compile-time basis tables."""
+    os.makedirs(BUILD, exist_ok=True)
+    exe = os.path.join(BUILD, "gen_tables")
+    cxx = os.environ.get("CXX") or shutil.which("g++") or "c++"
+    cmd = [cxx, "-O2", "-std=c++17", "-I" + CSRC, os.path.join(CSRC, "gen_tables.cpp"),
+           os.path.join(CSRC, "basis.cpp"), "-o", exe]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"building gen_tables failed:\n{res.stderr}")
+    res = subprocess.run([exe, os.path.join(BUILD, "basis_tables.inc")], capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError("gen_tables failed")
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the library if any source is newer than librve.so; returns its path."""
-    srcs = [os.path.join(CSRC, s) for s in SOURCES]
+    srcs = [os.path.join(CSRC, s) for s in SOURCES + ["gen_tables.cpp"]]
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hdrs.append(os.path.join(os.path.dirname(HERE), "include", "rve.h"))
     if not force and os.path.exists(LIB):
@@ -52,6 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if all(os.path.getmtime(f) <= t for f in srcs + hdrs):
             return LIB
     os.makedirs(BUILD, exist_ok=True)
+    gen_tables()
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + ".tmp"

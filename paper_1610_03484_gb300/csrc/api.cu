@@ -348,11 +348,10 @@ struct Solver {
         RowView<T> rvw = rv<T>(scale);
         ElemView<T> evw = ev<T>(scale);
         launch_schur<T>(rvw, cs, L);
-        launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), false, L);
-        launch_constraint_dot<T>(rvw, r, m->cpart.as<double>(), L);
+        launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), false, L, m->cpart.as<double>());
         launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, true, L);
         launch_pupdate<T>(rvw, r, p, q, cs, true, L);
-        *launches += 6;
+        *launches += 5;
         std::vector<int32_t> act(ncols);
         int it = 0;
         conv = false;
@@ -373,8 +372,7 @@ struct Solver {
                 launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active);
                 if (prof) cudaEventRecord(m->ctx->ev[2 * k + 1], Lx.stream);
                 launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
-                launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx);
-                launch_constraint_dot<T>(rvw, r, m->cpart.as<double>(), Lx);
+                launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx, m->cpart.as<double>());
                 launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, Lx);
                 launch_pupdate<T>(rvw, r, p, q, cs, false, Lx);
             }
@@ -403,7 +401,7 @@ struct Solver {
             else
                 RVE_CUDA(cudaGraphLaunch(exec, s));
             it += check;
-            *launches += (int64_t)check * (f.m > 0 ? 6 : 5);
+            *launches += (int64_t)check * 5;
             RVE_CUDA(cudaGetLastError());
             RVE_CUDA(cudaMemcpyAsync(act.data(), cs.active, sizeof(int32_t) * ncols,
                                      cudaMemcpyDeviceToHost, s));
@@ -467,7 +465,10 @@ struct Solver {
         return RVE_OK;
     }
 
-    int run(int precision, SolveOut& out) {
+    // warm: optional previous solutions [n_rows][warm_cols] (FP64) and the
+    // device column map choosing, for each column, its starting column there.
+    int run(int precision, SolveOut& out, const double* warm = nullptr, int warm_cols = 0,
+            const int32_t* warm_map = nullptr) {
         const rve_options& o = m->ctx->opt;
         const bool mixed = precision == RVE_PREC_MIXED;
         RVE_TRY(alloc(mixed));
@@ -475,8 +476,7 @@ struct Solver {
         double* x64 = m->x64.as<double>();
         double* r64 = m->r64.as<double>();
         double* b64 = m->b64.as<double>();
-        RVE_CUDA(cudaMemsetAsync(x64, 0, nv * 8, s));
-        RVE_TRY(residual64(x64, b64));   // b = -(K 0 + macro)
+        RVE_TRY(residual64(nullptr, b64));   // b = -(macro load): the operator skips the gathers
         RVE_CUDA(cudaMemcpyAsync(r64, b64, nv * 8, cudaMemcpyDeviceToDevice, s));
         // reference norms (b, P b); r64 becomes the projected right-hand side
         std::vector<double> bn(ncols, 1.0);
@@ -488,37 +488,53 @@ struct Solver {
         out.iterations = 0;
         out.sweeps = 0;
         out.converged = false;
-        if (!mixed) {
-            int its = 0;
-            bool conv = false;
-            RVE_TRY(pcg<double>(x64, r64, m->p64.as<double>(), m->q64.as<double>(), m->scale64,
-                                o.rtol, o.max_iter, its, conv));
-            out.iterations = its;
+        double rel = 1.0;
+        if (warm) {
+            // start from the neighbouring solutions: r = b - K x0 in FP64
+            launch_gather_columns(n_rows, ncols, warm_cols, warm_map, warm, x64, s);
+            *launches += 1;
             RVE_TRY(residual64(x64, r64));
-            RVE_TRY(rel_residual(r64, bn, out.rel_res));
-            out.converged = conv || out.rel_res <= o.rtol * 10;
+            RVE_TRY(rel_residual(r64, bn, rel));
+        } else {
+            RVE_CUDA(cudaMemsetAsync(x64, 0, nv * 8, s));
+        }
+        out.rel_res = rel;
+        if (!mixed) {
+            if (rel > o.rtol) {
+                int its = 0;
+                bool conv = false;
+                RVE_TRY(pcg<double>(x64, r64, m->p64.as<double>(), m->q64.as<double>(), m->scale64,
+                                    o.rtol / rel, o.max_iter, its, conv));
+                out.iterations = its;
+                RVE_TRY(residual64(x64, r64));
+                RVE_TRY(rel_residual(r64, bn, out.rel_res));
+                out.converged = conv || out.rel_res <= o.rtol * 10;
+            } else {
+                out.converged = true;
+            }
         } else {
             float* x32 = m->x32.as<float>();
             float* r32 = m->r32.as<float>();
             int total = 0;
-            for (int sw = 0; sw < std::max(1, o.max_refine); ++sw) {
+            out.converged = rel <= o.rtol;
+            for (int sw = 0; sw < std::max(1, o.max_refine) && !out.converged; ++sw) {
+                // reduce the residual only as far as the outer tolerance needs
+                // (half again for margin), never below what FP32 can resolve
+                const double inner = std::max(o.inner_rtol, 0.5 * o.rtol / out.rel_res);
                 launch_cast_d2f((int64_t)nv, r64, r32, s);
                 RVE_CUDA(cudaMemsetAsync(x32, 0, nv * 4, s));
                 *launches += 1;
                 int its = 0;
                 bool conv = false;
                 RVE_TRY(pcg<float>(x32, r32, m->p32.as<float>(), m->q32.as<float>(), m->scale32,
-                                   o.inner_rtol, o.max_iter, its, conv));
+                                   std::min(inner, 0.5), o.max_iter, its, conv));
                 total += its;
                 launch_axpy_f2d((int64_t)nv, x32, x64, s);
                 *launches += 1;
                 RVE_TRY(residual64(x64, r64));
                 RVE_TRY(rel_residual(r64, bn, out.rel_res));
                 out.sweeps = sw + 1;
-                if (out.rel_res <= o.rtol) {
-                    out.converged = true;
-                    break;
-                }
+                out.converged = out.rel_res <= o.rtol;
             }
             out.iterations = total;
         }
@@ -565,7 +581,7 @@ double rel_fro(const double* a, const double* b, int n) {
 
 // Solve B RVEs of one mesh whose degradation factors are in d_w (device).
 int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D,
-                          rve_stats* st) {
+                          rve_stats* st, const double* w_host) {
     cudaStream_t s = m->ctx->stream;
     const int ncols = 6 * B;
     RVE_TRY(m->scale64.ensure((size_t)ncols * 2 * 8));
@@ -576,16 +592,52 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
     launch_column_scales<float>(B, d_w, m->deg.apply_to_yarn, true, m->scale32.as<float>(), s);
     m->ctx->launches += 2;
     SolveOut om, osc;
+    // warm start: column map from this batch to the nearest degradation factor
+    // of the mesh's previous batch (set up by macro_update_gauss_points)
+    std::vector<int32_t> cmap;
+    auto warm_ready = [&](int f) { return w_host && m->warm_cols[f] > 0 && !m->warm_w[f].empty(); };
+    auto build_map = [&](int f) -> int {
+        const std::vector<double>& pw = m->warm_w[f];
+        cmap.assign((size_t)6 * B, 0);
+        for (int b = 0; b < B; ++b) {
+            int best = 0;
+            for (int q = 1; q < (int)pw.size(); ++q)
+                if (std::fabs(pw[q] - w_host[b]) < std::fabs(pw[best] - w_host[b])) best = q;
+            for (int c = 0; c < 6; ++c) cmap[6 * b + c] = 6 * best + c;
+        }
+        return upload(m->warm_map, cmap.data(), cmap.size(), s);
+    };
+    auto keep_warm = [&](int f, FieldDev& fd) -> int {
+        if (!w_host) return RVE_OK;
+        const size_t nb = (size_t)fd.n_rows * 6 * B * 8;
+        RVE_TRY(m->warm[f].ensure(nb));
+        RVE_CUDA(cudaMemcpyAsync(m->warm[f].p, m->x64.p, nb, cudaMemcpyDeviceToDevice, s));
+        m->warm_cols[f] = 6 * B;
+        m->warm_w[f].assign(w_host, w_host + B);
+        return RVE_OK;
+    };
     {
         Solver sv(m, m->mech, B);
-        RVE_TRY(sv.run(prec, om));
+        if (warm_ready(0)) {
+            RVE_TRY(build_map(0));
+            RVE_TRY(sv.run(prec, om, m->warm[0].as<double>(), m->warm_cols[0], m->warm_map.as<int32_t>()));
+        } else {
+            RVE_TRY(sv.run(prec, om));
+        }
+        RVE_TRY(keep_warm(0, m->mech));
     }
     launch_column_scales<double>(B, d_w, 0, false, m->scale64.as<double>(), s);
     launch_column_scales<float>(B, d_w, 0, false, m->scale32.as<float>(), s);
     m->ctx->launches += 2;
     {
         Solver sv(m, m->scal, B);
-        RVE_TRY(sv.run(prec, osc));
+        if (warm_ready(1)) {
+            RVE_TRY(build_map(1));
+            RVE_TRY(sv.run(prec, osc, m->warm[1].as<double>(), m->warm_cols[1], m->warm_map.as<int32_t>()));
+        } else {
+            RVE_TRY(sv.run(prec, osc));
+        }
+        RVE_TRY(keep_warm(1, m->scal));
     }
     double hm_m = 0, hm_s = 0;
     for (int b = 0; b < B; ++b) {
@@ -669,6 +721,7 @@ void rve_default_options(rve_options* o) {
     o->batch = 0;
     o->stream = nullptr;
     o->profile = 0;
+    o->warm_start = 1;
 }
 
 int rve_create(rve_ctx* out, const rve_options* opts) {
@@ -974,6 +1027,14 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
     int rc_all = RVE_OK;
     DevBuf d_idx, d_tmp, d_res;
     std::vector<double> res;
+    // host copy of the states, used only to order the points of each mesh
+    std::vector<double> hT_all(G), hc_all(G), ht_all(G);
+    if (G > 0) {
+        RVE_CUDA(cudaMemcpyAsync(hT_all.data(), T_dev, G * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaMemcpyAsync(hc_all.data(), c_dev, G * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaMemcpyAsync(ht_all.data(), t_dev, G * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaStreamSynchronize(s));
+    }
     for (int mi = 0; mi < n_meshes; ++mi) {
         auto& grp = groups[mi];
         if (grp.empty()) continue;
@@ -983,6 +1044,33 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
             return RVE_ERR_STATE;
         }
         const int Bmax = c->opt.batch > 0 ? c->opt.batch : auto_batch(m);
+        // order the points by degradation factor so that each batch starts from
+        // the solutions of its neighbours in the previous batch; no solution is
+        // carried over from an earlier call
+        std::vector<double> wg(grp.size());
+        {
+            const rve_degradation& dg = m->deg;
+            for (size_t i = 0; i < grp.size(); ++i) {
+                const int64_t g = grp[i];
+                const double cn = std::min(std::max(hc_all[g] / dg.c_sat_wt, 0.0), 1.0);
+                const double alpha = dg.beta * std::log(1.0 - (hT_all[g] + 273.15) / (dg.Tg_C + 273.15));
+                wg[i] = std::exp(-cn * alpha * ht_all[g] / 24.0);
+            }
+            std::vector<size_t> order(grp.size());
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](size_t a2, size_t b2) { return wg[a2] < wg[b2]; });
+            std::vector<int64_t> g2(grp.size());
+            std::vector<double> w2(grp.size());
+            for (size_t i = 0; i < grp.size(); ++i) {
+                g2[i] = grp[order[i]];
+                w2[i] = wg[order[i]];
+            }
+            grp.swap(g2);
+            wg.swap(w2);
+        }
+        m->warm_cols[0] = m->warm_cols[1] = 0;
+        m->warm_w[0].clear();
+        m->warm_w[1].clear();
         RVE_TRY(upload(d_idx, grp.data(), grp.size(), s));
         for (size_t off = 0; off < grp.size(); off += Bmax) {
             const int B = (int)std::min<size_t>(Bmax, grp.size() - off);
@@ -995,7 +1083,8 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
             c->launches += 2;
             res.assign((size_t)B * 55, 0.0);
             std::vector<double> hC((size_t)B * 36), hK((size_t)B * 9), hD((size_t)B * 9);
-            int rc = homogenise_batch(m, B, dw, hC.data(), hK.data(), hD.data(), st);
+            int rc = homogenise_batch(m, B, dw, hC.data(), hK.data(), hD.data(), st,
+                                      c->opt.warm_start ? &wg[off] : nullptr);
             if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return rc;
             if (rc != RVE_OK) rc_all = rc;
             for (int b = 0; b < B; ++b) {

@@ -133,11 +133,18 @@ struct rve_mesh_s {
     rve::DevBuf x64, r64, b64, p64, q64, x32, r32, p32, q32;
     rve::DevBuf epart, rzp, cpart, gpart, mpart, gsum, msum;
     rve::DevBuf colstate, scale64, scale32, wdev;
+    // warm start: the previous batch's FP64 solutions per field and their factors
+    rve::DevBuf warm[2], warm_map;
+    int warm_cols[2] = {0, 0};
+    std::vector<double> warm_w[2];
 };
 
 namespace rve {
 // Batched PCG homogenisation of B RVEs of one mesh (degradation factors d_w on
 // the device); host outputs C [B][36], K [B][9], D [B][9] (any may be null).
-int homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D, rve_stats* st);
+// w_host (optional, [B]) enables the warm start from the mesh's previous batch
+// (see macro_update_gauss_points); the batch's solutions become the next start.
+int homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D, rve_stats* st,
+                     const double* w_host = nullptr);
 int check_ctx(rve_ctx c);
 }  // namespace rve

@@ -45,6 +45,24 @@ struct Tab<float> {
     __device__ __forceinline__ static float a(int p, int i) { return cA32[p - 1][i]; }
 };
 
+// Compile-time copies of the same tables (generated at build time from
+// basis.cpp): inside fully unrolled loops every entry is a literal, so the
+// structurally zero entries drop out of the operator's arithmetic.
+#include "basis_tables.inc"
+
+template <int P, typename T>
+__device__ __forceinline__ T basis_a(int i) {
+    if constexpr (sizeof(T) == 4) {
+        if constexpr (P == 1) return ctab::A1f[i];
+        else if constexpr (P == 2) return ctab::A2f[i];
+        else return ctab::A3f[i];
+    } else {
+        if constexpr (P == 1) return ctab::A1[i];
+        else if constexpr (P == 2) return ctab::A2[i];
+        else return ctab::A3[i];
+    }
+}
+
 template <int P>
 struct Order {
     static constexpr int NE = P == 1 ? 4 : (P == 2 ? 10 : 20);
@@ -154,8 +172,16 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
         const int32_t* ed = ev.edofs + e * NE;
         // ---- forward: reference-gradient modes V[m][k][c] = sum_j A[k][m][j] x_j,c.
         // Each gathered value is used for every mode at once and then dropped.
+        // Without x (macro load only) every mode starts at zero.
         T V[NM][3][NC];
-        {
+        if (MACRO && x == nullptr) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) V[m][k][c] = T(0);
+        } else {
             const int d0 = __ldg(ed);
             T x0[NC];
 #pragma unroll
@@ -173,6 +199,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
 #pragma unroll
                     for (int c = 0; c < NC; ++c) V[m][k][c] = T(0);
         }
+        if (!(MACRO && x == nullptr)) {
 #pragma unroll
         for (int j = 4; j < NE; ++j) {
             const int dj = __ldg(ed + j);
@@ -183,10 +210,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
             for (int m = 0; m < NM; ++m)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const T a = Tab<T>::a(P, (k * NM + m) * NE + j);
+                    const T a = basis_a<P, T>((k * NM + m) * NE + j);
+                    if (a != T(0))
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) V[m][k][c] = fma(a, xj[c], V[m][k][c]);
+                        for (int c = 0; c < NC; ++c) V[m][k][c] = fma(a, xj[c], V[m][k][c]);
                 }
+        }
         }
         // ---- element data; s * |T| folded into the material
         T G[9];
@@ -199,9 +228,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
         for (int i = 0; i < NMAT; ++i)
             Dm[i] = sv * __ldg(ev.mat + e * (NC == 3 ? 21 : 12) + (NC == 3 ? 0 : 6 * field) + i);
         // ---- per mode: gradient -> stress/flux -> W = J^-1 S, overwriting V
+        // (macro load only: the higher modes are zero and stay zero)
         T e_elem = T(0);
+        const int nm_live = (MACRO && x == nullptr) ? 1 : NM;
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
+            if (m >= nm_live) break;
             T H[NC][3];
 #pragma unroll
             for (int c = 0; c < NC; ++c)
@@ -270,9 +302,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_ope
             for (int m = 0; m < NM; ++m)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const T a = Tab<T>::a(P, (k * NM + m) * NE + j);
+                    const T a = basis_a<P, T>((k * NM + m) * NE + j);
+                    if (a != T(0))
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) yj[c] = fma(a, V[m][k][c], yj[c]);
+                        for (int c = 0; c < NC; ++c) yj[c] = fma(a, V[m][k][c], yj[c]);
                 }
             const int dj = __ldg(ed + j);
 #pragma unroll
@@ -615,18 +648,22 @@ void launch_finalize_alpha(const double* energy_partial, ColState cs, const Laun
 template void launch_finalize_alpha<float>(const double*, ColState, const Launch&);
 template void launch_finalize_alpha<double>(const double*, ColState, const Launch&);
 
-// x += alpha p, r -= alpha q (when apply), partial (r, M^-1 r) per column.
+// x += alpha p, r -= alpha q (when apply), partial (r, M^-1 r) per column and,
+// on constraint-support rows, the partial constraint products C M^-1 r
+// (m <= 12 rows), written to cp[(blockIdx.y * m + k) * ncols + col].
 template <typename T>
 __global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x, T* __restrict__ r,
                                                 const T* __restrict__ p, const T* __restrict__ q,
-                                                ColState cs, double* __restrict__ rzp, int ncols,
-                                                int cpb, int apply) {
+                                                ColState cs, double* __restrict__ rzp,
+                                                double* __restrict__ cp, int ncols, int cpb, int apply) {
     const int rows = blockDim.x / cpb;
     const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
     const int col = blockIdx.x * cpb + cl;
     const T a = apply ? (T)cs.alpha[col] : T(0);
+    const int m = rv.m;
     PartialSum<T> acc;
-    // a converged column keeps x and r; its partial stays zero
+    PartialSum<T> cacc[12];
+    // a converged column keeps x and r; its partials stay zero
     const int64_t i_end = (apply && !cs.active[col]) ? 0 : rv.n_rows;
     for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += (int64_t)gridDim.y * rows) {
         const int64_t idx = i * ncols + col;
@@ -638,22 +675,43 @@ __global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x
         }
         const T w = inv_diag(rv, i, col, ncols) * rv_;
         acc.add(rv_ * w);
+        if (m > 0) {
+            const int32_t sidx = rv.sup_of_row[i];
+            if (sidx >= 0) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k)
+                    if (k < m) cacc[k].add((T)rv.sup_coef[(int64_t)sidx * m + k] * w);
+            }
+        }
     }
     double accs[1] = {acc.value()};
     block_column_reduce<1>(accs, rzp, ncols, cpb, col);
+    if (m > 0 && cp) {
+        __shared__ double buf[256];
+        for (int k = 0; k < m; ++k) {
+            buf[threadIdx.x] = cacc[k].value();
+            __syncthreads();
+            if (rr == 0) {
+                double sacc = 0.0;
+                for (int qq = 0; qq < rows; ++qq) sacc += buf[qq * cpb + cl];
+                cp[((int64_t)blockIdx.y * m + k) * ncols + col] = sacc;
+            }
+            __syncthreads();
+        }
+    }
 }
 
 template <typename T>
 void launch_update(const RowView<T>& rv, T* x, T* r, const T* p, const T* q, ColState cs,
-                   double* rz_partial, bool apply_update, const Launch& L) {
+                   double* rz_partial, bool apply_update, const Launch& L, double* c_partial) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
-    k_update<T><<<grid, block, 0, L.stream>>>(rv, x, r, p, q, cs, rz_partial, L.ncols, L.cpb,
+    k_update<T><<<grid, block, 0, L.stream>>>(rv, x, r, p, q, cs, rz_partial, c_partial, L.ncols, L.cpb,
                                                apply_update ? 1 : 0);
 }
 template void launch_update<float>(const RowView<float>&, float*, float*, const float*, const float*,
-                                   ColState, double*, bool, const Launch&);
+                                   ColState, double*, bool, const Launch&, double*);
 template void launch_update<double>(const RowView<double>&, double*, double*, const double*,
-                                    const double*, ColState, double*, bool, const Launch&);
+                                    const double*, ColState, double*, bool, const Launch&, double*);
 
 // partial C M^-1 r over the constraint support (m <= 12 rows)
 template <typename T>
@@ -828,9 +886,10 @@ __global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, T* __restrict__ 
         if (m > 0) {
             const int32_t s = rv.sup_of_row[i];
             if (s >= 0) {
-                double corr = 0.0;
-                for (int k = 0; k < m; ++k) corr += rv.sup_coef[(int64_t)s * m + k] * cs.mu[(int64_t)k * ncols + col];
-                rr_ = (T)((double)rr_ - corr);
+                T corr = T(0);
+                for (int k = 0; k < m; ++k)
+                    corr = fma((T)rv.sup_coef[(int64_t)s * m + k], (T)cs.mu[(int64_t)k * ncols + col], corr);
+                rr_ -= corr;
                 r[idx] = rr_;   // residual reset: keeps r in the projected space
             }
         }
@@ -1065,6 +1124,25 @@ __global__ void k_scatter_results(int B, const int64_t* __restrict__ idx, const 
 void launch_scatter_results(int B, const int64_t* idx, const double* res, double* C, double* K, double* D,
                             int32_t* status, cudaStream_t s) {
     k_scatter_results<<<B, 64, 0, s>>>(B, idx, res, C, K, D, status);
+}
+
+// x[row][col] = src[row][map[col]]  (warm start from a previous batch's solution)
+__global__ void k_gather_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* __restrict__ map,
+                                 const double* __restrict__ src, double* __restrict__ x) {
+    const int64_t n = n_rows * ncols;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / ncols;
+        const int col = (int)(i % ncols);
+        x[i] = src[row * src_cols + map[col]];
+    }
+}
+
+void launch_gather_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* src,
+                           double* x, cudaStream_t s) {
+    int64_t b = (n_rows * ncols + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    k_gather_columns<<<(unsigned)b, 256, 0, s>>>(n_rows, ncols, src_cols, map, src, x);
 }
 
 // ---------------------------------------------------------- elementwise

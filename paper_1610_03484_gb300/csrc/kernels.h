@@ -95,9 +95,10 @@ void launch_column_scales(int nrve, const double* w, int apply_to_yarn, bool mec
 // PCG pieces
 template <typename T>
 void launch_finalize_alpha(const double* energy_partial, ColState cs, const Launch& L);
+// also accumulates the constraint products C M^-1 r into c_partial when given
 template <typename T>
 void launch_update(const RowView<T>& rv, T* x, T* r, const T* p, const T* q, ColState cs,
-                   double* rz_partial, bool apply_update, const Launch& L);
+                   double* rz_partial, bool apply_update, const Launch& L, double* c_partial = nullptr);
 template <typename T>
 void launch_constraint_dot(const RowView<T>& rv, const T* r, double* c_partial, const Launch& L);
 void launch_finalize_beta(int m, const double* rz_partial, const double* c_partial, ColState cs,
@@ -126,6 +127,9 @@ void launch_gather_states(int B, const int64_t* idx, const double* T, const doub
                           double* out, cudaStream_t s);
 void launch_scatter_results(int B, const int64_t* idx, const double* res, double* C, double* K, double* D,
                             int32_t* status, cudaStream_t s);
+
+void launch_gather_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* src,
+                           double* x, cudaStream_t s);
 
 // elementwise helpers
 void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);

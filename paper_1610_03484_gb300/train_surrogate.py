@@ -29,7 +29,7 @@ import rve_inputs as ri  # noqa: E402
 import paper_1610_03484_gb300 as rve  # noqa: E402
 
 DEFAULT_OUT = os.path.join(HERE, "surrogate_24x24x8_p2.npz")
-TAU = 2e-2          # ensemble-spread gate: larger spread -> fallback to the PCG solve
+TAU = 5e-3          # ensemble-spread gate: larger spread -> fallback to the PCG solve
 
 
 def rel_err(P, R):

@@ -1,0 +1,167 @@
+"""GPU surrogate: BF16 tensor-core gradients against the FP64 oracle, training
+on solves of the GPU solver, accuracy against held-out PCG solves, and what
+the network gains over the plain method (points answered without a solve)."""
+import time
+
+import numpy as np
+import pytest
+
+import rve_inputs as ri
+from oracle import surrogate as osg
+
+pytestmark = pytest.mark.gpu
+TAU = 5e-3          # ensemble-spread gate
+
+
+@pytest.fixture(scope="module")
+def rve():
+    import paper_1610_03484_gb300 as pkg
+    from paper_1610_03484_gb300 import _build
+    _build.build()
+    pkg.load_library()
+    return pkg
+
+
+def bf16(a):
+    """Round-to-nearest-even to bfloat16, returned as float64."""
+    a = np.asarray(a, np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def oracle_params(buf, member, nparam):
+    """Unpack one member from the get_params layout into oracle (W, b) pairs,
+    dropping the zero padding (8 of 64 inputs, 33 of 64 outputs)."""
+    p = buf[52 + member * nparam: 52 + (member + 1) * nparam]
+    dims = [(64, 256), (256, 256), (256, 256), (256, 256), (256, 64)]
+    out, o = [], 0
+    for l, (k, n) in enumerate(dims):
+        W = p[o:o + k * n].reshape(k, n).astype(np.float64)
+        o += k * n
+        b = p[o:o + n].astype(np.float64)
+        o += n
+        if l == 0:
+            W = W[:8]
+        if l == 4:
+            W, b = W[:, :33], b[:33]
+        out.append((W, b))
+    return out
+
+
+def test_gradients_match_fp64_oracle(rve):
+    with rve.Context() as ctx:
+        s = rve.Surrogate(ctx, members=1, seed=3)
+        rng = np.random.default_rng(0)
+        n = 128
+        feat = rng.normal(size=(n, 8))
+        target = (rng.normal(size=(n, 33)) * 0.5 + 1.0).astype(np.float32)
+        g_gpu, loss_gpu = s.gradients(0, feat, target)
+        buf = s.get_params()
+        nparam = (len(buf) - 52)
+        params = oracle_params(buf, 0, nparam)
+        # the GPU multiplies BF16 weights and BF16 activations: give the oracle the same weights and inputs
+        params_bf = [(bf16(W), b) for W, b in params]
+        loss_ref, g_ref = osg.loss_and_grads(params_bf, bf16(feat), target.astype(np.float64), np.ones(33))
+        assert abs(loss_gpu - loss_ref) / loss_ref < 1e-2
+        g_ref_flat = []
+        dims = [(64, 256), (256, 256), (256, 256), (256, 256), (256, 64)]
+        for l, ((gW, gb), (k, n_)) in enumerate(zip(g_ref, dims)):
+            W = np.zeros((k, n_))
+            b = np.zeros(n_)
+            W[:gW.shape[0], :gW.shape[1]] = gW
+            b[:gb.shape[0]] = gb
+            g_ref_flat += [W.ravel(), b]
+        g_ref_flat = np.concatenate(g_ref_flat)
+        o = 0
+        for k, n_ in dims:
+            gw = g_gpu[o:o + k * n_]
+            rw = g_ref_flat[o:o + k * n_]
+            assert np.linalg.norm(gw - rw) / np.linalg.norm(rw) < 2e-2
+            o += k * n_
+            gb_ = g_gpu[o:o + n_]
+            rb = g_ref_flat[o:o + n_]
+            assert np.linalg.norm(gb_ - rb) / np.linalg.norm(rb) < 2e-2
+            o += n_
+        s.free()
+
+
+@pytest.fixture(scope="module")
+def trained(rve):
+    grid, p = (6, 6, 4), 1
+    xyz, tets, phase, tangent = ri.weave_rve(*grid)
+    ctx = rve.Context(precision=rve.PREC_MIXED, rtol=1e-7, inner_rtol=1e-6)
+    mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
+    mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+    mesh.set_bc(rve.BC_PERIODIC)
+    T, c, t, _, _ = ri.gauss_point_states(1024 + 256, seed=3)
+    mid = np.zeros(len(T), np.int32)
+    t0 = time.perf_counter()
+    Cg, Kg, Dg, st, stats, rc = ctx.macro_update([mesh], T, c, t, mid)
+    pcg_s = time.perf_counter() - t0
+    assert (st == 0).all()
+    feat = ctx.features(mesh, T, c, t)
+    s = rve.Surrogate(ctx, members=4, seed=11)
+    hist = s.train(feat[:1024], Cg[:1024], Kg[:1024], Dg[:1024], epochs=300, batch=128, lr=2e-3, seed=1)
+    yield dict(ctx=ctx, mesh=mesh, s=s, T=T, c=c, t=t, C=Cg, K=Kg, D=Dg, feat=feat, hist=hist, pcg_s=pcg_s)
+    s.free()
+    mesh.free()
+    ctx.close()
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).reshape(len(a), -1), axis=1) / np.linalg.norm(b.reshape(len(b), -1), axis=1)
+
+
+def test_training_converges(trained):
+    h = trained["hist"]
+    assert h[-1] < 0.05 * h[0]
+
+
+def test_heldout_accuracy_and_spd(trained):
+    s, f = trained["s"], trained["feat"][1024:]
+    Cp, Kp, Dp, spread = s.predict(f)
+    for P, R in ((Cp, trained["C"][1024:]), (Kp, trained["K"][1024:]), (Dp, trained["D"][1024:])):
+        assert np.median(rel(P, R)) < 5e-3
+        assert np.linalg.eigvalsh(P).min() > 0
+    gated = spread <= TAU
+    assert gated.mean() > 0.5
+    for P, R in ((Cp, trained["C"][1024:]), (Kp, trained["K"][1024:]), (Dp, trained["D"][1024:])):
+        assert rel(P[gated], R[gated]).max() < 1e-2
+
+
+def test_surrogate_with_fallback_gains_over_plain_pcg(rve, trained):
+    """What the network gains: held-out points are answered within 1e-2 of
+    the PCG solve while only the gated-out points are solved, in less time."""
+    ctx, mesh, s = trained["ctx"], trained["mesh"], trained["s"]
+    sl = slice(1024, None)
+    T, c, t = trained["T"][sl], trained["c"][sl], trained["t"][sl]
+    mid = np.zeros(len(T), np.int32)
+    t0 = time.perf_counter()
+    Cs, Ks, Ds, st, fb, stats, rc = ctx.macro_update_surrogate([mesh], [s], TAU, T, c, t, mid)
+    sur_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.macro_update([mesh], T, c, t, mid)
+    pcg_s = time.perf_counter() - t0
+    assert (st == 0).all()
+    assert fb.mean() < 0.5
+    for P, R in ((Cs, trained["C"][sl]), (Ks, trained["K"][sl]), (Ds, trained["D"][sl])):
+        assert rel(P, R).max() < 1e-2
+    # fallback points are exact PCG solves
+    if fb.any():
+        assert rel(Cs[fb == 1], trained["C"][sl][fb == 1]).max() < 1e-6
+    assert sur_s < pcg_s
+
+
+def test_save_load_round_trip(rve, trained):
+    ctx, s = trained["ctx"], trained["s"]
+    buf = s.get_params()
+    s2 = rve.Surrogate(ctx, members=4, seed=99)
+    s2.set_params(buf)
+    f = trained["feat"][:64]
+    a = s.predict(f)
+    b = s2.predict(f)
+    # weights round-trip exactly; the saved normalisation scales are FP32
+    np.testing.assert_allclose(a[0], b[0], rtol=1e-6)
+    np.testing.assert_allclose(a[3], b[3], rtol=1e-6, atol=1e-9)
+    s2.free()
