@@ -43,6 +43,9 @@ INNER_RTOL = 5e-6    # FP32 inner PCG tolerance per refinement sweep
 # dram read + write bytes per operator launch from the ncu capture in profiles/ (None until
 # the kernel's current version has been captured)
 TRAFFIC_PER_LAUNCH = None
+# one ncu capture of the current operator (profiles/k_operator_p2_mech_f32_32x32x10_b8.md)
+TRAFFIC_CAPTURE = {"case": "k_operator<2,3,float>, 32x32x10 p=2, 8 RVEs (48 columns)",
+                   "dram_bytes": 115.87e6, "algorithmic_bytes": 112.3e6, "ratio": 1.03}
 
 
 def parse():
@@ -54,6 +57,8 @@ def parse():
     ap.add_argument("--points", type=int, default=G_POINTS)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-points", type=int, default=1 << 20)
     return ap.parse_args()
 
 
@@ -268,6 +273,8 @@ def run_ours(args, world, rank, local):
         result["roofline"] = roofline(op_ms, op_n, op_bytes, op_flops, pk, pk_kind, clk)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_baseline(budget_s=20.0)
+    if not args.no_surrogate:
+        result["surrogate"] = surrogate_leg(ctx, rve, args.surrogate_points, rank)
     for m in meshes:
         m.free()
     ctx.close()
@@ -288,7 +295,7 @@ def roofline(op_ms, op_n, op_bytes, op_flops, pk, pk_kind, clk):
     out = {"kernel": "k_operator (all classes, FP32 inner solves)", "launches": op_n,
            "how": "one extra step of the same workload after the timed ones, every operator launch "
                   "bracketed by CUDA events on its stream; bytes and flops are algorithmic",
-           "mean_launch_ms": t * 1e3, "traffic": TRAFFIC_PER_LAUNCH,
+           "mean_launch_ms": t * 1e3, "traffic": TRAFFIC_PER_LAUNCH, "traffic_capture": TRAFFIC_CAPTURE,
            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
                    "peak_kind": f"{pk_kind} (MEASURED_PEAKS.json copy bandwidth)"},
            "alu": {"achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu_frac,
@@ -299,6 +306,53 @@ def roofline(op_ms, op_n, op_bytes, op_flops, pk, pk_kind, clk):
     else:
         out.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac})
     return out
+
+
+# ------------------------------------------------------------ surrogate leg
+SURROGATE_FILE = os.path.join(ROOT, "paper_1610_03484_gb300", "surrogate_24x24x8_p2.npz")
+SURROGATE_TAU = 5e-3
+
+
+def surrogate_leg(ctx, rve, n_points, rank):
+    """Surrogate + fallback against plain batched PCG on the surrogate's RVE class
+    (24x24x8, p = 2, periodic): n_points Gauss points (seed 5 + rank) through
+    macro_update_gauss_points_surrogate; the error is judged on a sample solved
+    by the plain PCG, and the plain PCG rate on that class is measured beside it."""
+    if not os.path.exists(SURROGATE_FILE):
+        return {"unavailable": "no trained surrogate weights in the package"}
+    import time as _t
+    z = np.load(SURROGATE_FILE)
+    s = rve.Surrogate(ctx, members=int(z["members"]), seed=0)
+    s.set_params(z["params"])
+    xyz, tets, phase, tangent = ri.weave_rve(24, 24, 8)
+    mesh = ctx.mesh_load(xyz, tets, 2, phase, tangent)
+    mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+    mesh.set_bc(rve.BC_PERIODIC)
+    T, c, t, _, _ = ri.gauss_point_states(n_points, 5 + rank)
+    mid = np.zeros(n_points, np.int32)
+    ctx.macro_update_surrogate([mesh], [s], SURROGATE_TAU, T[:4096], c[:4096], t[:4096], mid[:4096])  # warm-up
+    t0 = _t.perf_counter()
+    Cs, Ks, Ds, st, fb, stats, rc = ctx.macro_update_surrogate([mesh], [s], SURROGATE_TAU, T, c, t, mid)
+    sur_s = _t.perf_counter() - t0
+    # plain batched PCG on a sample of the same points: rate and the error reference
+    ns = 256
+    t0 = _t.perf_counter()
+    Cp, Kp, Dp, stp, _, _ = ctx.macro_update([mesh], T[:ns], c[:ns], t[:ns], mid[:ns])
+    pcg_s = _t.perf_counter() - t0
+
+    def rel(a, b):
+        a = a.reshape(len(a), -1)
+        b = b.reshape(len(b), -1)
+        return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    err = max(rel(Cs[:ns], Cp).max(), rel(Ks[:ns], Kp).max(), rel(Ds[:ns], Dp).max())
+    mesh.free()
+    s.free()
+    return {"value": n_points / sur_s, "unit": UNIT, "points": n_points, "seconds": sur_s,
+            "fallback_frac": float(fb.mean()), "status_ok": int((st == 0).sum()), "gate_tau": SURROGATE_TAU,
+            "max_rel_err_vs_pcg": float(err), "err_sample": ns,
+            "pcg_same_class": {"value": ns / pcg_s, "unit": UNIT, "sample": ns},
+            "workload": "24x24x8 p=2 plain weave, periodic; 4-member BF16 MLP ensemble (8 -> 4x256 SiLU -> 33), "
+                        "spread gate -> batched mixed-precision PCG fallback; timed through the host-buffer call"}
 
 
 # ------------------------------------------------------------------ CPU oracle

@@ -37,6 +37,7 @@ int check_ctx(rve_ctx c) {
 }  // namespace rve
 
 namespace {
+int table_nonzeros(int p);
 
 // ------------------------------------------------------------ geometry + map
 int rebuild_map(rve_mesh m) {
@@ -81,7 +82,11 @@ int build_constraints(rve_mesh m, FieldDev& f, const std::vector<double>& geo) {
     RVE_TRY(upload(f.mask, mask.data(), mask.size(), s));
     f.m = 0;
     f.n_sup = 0;
-    if (m->bc == RVE_BC_DIRICHLET) return RVE_OK;
+    // Periodic: the folded (torus) problem is singular only by rigid translations,
+    // to which the right-hand side is orthogonal; PCG on this consistent system
+    // converges without a projection, and translations change no strain, so no
+    // constraint rows are needed.  Dirichlet: the mask is the whole constraint.
+    if (m->bc == RVE_BC_DIRICHLET || m->bc == RVE_BC_PERIODIC) return RVE_OK;
 
     // vertex coordinates relative to the centroid (rotation rows)
     double cen[3] = {0, 0, 0};
@@ -412,7 +417,10 @@ struct Solver {
                 const double sz = sizeof(T);
                 const double bytes = 2.0 * n_rows * ncols * sz +
                                      (double)m->nt * (4.0 * ne + 10 * sz + (nc == 3 ? 21 : 6) * sz + 1);
-                const double fma = 2.0 * (ne - 4) * nmod * 3 * nc + nmod * (18.0 * nc + (nc == 3 ? 36 : 9));
+                // FMAs per element and column: forward and backward contractions with the
+                // non-zero entries of the edge/face table, plus per-mode gradient, stress
+                // and back-mapping
+                const double fma = 2.0 * table_nonzeros(m->p) * nc + nmod * (18.0 * nc + (nc == 3 ? 36 : 9));
                 const double flops = 2.0 * fma * (double)m->nt * ncols;
                 for (int k = 0; k < check; ++k) {
                     float ms = 0;
@@ -567,6 +575,17 @@ struct Solver {
         return RVE_OK;
     }
 };
+
+// Non-zero entries of the edge/face part (j >= 4) of the basis table of order p.
+int table_nonzeros(int p) {
+    const Basis& B = basis(p);
+    int n = 0;
+    for (int k = 0; k < 3; ++k)
+        for (int mm = 0; mm < B.nm; ++mm)
+            for (int j = 4; j < B.ne; ++j)
+                if (std::fabs(B.A[(k * B.nm + mm) * B.ne + j]) >= 1e-14) ++n;
+    return n;
+}
 
 double rel_fro(const double* a, const double* b, int n) {
     double num = 0, den = 0;
