@@ -228,8 +228,13 @@ def run_ours(args, world, rank, local):
     ctx.set_options(profile=1)
     flush.fill_(1.0)
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     st = step()
+    e1.record(stream)
     torch.cuda.synchronize()
+    prof_step_ms = e0.elapsed_time(e1)
     ctx.set_options(profile=0)
     op_ms, op_n, op_bytes, op_flops = st["op_ms"], st["op_launches"], st["op_bytes"], st["op_flops"]
     local_s = sum(times) / 1000.0
@@ -270,7 +275,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": None,
     }
     if op_n > 0:
-        result["roofline"] = roofline(op_ms, op_n, op_bytes, op_flops, pk, pk_kind, clk)
+        result["roofline"] = roofline(st, prof_step_ms, pk, pk_kind, clk)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_baseline(budget_s=20.0)
     if not args.no_surrogate:
@@ -281,30 +286,44 @@ def run_ours(args, world, rank, local):
     return result
 
 
-def roofline(op_ms, op_n, op_bytes, op_flops, pk, pk_kind, clk):
-    """Roofline of the dominant kernel (the matrix-free operator) over every
-    launch in the timed region: algorithmic bytes and flops per launch divided
-    by the mean CUDA-event duration of a launch."""
-    t = op_ms / 1e3 / op_n
-    gbs = op_bytes / op_n / t / 1e9
-    tfs = op_flops / op_n / t / 1e12
+def roofline(st, step_ms, pk, pk_kind, clk):
+    """Roofline of the step's kernels from one profiled step of the same workload:
+    every launch of the PCG iteration is bracketed by CUDA events on its stream
+    and its algorithmic bytes (and, for the operator, flops) are counted by the
+    library.  The dominant kernel (largest share of the step) fills the
+    top-level fields."""
+    n = st["op_launches"]
     hbm_peak = pk["hbm_gbs"]
     mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12      # FP32 CUDA-core FMA peak at the sampled clock
-    hbm_frac, alu_frac = gbs / hbm_peak, tfs / fp32_peak
-    out = {"kernel": "k_operator (all classes, FP32 inner solves)", "launches": op_n,
-           "how": "one extra step of the same workload after the timed ones, every operator launch "
+    op_s = st["op_ms"] / 1e3
+    op = {"launches": n, "mean_launch_ms": st["op_ms"] / n, "share_of_step": st["op_ms"] / step_ms,
+          "hbm_gbs": st["op_bytes"] / op_s / 1e9, "hbm_frac": st["op_bytes"] / op_s / 1e9 / hbm_peak,
+          "tflops": st["op_flops"] / op_s / 1e12, "alu_frac": st["op_flops"] / op_s / 1e12 / fp32_peak,
+          "bytes_per_launch": st["op_bytes"] / n, "flops_per_launch": st["op_flops"] / n}
+    vec = {}
+    for name, ms, by in (("k_update", st["update_ms"], st["update_bytes"]),
+                         ("k_pupdate", st["pupdate_ms"], st["pupdate_bytes"])):
+        vec[name] = {"launches": n, "mean_launch_ms": ms / n, "share_of_step": ms / step_ms,
+                     "hbm_gbs": by / (ms / 1e3) / 1e9, "hbm_frac": by / (ms / 1e3) / 1e9 / hbm_peak,
+                     "bytes_per_launch": by / n}
+    kernels = {"k_operator": op, **vec,
+               "finalize (alpha, beta)": {"share_of_step": st["finalize_ms"] / step_ms}}
+    dom = max(("k_operator", "k_update", "k_pupdate"), key=lambda k: kernels[k]["share_of_step"])
+    out = {"how": "one extra step of the same workload after the timed ones, every PCG-iteration launch "
                   "bracketed by CUDA events on its stream; bytes and flops are algorithmic",
-           "mean_launch_ms": t * 1e3, "traffic": TRAFFIC_PER_LAUNCH, "traffic_capture": TRAFFIC_CAPTURE,
-           "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
-                   "peak_kind": f"{pk_kind} (MEASURED_PEAKS.json copy bandwidth)"},
-           "alu": {"achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu_frac,
-                   "peak_kind": f"derived: 152 SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled median)"},
-           "bytes_per_launch": op_bytes / op_n, "flops_per_launch": op_flops / op_n}
-    if alu_frac >= hbm_frac:
-        out.update({"bound": "alu", "achieved": tfs, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu_frac})
+           "profiled_step_ms": step_ms, "kernels": kernels, "kernel": dom,
+           "traffic": TRAFFIC_PER_LAUNCH, "traffic_capture": TRAFFIC_CAPTURE,
+           "peaks": {"hbm_gbs": hbm_peak, "hbm_kind": f"{pk_kind} (MEASURED_PEAKS.json copy bandwidth)",
+                     "fp32_tflops": fp32_peak,
+                     "fp32_kind": f"derived: 152 SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled median)"}}
+    k = kernels[dom]
+    if dom == "k_operator" and op["alu_frac"] >= op["hbm_frac"]:
+        out.update({"bound": "alu", "achieved": op["tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": op["alu_frac"]})
     else:
-        out.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac})
+        out.update({"bound": "hbm", "achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": k["hbm_frac"]})
     return out
 
 

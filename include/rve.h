@@ -131,6 +131,10 @@ typedef struct rve_stats {
     double  op_bytes;             /* algorithmic bytes of those launches: x read + y written
                                      (2 n_rows ncols sizeof(real)) + element data once */
     double  op_flops;             /* algorithmic flops of those launches (FMA = 2) */
+    /* profile mode, the PCG vector kernels of the same iterations: */
+    double  update_ms, update_bytes;     /* x, r read+written, p, q read (6 n_rows ncols s) */
+    double  pupdate_ms, pupdate_bytes;   /* r, p read, p, q written (4 n_rows ncols s) */
+    double  finalize_ms;                 /* alpha and beta/multiplier kernels */
 } rve_stats;
 
 /* ------------------------------------------------------------------ calls */

@@ -64,7 +64,9 @@ class Stats(C.Structure):
                 ("rel_residual_mech", C.c_double), ("rel_residual_scalar", C.c_double),
                 ("hill_mandel_mech", C.c_double), ("hill_mandel_scalar", C.c_double),
                 ("seconds", C.c_double), ("kernel_launches", C.c_int64), ("op_ms", C.c_double),
-                ("op_launches", C.c_int64), ("op_bytes", C.c_double), ("op_flops", C.c_double)]
+                ("op_launches", C.c_int64), ("op_bytes", C.c_double), ("op_flops", C.c_double),
+                ("update_ms", C.c_double), ("update_bytes", C.c_double), ("pupdate_ms", C.c_double),
+                ("pupdate_bytes", C.c_double), ("finalize_ms", C.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -364,22 +364,31 @@ struct Solver {
         // capture stream) and replayed on the context stream until every column
         // has converged; the host reads the convergence flags between replays.
         const bool prof = m->ctx->opt.profile != 0;
-        if (prof && (int)m->ctx->ev.size() < 2 * check) {
-            for (int k = (int)m->ctx->ev.size(); k < 2 * check; ++k) {
+        // profile mode: 6 events per iteration bracket operator, alpha, update,
+        // beta and p-update launches
+        if (prof && (int)m->ctx->ev.size() < 6 * check) {
+            for (int k = (int)m->ctx->ev.size(); k < 6 * check; ++k) {
                 cudaEvent_t e;
                 RVE_CUDA(cudaEventCreate(&e));
                 m->ctx->ev.push_back(e);
             }
         }
+        auto evr = [&](int k, int i, cudaStream_t st) {
+            if (prof) cudaEventRecord(m->ctx->ev[6 * k + i], st);
+        };
         auto body = [&](const Launch& Lx) {
             for (int k = 0; k < check; ++k) {
-                if (prof) cudaEventRecord(m->ctx->ev[2 * k], Lx.stream);
+                evr(k, 0, Lx.stream);
                 launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active);
-                if (prof) cudaEventRecord(m->ctx->ev[2 * k + 1], Lx.stream);
+                evr(k, 1, Lx.stream);
                 launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
+                evr(k, 2, Lx.stream);
                 launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx, m->cpart.as<double>());
+                evr(k, 3, Lx.stream);
                 launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, Lx);
+                evr(k, 4, Lx.stream);
                 launch_pupdate<T>(rvw, r, p, q, cs, false, Lx);
+                evr(k, 5, Lx.stream);
             }
         };
         // Profile mode launches the body directly on the context stream so that
@@ -422,14 +431,22 @@ struct Solver {
                 // and back-mapping
                 const double fma = 2.0 * table_nonzeros(m->p) * nc + nmod * (18.0 * nc + (nc == 3 ? 36 : 9));
                 const double flops = 2.0 * fma * (double)m->nt * ncols;
-                for (int k = 0; k < check; ++k) {
+                const double vb = (double)n_rows * ncols * sz;
+                auto el = [&](int k, int a2, int b2) {
                     float ms = 0;
-                    if (cudaEventElapsedTime(&ms, m->ctx->ev[2 * k], m->ctx->ev[2 * k + 1]) == cudaSuccess) {
-                        m->ctx->op_ms += ms;
-                        m->ctx->op_launches++;
-                        m->ctx->op_bytes += bytes;
-                        m->ctx->op_flops += flops;
-                    }
+                    return cudaEventElapsedTime(&ms, m->ctx->ev[6 * k + a2], m->ctx->ev[6 * k + b2]) == cudaSuccess
+                               ? (double)ms : 0.0;
+                };
+                for (int k = 0; k < check; ++k) {
+                    m->ctx->op_ms += el(k, 0, 1);
+                    m->ctx->op_launches++;
+                    m->ctx->op_bytes += bytes;
+                    m->ctx->op_flops += flops;
+                    m->ctx->fin_ms += el(k, 1, 2) + el(k, 3, 4);
+                    m->ctx->upd_ms += el(k, 2, 3);
+                    m->ctx->upd_bytes += 6 * vb;
+                    m->ctx->pup_ms += el(k, 4, 5);
+                    m->ctx->pup_bytes += 4 * vb;
                 }
             }
             bool any = false;
@@ -1006,6 +1023,7 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
     launch_degradation(1, d, d + 1, d + 2, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, d + 3, s);
     c->launches++;
     const double op0 = c->op_ms, ob0 = c->op_bytes, of0 = c->op_flops;
+    const double u0 = c->upd_ms, ub0 = c->upd_bytes, pu0 = c->pup_ms, pb0 = c->pup_bytes, f0 = c->fin_ms;
     const int64_t on0 = c->op_launches;
     int rc = homogenise_batch(m, 1, d + 3, C, K, D, st);
     RVE_CUDA(cudaStreamSynchronize(s));
@@ -1016,6 +1034,11 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
         st->op_launches = c->op_launches - on0;
         st->op_bytes = c->op_bytes - ob0;
         st->op_flops = c->op_flops - of0;
+        st->update_ms = c->upd_ms - u0;
+        st->update_bytes = c->upd_bytes - ub0;
+        st->pupdate_ms = c->pup_ms - pu0;
+        st->pupdate_bytes = c->pup_bytes - pb0;
+        st->finalize_ms = c->fin_ms - f0;
     }
     return rc;
 }
@@ -1139,6 +1162,7 @@ int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshe
         st->converged = 1;
     }
     const double op0 = c->op_ms, ob0 = c->op_bytes, of0 = c->op_flops;
+    const double u0 = c->upd_ms, ub0 = c->upd_bytes, pu0 = c->pup_ms, pb0 = c->pup_bytes, f0 = c->fin_ms;
     const int64_t on0 = c->op_launches;
     int rc = macro_update_impl(c, meshes, n_meshes, G, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev,
                                D_dev, status_dev, st);
@@ -1150,6 +1174,11 @@ int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshe
         st->op_launches = c->op_launches - on0;
         st->op_bytes = c->op_bytes - ob0;
         st->op_flops = c->op_flops - of0;
+        st->update_ms = c->upd_ms - u0;
+        st->update_bytes = c->upd_bytes - ub0;
+        st->pupdate_ms = c->pup_ms - pu0;
+        st->pupdate_bytes = c->pup_bytes - pb0;
+        st->finalize_ms = c->fin_ms - f0;
     }
     return rc;
 }

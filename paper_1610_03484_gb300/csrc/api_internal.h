@@ -105,6 +105,7 @@ struct rve_ctx_s {
     double op_ms = 0;
     int64_t op_launches = 0;
     double op_bytes = 0, op_flops = 0;
+    double upd_ms = 0, upd_bytes = 0, pup_ms = 0, pup_bytes = 0, fin_ms = 0;
     ~rve_ctx_s() {
         for (auto e : ev) cudaEventDestroy(e);
     }
