@@ -75,9 +75,11 @@ typedef struct rve_options {
     int     batch;           /* RVEs solved together in macro_update_gauss_points, 0 = auto */
     void*   stream;          /* cudaStream_t to run on; NULL = library-created stream */
     int     profile;         /* 1: time every operator launch with CUDA events (rve_stats.op_*) */
-    int     warm_start;      /* macro_update_gauss_points: 1 (default) solves each mesh's points in
-                                order of their degradation factor and starts every batch from the
-                                nearest solutions of the previous batch of the same call */
+    int     warm_start;      /* macro_update_gauss_points: >0 solves each mesh's points in order of
+                                their degradation factor and starts every batch from the previous
+                                batch of the same call: 1 the nearest solution, 2 (default) the
+                                line and 3 the parabola in the factor through 2 or 3 of them;
+                                0 starts every batch from zero */
 } rve_options;
 
 /* Isotropic matrix phase (Sec. 1, Sec. 7). */
@@ -135,6 +137,10 @@ typedef struct rve_stats {
     double  update_ms, update_bytes;     /* x, r read+written, p, q read (6 n_rows ncols s) */
     double  pupdate_ms, pupdate_bytes;   /* r, p read, p, q written (4 n_rows ncols s) */
     double  finalize_ms;                 /* alpha and beta/multiplier kernels */
+    /* profile mode, outside the PCG iterations: */
+    double  residual_ms;                 /* FP64 true residual r = b - K x (operator + sign) */
+    int64_t residual_launches;           /* FP64 operator applications counted in residual_ms */
+    double  op_active_frac;              /* active columns / columns, averaged over operator launches */
 } rve_stats;
 
 /* ------------------------------------------------------------------ calls */

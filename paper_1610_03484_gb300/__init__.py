@@ -66,7 +66,9 @@ class Stats(C.Structure):
                 ("seconds", C.c_double), ("kernel_launches", C.c_int64), ("op_ms", C.c_double),
                 ("op_launches", C.c_int64), ("op_bytes", C.c_double), ("op_flops", C.c_double),
                 ("update_ms", C.c_double), ("update_bytes", C.c_double), ("pupdate_ms", C.c_double),
-                ("pupdate_bytes", C.c_double), ("finalize_ms", C.c_double)]
+                ("pupdate_bytes", C.c_double), ("finalize_ms", C.c_double),
+                ("residual_ms", C.c_double), ("residual_launches", C.c_int64),
+                ("op_active_frac", C.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -177,14 +179,14 @@ class Context:
 
     def __init__(self, precision=PREC_FP64, rtol=1e-10, max_iter=20000, inner_rtol=1e-6,
                  max_refine=4, check_every=16, batch=0, stream=None, device=0, profile=False,
-                 warm_start=True):
+                 warm_start=2):
         lib = load_library()
         o = default_options()
         o.device, o.precision, o.rtol, o.max_iter = device, precision, rtol, max_iter
         o.inner_rtol, o.max_refine, o.check_every, o.batch = inner_rtol, max_refine, check_every, batch
         o.stream = stream
         o.profile = int(profile)
-        o.warm_start = int(warm_start)
+        o.warm_start = (2 if warm_start else 0) if isinstance(warm_start, bool) else int(warm_start)
         h = C.c_void_p()
         _check(lib.rve_create(C.byref(h), C.byref(o)), "rve_create")
         self.h = h

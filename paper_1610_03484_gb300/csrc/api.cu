@@ -245,6 +245,26 @@ struct SolveOut {
     bool numeric = false;
 };
 
+// Starting data for a warm-started batch: the previous batch's solutions u_k
+// (factors w_k) and, in mixed precision, their final projected FP64 residuals r_k.
+// Column c starts from x0 = sum_k c_k u_k; because the modulus of the degrading
+// phases is linear in w, its residual is
+//   b(w) - K(w) x0 = sum_k c_k r_k - K_deg v - alpha K_deg u_macro,
+//   v = sum_k c_k (w - w_k) u_k,   alpha = sum_k c_k (w - w_k),
+// where K_deg is the operator over the degrading phases at unit modulus.  v is
+// small (|w - w_k| |u|), so K_deg v is accurate in FP32; alpha is zero whenever
+// the weights reproduce lines (two or three sources).
+struct WarmStart {
+    const double* x = nullptr;      // [n_rows][cols] previous solutions
+    const double* r = nullptr;      // [n_rows][cols] their residuals (nullptr: recompute in FP64)
+    int cols = 0;
+    const int32_t* map = nullptr;   // [ncols][WARM_SOURCES] source columns
+    const double* coef = nullptr;   // [ncols][WARM_SOURCES] c_k
+    const double* dcoef = nullptr;  // [ncols][WARM_SOURCES] c_k (w - w_k)
+    std::vector<double> alpha;      // [ncols]
+    double degrade[2] = {0, 0};     // 1 for a phase whose modulus is proportional to w
+};
+
 struct Solver {
     rve_mesh m;
     FieldDev& f;
@@ -337,17 +357,36 @@ struct Solver {
 
     // y = -(K x + macro)  (FP64): the fluctuation residual b - K x
     int residual64(const double* x, double* y) {
+        const bool prof = m->ctx->opt.profile != 0;
+        auto& evs = m->ctx->ev;
+        while (prof && evs.size() < 2) {
+            cudaEvent_t e;
+            RVE_CUDA(cudaEventCreate(&e));
+            evs.push_back(e);
+        }
+        if (prof) RVE_CUDA(cudaEventRecord(evs[0], s));
         RVE_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n_rows * ncols, s));
         launch_operator<double>(m->p, f.nc, true, ev<double>(m->scale64), x, y, nullptr, L);
         launch_neg(n_rows * ncols, y, s);
         *launches += 2;
+        if (prof) {
+            RVE_CUDA(cudaEventRecord(evs[1], s));
+            RVE_CUDA(cudaEventSynchronize(evs[1]));
+            float ms = 0;
+            RVE_CUDA(cudaEventElapsedTime(&ms, evs[0], evs[1]));
+            m->ctx->res_ms += ms;
+            m->ctx->res_launches++;
+        }
         return RVE_OK;
     }
 
     template <typename T>
     int pcg(T* x, T* r, T* p, T* q, const DevBuf& scale, double tol, int max_iter, int& iters_out,
             bool& conv) {
-        const int check = std::max(1, m->ctx->opt.check_every);
+        // profile mode launches one iteration at a time so that the byte and flop
+        // counts follow the set of columns still iterating
+        const bool prof = m->ctx->opt.profile != 0;
+        const int check = prof ? 1 : std::max(1, m->ctx->opt.check_every);
         ColState cs = cs64;
         cs.tol = tol;
         RowView<T> rvw = rv<T>(scale);
@@ -360,10 +399,19 @@ struct Solver {
         std::vector<int32_t> act(ncols);
         int it = 0;
         conv = false;
+        int n_act = ncols;
+        auto read_active = [&]() -> int {
+            RVE_CUDA(cudaMemcpyAsync(act.data(), cs.active, sizeof(int32_t) * ncols,
+                                     cudaMemcpyDeviceToHost, s));
+            RVE_CUDA(cudaStreamSynchronize(s));
+            n_act = 0;
+            for (int c = 0; c < ncols; ++c) n_act += act[c] != 0;
+            return RVE_OK;
+        };
+        if (prof) RVE_TRY(read_active());
         // `check` iterations are captured once into a CUDA graph (on the private
         // capture stream) and replayed on the context stream until every column
         // has converged; the host reads the convergence flags between replays.
-        const bool prof = m->ctx->opt.profile != 0;
         // profile mode: 6 events per iteration bracket operator, alpha, update,
         // beta and p-update launches
         if (prof && (int)m->ctx->ev.size() < 6 * check) {
@@ -417,21 +465,22 @@ struct Solver {
             it += check;
             *launches += (int64_t)check * 5;
             RVE_CUDA(cudaGetLastError());
-            RVE_CUDA(cudaMemcpyAsync(act.data(), cs.active, sizeof(int32_t) * ncols,
-                                     cudaMemcpyDeviceToHost, s));
-            RVE_CUDA(cudaStreamSynchronize(s));
+            const int n_act_run = n_act;    // columns the iteration just run worked on
+            RVE_TRY(read_active());
             if (prof) {
-                // algorithmic bytes / flops of one operator launch of this solve
+                // algorithmic bytes / flops of one operator launch of this solve:
+                // vectors and flops of the columns still active, element data once
                 const int ne = n_local(m->p), nmod = n_modes(m->p), nc = f.nc;
                 const double sz = sizeof(T);
-                const double bytes = 2.0 * n_rows * ncols * sz +
+                const int na = n_act_run;
+                const double bytes = 2.0 * n_rows * na * sz +
                                      (double)m->nt * (4.0 * ne + 10 * sz + (nc == 3 ? 21 : 6) * sz + 1);
                 // FMAs per element and column: forward and backward contractions with the
                 // non-zero entries of the edge/face table, plus per-mode gradient, stress
                 // and back-mapping
                 const double fma = 2.0 * table_nonzeros(m->p) * nc + nmod * (18.0 * nc + (nc == 3 ? 36 : 9));
-                const double flops = 2.0 * fma * (double)m->nt * ncols;
-                const double vb = (double)n_rows * ncols * sz;
+                const double flops = 2.0 * fma * (double)m->nt * na;
+                const double vb = (double)n_rows * na * sz;
                 auto el = [&](int k, int a2, int b2) {
                     float ms = 0;
                     return cudaEventElapsedTime(&ms, m->ctx->ev[6 * k + a2], m->ctx->ev[6 * k + b2]) == cudaSuccess
@@ -442,6 +491,8 @@ struct Solver {
                     m->ctx->op_launches++;
                     m->ctx->op_bytes += bytes;
                     m->ctx->op_flops += flops;
+                    m->ctx->op_cols += na;
+                    m->ctx->op_cols_all += ncols;
                     m->ctx->fin_ms += el(k, 1, 2) + el(k, 3, 4);
                     m->ctx->upd_ms += el(k, 2, 3);
                     m->ctx->upd_bytes += 6 * vb;
@@ -449,9 +500,7 @@ struct Solver {
                     m->ctx->pup_bytes += 4 * vb;
                 }
             }
-            bool any = false;
-            for (int c = 0; c < ncols; ++c) any |= act[c] != 0;
-            if (!any) {
+            if (n_act == 0) {
                 conv = true;
                 break;
             }
@@ -490,10 +539,8 @@ struct Solver {
         return RVE_OK;
     }
 
-    // warm: optional previous solutions [n_rows][warm_cols] (FP64) and the
-    // device column map choosing, for each column, its starting column there.
-    int run(int precision, SolveOut& out, const double* warm = nullptr, int warm_cols = 0,
-            const int32_t* warm_map = nullptr) {
+    // warm: optional starting data from the previous batch (see WarmStart).
+    int run(int precision, SolveOut& out, const WarmStart* warm = nullptr) {
         const rve_options& o = m->ctx->opt;
         const bool mixed = precision == RVE_PREC_MIXED;
         RVE_TRY(alloc(mixed));
@@ -510,18 +557,76 @@ struct Solver {
             std::vector<double> ones(ncols, 1.0);
             RVE_TRY(rel_residual(r64, ones, dummy, &bn));
         }
+        // A column whose projected right-hand side is rounding noise (a single-phase
+        // RVE, whose exact fluctuation is zero) is solved by u = 0: its (b, P b)
+        // is compared with the Voigt energy scale V <D>_jj of its unit load.
+        std::vector<int> zero_cols;
+        {
+            std::vector<double> sc((size_t)ncols * 2);
+            RVE_CUDA(cudaMemcpyAsync(sc.data(), m->scale64.p, sc.size() * 8, cudaMemcpyDeviceToHost, s));
+            RVE_CUDA(cudaStreamSynchronize(s));
+            for (int c = 0; c < ncols; ++c) {
+                const int j = f.nc == 3 ? c % 6 : ((c % 6) < 3 ? 6 + c % 3 : 9 + c % 3);
+                const double ev = sc[2 * c] * m->phase_voigt[0][j] + sc[2 * c + 1] * m->phase_voigt[1][j];
+                if (bn[c] <= 1e-24 * ev) {
+                    zero_cols.push_back(c);
+                    bn[c] = 0.0;
+                }
+            }
+        }
+        auto zero_noise_columns = [&]() -> int {
+            for (int c : zero_cols) {
+                RVE_CUDA(cudaMemset2DAsync(r64 + c, (size_t)ncols * 8, 0, 8, (size_t)n_rows, s));
+                RVE_CUDA(cudaMemset2DAsync(x64 + c, (size_t)ncols * 8, 0, 8, (size_t)n_rows, s));
+            }
+            return RVE_OK;
+        };
         out.iterations = 0;
         out.sweeps = 0;
         out.converged = false;
         double rel = 1.0;
         if (warm) {
-            // start from the neighbouring solutions: r = b - K x0 in FP64
-            launch_gather_columns(n_rows, ncols, warm_cols, warm_map, warm, x64, s);
+            launch_combine_columns<double>(n_rows, ncols, warm->cols, warm->map, warm->coef, warm->x, x64, s);
             *launches += 1;
-            RVE_TRY(residual64(x64, r64));
+            if (mixed && warm->r) {
+                // the residual from the previous residuals (see WarmStart); a plain
+                // FP32 b - K x0 would be too noisy to set the inner tolerance from
+                launch_combine_columns<double>(n_rows, ncols, warm->cols, warm->map, warm->coef, warm->r, r64, s);
+                *launches += 1;
+                if (warm->degrade[0] != 0.0 || warm->degrade[1] != 0.0) {
+                    float* v32 = m->x32.as<float>();
+                    float* y32 = m->r32.as<float>();
+                    launch_combine_columns<float>(n_rows, ncols, warm->cols, warm->map, warm->dcoef, warm->x, v32, s);
+                    std::vector<float> sc32((size_t)ncols * 2);
+                    for (int c = 0; c < ncols; ++c)
+                        for (int ph = 0; ph < 2; ++ph) sc32[2 * c + ph] = (float)-warm->degrade[ph];
+                    RVE_TRY(upload(m->dscale32, sc32.data(), sc32.size(), s));
+                    RVE_CUDA(cudaMemsetAsync(y32, 0, nv * 4, s));
+                    launch_operator<float>(m->p, f.nc, false, ev<float>(m->dscale32), v32, y32, nullptr, L);
+                    launch_axpy_f2d((int64_t)nv, y32, r64, s);      // r0 -= K_deg v
+                    *launches += 3;
+                    bool any_alpha = false;
+                    std::vector<double> sc64((size_t)ncols * 2);
+                    for (int c = 0; c < ncols; ++c)
+                        for (int ph = 0; ph < 2; ++ph) {
+                            sc64[2 * c + ph] = -warm->alpha[c] * warm->degrade[ph];
+                            any_alpha |= sc64[2 * c + ph] != 0.0;
+                        }
+                    if (any_alpha) {
+                        // r0 -= alpha K_deg u_macro (macro load only: the cheap FP64 path)
+                        RVE_TRY(upload(m->dscale64, sc64.data(), sc64.size(), s));
+                        launch_operator<double>(m->p, f.nc, true, ev<double>(m->dscale64), nullptr, r64, nullptr, L);
+                        *launches += 1;
+                    }
+                }
+            } else {
+                RVE_TRY(residual64(x64, r64));
+            }
+            RVE_TRY(zero_noise_columns());
             RVE_TRY(rel_residual(r64, bn, rel));
         } else {
             RVE_CUDA(cudaMemsetAsync(x64, 0, nv * 8, s));
+            RVE_TRY(zero_noise_columns());
         }
         out.rel_res = rel;
         if (!mixed) {
@@ -532,6 +637,7 @@ struct Solver {
                                     o.rtol / rel, o.max_iter, its, conv));
                 out.iterations = its;
                 RVE_TRY(residual64(x64, r64));
+                RVE_TRY(zero_noise_columns());
                 RVE_TRY(rel_residual(r64, bn, out.rel_res));
                 out.converged = conv || out.rel_res <= o.rtol * 10;
             } else {
@@ -541,32 +647,47 @@ struct Solver {
             float* x32 = m->x32.as<float>();
             float* r32 = m->r32.as<float>();
             int total = 0;
-            out.converged = rel <= o.rtol;
-            for (int sw = 0; sw < std::max(1, o.max_refine) && !out.converged; ++sw) {
-                // reduce the residual only as far as the outer tolerance needs
-                // (half again for margin), never below what FP32 can resolve
-                const double inner = std::max(o.inner_rtol, 0.5 * o.rtol / out.rel_res);
-                launch_cast_d2f((int64_t)nv, r64, r32, s);
-                RVE_CUDA(cudaMemsetAsync(x32, 0, nv * 4, s));
-                *launches += 1;
-                int its = 0;
-                bool conv = false;
-                RVE_TRY(pcg<float>(x32, r32, m->p32.as<float>(), m->q32.as<float>(), m->scale32,
-                                   std::min(inner, 0.5), o.max_iter, its, conv));
-                total += its;
-                launch_axpy_f2d((int64_t)nv, x32, x64, s);
-                *launches += 1;
+            // Every sweep ends with the FP64 true residual, which alone decides
+            // convergence and feeds the tensor reduction; a sweep whose starting
+            // residual is already below rtol skips the FP32 inner solve.
+            for (int sw = 0; sw < std::max(1, o.max_refine); ++sw) {
+                if (out.rel_res > o.rtol) {
+                    // reduce the residual only as far as the outer tolerance needs
+                    // (half again for margin), never below what FP32 can resolve
+                    const double inner = std::max(o.inner_rtol, 0.5 * o.rtol / out.rel_res);
+                    launch_cast_d2f((int64_t)nv, r64, r32, s);
+                    RVE_CUDA(cudaMemsetAsync(x32, 0, nv * 4, s));
+                    *launches += 1;
+                    int its = 0;
+                    bool conv = false;
+                    RVE_TRY(pcg<float>(x32, r32, m->p32.as<float>(), m->q32.as<float>(), m->scale32,
+                                       std::min(inner, 0.5), o.max_iter, its, conv));
+                    total += its;
+                    launch_axpy_f2d((int64_t)nv, x32, x64, s);
+                    *launches += 1;
+                }
                 RVE_TRY(residual64(x64, r64));
+                RVE_TRY(zero_noise_columns());
                 RVE_TRY(rel_residual(r64, bn, out.rel_res));
                 out.sweeps = sw + 1;
                 out.converged = out.rel_res <= o.rtol;
+                if (out.converged) break;
             }
             out.iterations = total;
         }
         // reductions for the tensors
         launch_gram(n_rows, b64, x64, r64, m->gpart.as<double>(), L);
         launch_reduce_partials(L.nby, ncols * 12, m->gpart.as<double>(), m->gsum.as<double>(), s);
-        launch_mean_stress<double>(m->p, f.nc, ev<double>(m->scale64), x64, m->mpart.as<double>(), L);
+        if (mixed) {
+            // the volume-averaged stress is a diagnostic (Hill-Mandel): FP32 with
+            // compensated sums, as the inner solve
+            float* u32 = m->x32.as<float>();
+            launch_cast_d2f((int64_t)nv, x64, u32, s);
+            launch_mean_stress<float>(m->p, f.nc, ev<float>(m->scale32), u32, m->mpart.as<double>(), L);
+            *launches += 1;
+        } else {
+            launch_mean_stress<double>(m->p, f.nc, ev<double>(m->scale64), x64, m->mpart.as<double>(), L);
+        }
         launch_reduce_partials(L.nby, ncols * 12, m->mpart.as<double>(), m->msum.as<double>(), s);
         *launches += 4;
         std::vector<double> Gs(ncols * 12), Ms(ncols * 12);
@@ -615,6 +736,49 @@ double rel_fro(const double* a, const double* b, int n) {
 
 }  // namespace
 
+// Starting guess for an RVE with degradation factor w from the solutions of the
+// previous batch (factors pw): the polynomial in w through up to `order` of them.
+// The nodes are the nearest factor, the farthest one and the one nearest the
+// middle; a node closer than 1e-9 to another is dropped, and the order is lowered
+// when w lies far outside the nodes (quadratic up to one node span beyond them,
+// linear up to three), so that the coefficients stay small (at most about 8).
+// Returns the number of sources written to src/coef.
+static int warm_sources(const std::vector<double>& pw, double w, int order, int* src, double* coef) {
+    const int n = (int)pw.size();
+    int q0 = 0;
+    for (int q = 1; q < n; ++q)
+        if (std::fabs(pw[q] - w) < std::fabs(pw[q0] - w)) q0 = q;
+    src[0] = q0;
+    coef[0] = 1.0;
+    if (order < 2 || n < 2) return 1;
+    int q2 = q0;
+    for (int q = 0; q < n; ++q)
+        if (std::fabs(pw[q] - pw[q0]) > std::fabs(pw[q2] - pw[q0])) q2 = q;
+    const double span = std::fabs(pw[q2] - pw[q0]);
+    const double d = std::fabs(w - pw[q0]);
+    if (span <= 1e-9 || d > 3.0 * span) return 1;
+    int nodes[3] = {q0, q2, -1};
+    int nn = 2;
+    if (order >= 3 && d <= span && n >= 3) {
+        const double mid = 0.5 * (pw[q0] + pw[q2]);
+        int q1 = -1;
+        for (int q = 0; q < n; ++q) {
+            if (std::fabs(pw[q] - pw[q0]) <= 1e-9 || std::fabs(pw[q] - pw[q2]) <= 1e-9) continue;
+            if (q1 < 0 || std::fabs(pw[q] - mid) < std::fabs(pw[q1] - mid)) q1 = q;
+        }
+        if (q1 >= 0 && std::fabs(pw[q1] - pw[q0]) > 0.25 * span && std::fabs(pw[q1] - pw[q2]) > 0.25 * span)
+            nodes[nn++] = q1;
+    }
+    for (int i = 0; i < nn; ++i) {
+        double l = 1.0;
+        for (int j = 0; j < nn; ++j)
+            if (j != i) l *= (w - pw[nodes[j]]) / (pw[nodes[i]] - pw[nodes[j]]);
+        src[i] = nodes[i];
+        coef[i] = l;
+    }
+    return nn;
+}
+
 // Solve B RVEs of one mesh whose degradation factors are in d_w (device).
 int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D,
                           rve_stats* st, const double* w_host) {
@@ -628,26 +792,57 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
     launch_column_scales<float>(B, d_w, m->deg.apply_to_yarn, true, m->scale32.as<float>(), s);
     m->ctx->launches += 2;
     SolveOut om, osc;
-    // warm start: column map from this batch to the nearest degradation factor
-    // of the mesh's previous batch (set up by macro_update_gauss_points)
-    std::vector<int32_t> cmap;
+    // warm start from the mesh's previous batch (set up by macro_update_gauss_points)
+    const bool mixed = prec == RVE_PREC_MIXED;
     auto warm_ready = [&](int f) { return w_host && m->warm_cols[f] > 0 && !m->warm_w[f].empty(); };
-    auto build_map = [&](int f) -> int {
+    auto build_warm = [&](int f, WarmStart& ws) -> int {
         const std::vector<double>& pw = m->warm_w[f];
-        cmap.assign((size_t)6 * B, 0);
+        ws.degrade[0] = f == 0 ? 1.0 : 0.0;
+        ws.degrade[1] = (f == 0 && m->deg.apply_to_yarn) ? 1.0 : 0.0;
+        // a field that does not degrade has one solution for every w: the nearest will do
+        const bool degrades = ws.degrade[0] != 0.0 || ws.degrade[1] != 0.0;
+        const int order = degrades ? std::max(1, std::min(m->ctx->opt.warm_start, WARM_SOURCES)) : 1;
+        const size_t n = (size_t)6 * B * WARM_SOURCES;
+        std::vector<int32_t> cmap(n, 0);
+        std::vector<double> ccoef(n, 0.0), dcoef(n, 0.0);
+        ws.alpha.assign((size_t)6 * B, 0.0);
         for (int b = 0; b < B; ++b) {
-            int best = 0;
-            for (int q = 1; q < (int)pw.size(); ++q)
-                if (std::fabs(pw[q] - w_host[b]) < std::fabs(pw[best] - w_host[b])) best = q;
-            for (int c = 0; c < 6; ++c) cmap[6 * b + c] = 6 * best + c;
+            int src[WARM_SOURCES];
+            double cf[WARM_SOURCES];
+            const int ns = warm_sources(pw, w_host[b], order, src, cf);
+            double al = 0.0;
+            for (int k = 0; k < ns; ++k) al += cf[k] * (w_host[b] - pw[src[k]]);
+            if (ns > 1) al = 0.0;   // the weights reproduce lines: zero up to rounding
+            for (int c = 0; c < 6; ++c) {
+                ws.alpha[6 * b + c] = al;
+                for (int k = 0; k < ns; ++k) {
+                    const size_t i = (size_t)(6 * b + c) * WARM_SOURCES + k;
+                    cmap[i] = 6 * src[k] + c;
+                    ccoef[i] = cf[k];
+                    dcoef[i] = cf[k] * (w_host[b] - pw[src[k]]);
+                }
+            }
         }
-        return upload(m->warm_map, cmap.data(), cmap.size(), s);
+        RVE_TRY(upload(m->warm_map, cmap.data(), n, s));
+        RVE_TRY(upload(m->warm_coef, ccoef.data(), n, s));
+        RVE_TRY(upload(m->warm_dcoef, dcoef.data(), n, s));
+        ws.x = m->warm[f].as<double>();
+        ws.r = mixed ? m->warm_r[f].as<double>() : nullptr;
+        ws.cols = m->warm_cols[f];
+        ws.map = m->warm_map.as<int32_t>();
+        ws.coef = m->warm_coef.as<double>();
+        ws.dcoef = m->warm_dcoef.as<double>();
+        return RVE_OK;
     };
     auto keep_warm = [&](int f, FieldDev& fd) -> int {
         if (!w_host) return RVE_OK;
         const size_t nb = (size_t)fd.n_rows * 6 * B * 8;
         RVE_TRY(m->warm[f].ensure(nb));
         RVE_CUDA(cudaMemcpyAsync(m->warm[f].p, m->x64.p, nb, cudaMemcpyDeviceToDevice, s));
+        if (mixed) {
+            RVE_TRY(m->warm_r[f].ensure(nb));
+            RVE_CUDA(cudaMemcpyAsync(m->warm_r[f].p, m->r64.p, nb, cudaMemcpyDeviceToDevice, s));
+        }
         m->warm_cols[f] = 6 * B;
         m->warm_w[f].assign(w_host, w_host + B);
         return RVE_OK;
@@ -655,8 +850,9 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
     {
         Solver sv(m, m->mech, B);
         if (warm_ready(0)) {
-            RVE_TRY(build_map(0));
-            RVE_TRY(sv.run(prec, om, m->warm[0].as<double>(), m->warm_cols[0], m->warm_map.as<int32_t>()));
+            WarmStart ws;
+            RVE_TRY(build_warm(0, ws));
+            RVE_TRY(sv.run(prec, om, &ws));
         } else {
             RVE_TRY(sv.run(prec, om));
         }
@@ -668,8 +864,9 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
     {
         Solver sv(m, m->scal, B);
         if (warm_ready(1)) {
-            RVE_TRY(build_map(1));
-            RVE_TRY(sv.run(prec, osc, m->warm[1].as<double>(), m->warm_cols[1], m->warm_map.as<int32_t>()));
+            WarmStart ws;
+            RVE_TRY(build_warm(1, ws));
+            RVE_TRY(sv.run(prec, osc, &ws));
         } else {
             RVE_TRY(sv.run(prec, osc));
         }
@@ -757,7 +954,7 @@ void rve_default_options(rve_options* o) {
     o->batch = 0;
     o->stream = nullptr;
     o->profile = 0;
-    o->warm_start = 1;
+    o->warm_start = 2;
 }
 
 int rve_create(rve_ctx* out, const rve_options* opts) {
@@ -963,6 +1160,25 @@ int rve_set_materials(rve_ctx c, rve_mesh m, const rve_matrix_props* mp, const r
         set_error("yarn tangent is zero or TI tensor not invertible");
         return RVE_ERR_NOT_SPD;
     }
+    {
+        std::vector<double> geo(nt * 10), mm(nt * 21), ms(nt * 12);
+        RVE_CUDA(cudaMemcpyAsync(geo.data(), m->d_geo64.p, geo.size() * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaMemcpyAsync(mm.data(), m->d_matm64.p, mm.size() * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaMemcpyAsync(ms.data(), m->d_mats64.p, ms.size() * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaStreamSynchronize(s));
+        static const int diag21[6] = {0, 6, 11, 15, 18, 20};   // (i,i) in the upper-triangular Voigt layout
+        for (int ph = 0; ph < 2; ++ph)
+            for (int k = 0; k < 12; ++k) m->phase_voigt[ph][k] = 0.0;
+        for (int64_t e = 0; e < nt; ++e) {
+            const int ph = m->phase[e];
+            const double v = geo[e * 10 + 9];
+            for (int k = 0; k < 6; ++k) m->phase_voigt[ph][k] += v * mm[e * 21 + diag21[k]];
+            for (int k = 0; k < 3; ++k) {
+                m->phase_voigt[ph][6 + k] += v * ms[e * 12 + k];
+                m->phase_voigt[ph][9 + k] += v * ms[e * 12 + 6 + k];
+            }
+        }
+    }
     m->mc = mc;
     m->deg = dg;
     m->T_C = T_C;
@@ -1024,6 +1240,9 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
     c->launches++;
     const double op0 = c->op_ms, ob0 = c->op_bytes, of0 = c->op_flops;
     const double u0 = c->upd_ms, ub0 = c->upd_bytes, pu0 = c->pup_ms, pb0 = c->pup_bytes, f0 = c->fin_ms;
+    const double rs0 = c->res_ms;
+    const double oc0 = c->op_cols, oa0 = c->op_cols_all;
+    const int64_t rl0 = c->res_launches;
     const int64_t on0 = c->op_launches;
     int rc = homogenise_batch(m, 1, d + 3, C, K, D, st);
     RVE_CUDA(cudaStreamSynchronize(s));
@@ -1039,6 +1258,9 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
         st->pupdate_ms = c->pup_ms - pu0;
         st->pupdate_bytes = c->pup_bytes - pb0;
         st->finalize_ms = c->fin_ms - f0;
+        st->residual_ms = c->res_ms - rs0;
+        st->residual_launches = c->res_launches - rl0;
+        st->op_active_frac = c->op_cols_all > oa0 ? (c->op_cols - oc0) / (c->op_cols_all - oa0) : 0.0;
     }
     return rc;
 }
@@ -1163,6 +1385,9 @@ int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshe
     }
     const double op0 = c->op_ms, ob0 = c->op_bytes, of0 = c->op_flops;
     const double u0 = c->upd_ms, ub0 = c->upd_bytes, pu0 = c->pup_ms, pb0 = c->pup_bytes, f0 = c->fin_ms;
+    const double rs0 = c->res_ms;
+    const double oc0 = c->op_cols, oa0 = c->op_cols_all;
+    const int64_t rl0 = c->res_launches;
     const int64_t on0 = c->op_launches;
     int rc = macro_update_impl(c, meshes, n_meshes, G, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev,
                                D_dev, status_dev, st);
@@ -1179,6 +1404,9 @@ int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshe
         st->pupdate_ms = c->pup_ms - pu0;
         st->pupdate_bytes = c->pup_bytes - pb0;
         st->finalize_ms = c->fin_ms - f0;
+        st->residual_ms = c->res_ms - rs0;
+        st->residual_launches = c->res_launches - rl0;
+        st->op_active_frac = c->op_cols_all > oa0 ? (c->op_cols - oc0) / (c->op_cols_all - oa0) : 0.0;
     }
     return rc;
 }

@@ -106,6 +106,9 @@ struct rve_ctx_s {
     int64_t op_launches = 0;
     double op_bytes = 0, op_flops = 0;
     double upd_ms = 0, upd_bytes = 0, pup_ms = 0, pup_bytes = 0, fin_ms = 0;
+    double res_ms = 0;          // FP64 true-residual operator applications
+    double op_cols = 0, op_cols_all = 0;   // active and total columns over operator launches
+    int64_t res_launches = 0;
     ~rve_ctx_s() {
         for (auto e : ev) cudaEventDestroy(e);
     }
@@ -127,6 +130,9 @@ struct rve_mesh_s {
     rve::DevBuf d_matm64, d_matm32, d_mats64, d_mats32;
     rve::FieldDev mech, scal;
     bool have_materials = false;
+    // per phase: sum over its tets of |T| times the diagonal of D (6, mechanics) and of
+    // k (3) and d (3), internal units; the energy scale of each unit load case
+    double phase_voigt[2][12] = {};
     rve::MaterialConsts mc{};
     rve_degradation deg{};
     double T_C = 20, c_wt = 0, t_h = 0;
@@ -135,7 +141,8 @@ struct rve_mesh_s {
     rve::DevBuf epart, rzp, cpart, gpart, mpart, gsum, msum;
     rve::DevBuf colstate, scale64, scale32, wdev;
     // warm start: the previous batch's FP64 solutions per field and their factors
-    rve::DevBuf warm[2], warm_map;
+    rve::DevBuf warm[2], warm_r[2], warm_map, warm_coef, warm_dcoef;
+    rve::DevBuf dscale32, dscale64;   // per-column phase scales of the warm-start residual
     int warm_cols[2] = {0, 0};
     std::vector<double> warm_w[2];
 };

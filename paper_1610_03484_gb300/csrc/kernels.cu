@@ -616,7 +616,10 @@ __device__ __forceinline__ T inv_diag(const RowView<T>& rv, int64_t row, int col
     const int f = (rv.nfield == 2 && (col % 6) >= 3) ? 1 : 0;
     const T d = rv.scale[2 * col] * rv.diag[(int64_t)(2 * f) * rv.n_rows + row] +
                 rv.scale[2 * col + 1] * rv.diag[(int64_t)(2 * f + 1) * rv.n_rows + row];
-    return d > T(0) ? T(1) / d : T(0);
+    if constexpr (sizeof(T) == 4)
+        return d > T(0) ? __frcp_rn(d) : T(0);   // correctly rounded reciprocal
+    else
+        return d > T(0) ? T(1) / d : T(0);
 }
 
 // One block per column: alpha = (r, z) / (p, K p) with (p, K p) summed in parallel.
@@ -999,6 +1002,8 @@ void launch_gram(int64_t n_rows, const double* b, const double* u, const double*
 
 // Volume integrals per column: int sigma(eps_bar + eps(u)) (Eq. macro_stress)
 // and int sigma(eps_bar) (the Voigt term), 6 + 6 values (3 + 3 for scalars).
+// Only the constant gradient mode enters an element mean (the higher modes
+// integrate to zero).  T = float keeps per-thread compensated sums.
 template <int P, int NC, typename T>
 __global__ void __launch_bounds__(256) k_mean_stress(ElemView<T> ev, const T* __restrict__ u,
                                                      double* __restrict__ part, int ncols, int cpb) {
@@ -1009,51 +1014,67 @@ __global__ void __launch_bounds__(256) k_mean_stress(ElemView<T> ev, const T* __
     const int col = blockIdx.x * cpb + cl;
     const int field = (col % 6) >= 3 ? 1 : 0;
     const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
-    double acc[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+    PartialSum<T> acc[12];
     for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < ev.nt; e += (int64_t)gridDim.y * rows) {
-        double G[9];
-        for (int i = 0; i < 9; ++i) G[i] = (double)ev.geo[e * 10 + i];
-        const double vol = (double)ev.geo[e * 10 + 9];
-        const double s = (double)ev.scale[col * 2 + ev.phase[e]];
-        double V[3][NC];
-        for (int k = 0; k < 3; ++k)
-            for (int c = 0; c < NC; ++c) {
-                double v = (double)u[((int64_t)ev.edofs[e * NE + k + 1] * NC + c) * ncols + col] -
-                           (double)u[((int64_t)ev.edofs[e * NE] * NC + c) * ncols + col];
-                for (int j = 4; j < NE; ++j)
-                    v += Tab<double>::a(P, (k * NM + 0) * NE + j) *
-                         (double)u[((int64_t)ev.edofs[e * NE + j] * NC + c) * ncols + col];
-                V[k][c] = v;
+        const int32_t* ed = ev.edofs + e * NE;
+        T G[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) G[i] = __ldg(ev.geo + e * 10 + i);
+        const T vol = __ldg(ev.geo + e * 10 + 9);
+        const T sc = __ldg(ev.scale + col * 2 + __ldg(ev.phase + e));
+        T V[3][NC];
+        const int d0 = __ldg(ed);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int dk = __ldg(ed + k + 1);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                V[k][c] = u[((int64_t)dk * NC + c) * ncols + col] - u[((int64_t)d0 * NC + c) * ncols + col];
+        }
+#pragma unroll
+        for (int j = 4; j < NE; ++j) {
+            const int dj = __ldg(ed + j);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const T a = basis_a<P, T>((k * NM + 0) * NE + j);
+                if (a != T(0))
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) V[k][c] = fma(a, u[((int64_t)dj * NC + c) * ncols + col], V[k][c]);
             }
-        double H[NC][3];
+        }
+        T H[NC][3];
+#pragma unroll
         for (int c = 0; c < NC; ++c)
+#pragma unroll
             for (int l = 0; l < 3; ++l) H[c][l] = V[0][c] * G[l] + V[1][c] * G[3 + l] + V[2][c] * G[6 + l];
-        if (NC == 3) {
-            double Dm[21];
-            for (int i = 0; i < 21; ++i) Dm[i] = s * (double)ev.mat[e * 21 + i];
-            double ev6[6] = {H[0][0], H[1 % NC][1], H[2 % NC][2], H[0][1] + H[1 % NC][0],
-                             H[1 % NC][2] + H[2 % NC][1], H[2 % NC][0] + H[0][2]};
-            ev6[macro_id] += 1.0;   // unit engineering macro strain of this column
+        const T sv = sc * vol;
+        if constexpr (NC == 3) {
+            T ev6[6] = {H[0][0], H[1][1], H[2][2], H[0][1] + H[1][0], H[1][2] + H[2][1], H[2][0] + H[0][2]};
+            ev6[macro_id] += T(1);   // unit engineering macro strain of this column
+#pragma unroll
             for (int i = 0; i < 6; ++i) {
-                double t = 0.0;
-                for (int j = 0; j < 6; ++j) t += Dm[ut6(i, j)] * ev6[j];
-                acc[i] += vol * t;
-                acc[6 + i] += vol * Dm[ut6(i, macro_id)];
+                T t = T(0);
+#pragma unroll
+                for (int j = 0; j < 6; ++j) t = fma(__ldg(ev.mat + e * 21 + ut6(i, j)), ev6[j], t);
+                acc[i].add(sv * t);
+                acc[6 + i].add(sv * __ldg(ev.mat + e * 21 + ut6(i, macro_id)));
             }
         } else {
-            double Km[6];
-            for (int i = 0; i < 6; ++i) Km[i] = s * (double)ev.mat[e * 12 + 6 * field + i];
-            double g[3] = {H[0][0], H[0][1], H[0][2]};
-            g[macro_id] += 1.0;
+            const T* Km = ev.mat + e * 12 + 6 * field;
+            T g[3] = {H[0][0], H[0][1], H[0][2]};
+            g[macro_id] += T(1);
+#pragma unroll
             for (int l = 0; l < 3; ++l) {
-                acc[l] += vol * (Km[s3(l, 0)] * g[0] + Km[s3(l, 1)] * g[1] + Km[s3(l, 2)] * g[2]);
-                acc[6 + l] += vol * Km[s3(l, macro_id)];
+                acc[l].add(sv * (__ldg(Km + s3(l, 0)) * g[0] + __ldg(Km + s3(l, 1)) * g[1] +
+                                 __ldg(Km + s3(l, 2)) * g[2]));
+                acc[6 + l].add(sv * __ldg(Km + s3(l, macro_id)));
             }
         }
     }
-    block_column_reduce<12>(acc, part, ncols, cpb, col);
+    double out[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = acc[k].value();
+    block_column_reduce<12>(out, part, ncols, cpb, col);
 }
 
 template <typename T>
@@ -1071,6 +1092,8 @@ void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const T* u, double
 }
 template void launch_mean_stress<double>(int, int, const ElemView<double>&, const double*, double*,
                                          const Launch&);
+template void launch_mean_stress<float>(int, int, const ElemView<float>&, const float*, double*,
+                                        const Launch&);
 
 // out[w] = sum_b part[b][w]: one block per output value (up to 128 outputs per
 // block row are handled by grid-striding over w).
@@ -1127,23 +1150,38 @@ void launch_scatter_results(int B, const int64_t* idx, const double* res, double
 }
 
 // x[row][col] = src[row][map[col]]  (warm start from a previous batch's solution)
-__global__ void k_gather_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* __restrict__ map,
-                                 const double* __restrict__ src, double* __restrict__ x) {
+// x[:, col] = sum_k coef[col][k] src[:, map[col][k]] over WARM_SOURCES previous
+// solutions (a polynomial in the degradation factor through them), stored as TO
+template <typename TO>
+__global__ void k_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* __restrict__ map,
+                                  const double* __restrict__ coef, const double* __restrict__ src,
+                                  TO* __restrict__ x) {
     const int64_t n = n_rows * ncols;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = i / ncols;
         const int col = (int)(i % ncols);
-        x[i] = src[row * src_cols + map[col]];
+        double v = 0.0;
+#pragma unroll
+        for (int k = 0; k < WARM_SOURCES; ++k) {
+            const double c = coef[col * WARM_SOURCES + k];
+            if (c != 0.0) v = fma(c, src[row * src_cols + map[col * WARM_SOURCES + k]], v);
+        }
+        x[i] = (TO)v;
     }
 }
 
-void launch_gather_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* src,
-                           double* x, cudaStream_t s) {
+template <typename TO>
+void launch_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* coef,
+                            const double* src, TO* x, cudaStream_t s) {
     int64_t b = (n_rows * ncols + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
     if (b < 1) b = 1;
-    k_gather_columns<<<(unsigned)b, 256, 0, s>>>(n_rows, ncols, src_cols, map, src, x);
+    k_combine_columns<TO><<<(unsigned)b, 256, 0, s>>>(n_rows, ncols, src_cols, map, coef, src, x);
 }
+template void launch_combine_columns<double>(int64_t, int, int, const int32_t*, const double*, const double*,
+                                             double*, cudaStream_t);
+template void launch_combine_columns<float>(int64_t, int, int, const int32_t*, const double*, const double*,
+                                            float*, cudaStream_t);
 
 // ---------------------------------------------------------- elementwise
 __global__ void k_cast_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {

@@ -128,8 +128,11 @@ void launch_gather_states(int B, const int64_t* idx, const double* T, const doub
 void launch_scatter_results(int B, const int64_t* idx, const double* res, double* C, double* K, double* D,
                             int32_t* status, cudaStream_t s);
 
-void launch_gather_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* src,
-                           double* x, cudaStream_t s);
+// previous solutions combined per column (warm starts); map and coef are [ncols][WARM_SOURCES]
+constexpr int WARM_SOURCES = 3;
+template <typename TO>
+void launch_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* coef,
+                            const double* src, TO* x, cudaStream_t s);
 
 // elementwise helpers
 void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);

@@ -202,12 +202,13 @@ def test_error_codes(rve, ctx64):
 
 def test_warm_started_batches_match_cold_and_oracle(rve):
     """Batches ordered by degradation factor and started from the previous
-    batch's solutions give the same tensors as cold starts (and the oracle)."""
+    batch's solutions (nearest, line, parabola in the factor) give the same
+    tensors as cold starts (and the oracle)."""
     grid, p = (6, 6, 4), 2
     xyz, tets, phase, tangent = ri.weave_rve(*grid)
     T, c, t, _, _ = ri.gauss_point_states(24, seed=9)
     out = {}
-    for warm in (True, False):
+    for warm in (0, 1, 2, 3):
         with rve.Context(precision=rve.PREC_MIXED, rtol=1e-7, inner_rtol=1e-6, batch=4, warm_start=warm) as ctx:
             mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
             mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
@@ -216,12 +217,14 @@ def test_warm_started_batches_match_cold_and_oracle(rve):
             assert (st == 0).all()
             out[warm] = (Cb, Kb, Db, stats)
             mesh.free()
-    for a, b in zip(out[True][:3], out[False][:3]):
-        for g in range(24):
-            assert rel(a[g], b[g]) < 1e-6
+    for warm in (1, 2, 3):
+        for a, b in zip(out[warm][:3], out[0][:3]):
+            for g in range(24):
+                assert rel(a[g], b[g]) < 1e-6
     for g in (0, 11, 23):
         w = float(mt.one_minus_omega(T[g], c[g], t[g]))
         Co, Ko, Do = oracle_tensors(xyz, tets, grid, p, 1, phase, tangent, w)
-        assert rel(out[True][0][g], Co) < TOL_MIXED
-        assert rel(out[True][1][g], Ko) < TOL_MIXED
-        assert rel(out[True][2][g], Do) < TOL_MIXED
+        for warm in (1, 3):
+            assert rel(out[warm][0][g], Co) < TOL_MIXED
+            assert rel(out[warm][1][g], Ko) < TOL_MIXED
+            assert rel(out[warm][2][g], Do) < TOL_MIXED
