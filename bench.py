@@ -40,12 +40,13 @@ WORKLOAD = ("batched FE2 evaluation: 4096 macro Gauss points per GPU, plain-weav
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 RTOL = 1e-5          # FP64 outer (true-residual) tolerance of every cell solve
 INNER_RTOL = 5e-6    # FP32 inner PCG tolerance per refinement sweep
-# dram read + write bytes per operator launch from the ncu capture in profiles/ (None until
-# the kernel's current version has been captured)
-TRAFFIC_PER_LAUNCH = None
-# one ncu capture of the current operator (profiles/k_operator_p2_mech_f32_32x32x10_b8.md)
+# One ncu capture of the current p = 2 mechanical operator
+# (profiles/k_operator_p2_mech_f32_32x32x10_b8.md): DRAM read + write bytes of one launch
+# against its algorithmic bytes.  The bench scales the ratio to its own mean launch of that
+# instance (traffic grows with the columns and elements processed); None for other kernels.
+TRAFFIC_KERNEL = "k_operator<p=2,mech,f32>"
 TRAFFIC_CAPTURE = {"case": "k_operator<2,3,float>, 32x32x10 p=2, 8 RVEs (48 columns)",
-                   "dram_bytes": 115.87e6, "algorithmic_bytes": 112.3e6, "ratio": 1.03}
+                   "dram_bytes": 115.87e6, "algorithmic_bytes": 112.3e6, "ratio": 115.87 / 112.3}
 
 
 def parse():
@@ -293,40 +294,56 @@ def roofline(st, step_ms, pk, pk_kind, clk):
     """Roofline of the step's kernels from one profiled step of the same workload:
     every launch of the PCG iteration is bracketed by CUDA events on its stream
     and its algorithmic bytes (and, for the operator, flops) are counted by the
-    library.  The dominant kernel (largest share of the step) fills the
-    top-level fields."""
-    n = st["op_launches"]
+    library, per operator instance (order p x field).  The dominant kernel (the
+    largest share of the step) fills the top-level fields, against the roof that
+    binds it (the larger of its HBM and FP32-ALU fractions)."""
     hbm_peak = pk["hbm_gbs"]
     mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12      # FP32 CUDA-core FMA peak at the sampled clock
-    op_s = st["op_ms"] / 1e3
-    op = {"launches": n, "mean_launch_ms": st["op_ms"] / n, "share_of_step": st["op_ms"] / step_ms,
-          "hbm_gbs": st["op_bytes"] / op_s / 1e9, "hbm_frac": st["op_bytes"] / op_s / 1e9 / hbm_peak,
-          "tflops": st["op_flops"] / op_s / 1e12, "alu_frac": st["op_flops"] / op_s / 1e12 / fp32_peak,
-          "bytes_per_launch": st["op_bytes"] / n, "flops_per_launch": st["op_flops"] / n,
-          "active_column_frac": st["op_active_frac"]}
-    vec = {}
+
+    def op_entry(ms, n, by, fl, act):
+        sec = ms / 1e3
+        e = {"launches": n, "mean_launch_ms": ms / n, "share_of_step": ms / step_ms,
+             "hbm_gbs": by / sec / 1e9, "hbm_frac": by / sec / 1e9 / hbm_peak,
+             "tflops": fl / sec / 1e12, "alu_frac": fl / sec / 1e12 / fp32_peak,
+             "bytes_per_launch": by / n, "flops_per_launch": fl / n, "active_column_frac": act}
+        e["bound"] = "alu" if e["alu_frac"] >= e["hbm_frac"] else "hbm"
+        return e
+
+    kernels = {}
+    for k in range(6):
+        n = st["op_class_launches"][k]
+        if n > 0:
+            name = f"k_operator<p={k // 2 + 1},{'mech' if k % 2 == 0 else 'scalar'},f32>"
+            kernels[name] = op_entry(st["op_class_ms"][k], n, st["op_class_bytes"][k],
+                                     st["op_class_flops"][k], st["op_class_active_frac"][k])
+    n = st["op_launches"]
+    kernels["k_operator (all instances)"] = op_entry(st["op_ms"], n, st["op_bytes"], st["op_flops"],
+                                                     st["op_active_frac"])
     for name, ms, by in (("k_update", st["update_ms"], st["update_bytes"]),
                          ("k_pupdate", st["pupdate_ms"], st["pupdate_bytes"])):
-        vec[name] = {"launches": n, "mean_launch_ms": ms / n, "share_of_step": ms / step_ms,
-                     "hbm_gbs": by / (ms / 1e3) / 1e9, "hbm_frac": by / (ms / 1e3) / 1e9 / hbm_peak,
-                     "bytes_per_launch": by / n}
-    kernels = {"k_operator": op, **vec,
-               "finalize (alpha, beta)": {"share_of_step": st["finalize_ms"] / step_ms},
-               "FP64 true residual": {"launches": st["residual_launches"],
-                                      "share_of_step": st["residual_ms"] / step_ms}}
-    dom = max(("k_operator", "k_update", "k_pupdate"), key=lambda k: kernels[k]["share_of_step"])
+        kernels[name] = {"launches": n, "mean_launch_ms": ms / n, "share_of_step": ms / step_ms,
+                         "hbm_gbs": by / (ms / 1e3) / 1e9, "hbm_frac": by / (ms / 1e3) / 1e9 / hbm_peak,
+                         "bytes_per_launch": by / n, "bound": "hbm"}
+    kernels["finalize (alpha, beta)"] = {"share_of_step": st["finalize_ms"] / step_ms}
+    kernels["true residual (double-float)"] = {"launches": st["residual_launches"],
+                                               "share_of_step": st["residual_ms"] / step_ms}
+    cands = [k for k, v in kernels.items() if "bound" in v and not k.endswith("(all instances)")]
+    dom = max(cands, key=lambda k: kernels[k]["share_of_step"])
     out = {"how": "one extra step of the same workload after the timed ones, every PCG-iteration launch "
-                  "bracketed by CUDA events on its stream; bytes and flops are algorithmic",
+                  "bracketed by CUDA events on its stream; bytes and flops are algorithmic, counted for "
+                  "the columns still iterating",
            "profiled_step_ms": step_ms, "kernels": kernels, "kernel": dom,
-           "traffic": TRAFFIC_PER_LAUNCH, "traffic_capture": TRAFFIC_CAPTURE,
+           "traffic": (TRAFFIC_CAPTURE["ratio"] * kernels[dom]["bytes_per_launch"]
+                       if dom == TRAFFIC_KERNEL else None),
+           "traffic_capture": TRAFFIC_CAPTURE,
            "peaks": {"hbm_gbs": hbm_peak, "hbm_kind": f"{pk_kind} (MEASURED_PEAKS.json copy bandwidth)",
                      "fp32_tflops": fp32_peak,
                      "fp32_kind": f"derived: 152 SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled median)"}}
     k = kernels[dom]
-    if dom == "k_operator" and op["alu_frac"] >= op["hbm_frac"]:
-        out.update({"bound": "alu", "achieved": op["tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": op["alu_frac"]})
+    if k["bound"] == "alu":
+        out.update({"bound": "alu", "achieved": k["tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": k["alu_frac"]})
     else:
         out.update({"bound": "hbm", "achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
                     "frac": k["hbm_frac"]})

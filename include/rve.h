@@ -138,9 +138,16 @@ typedef struct rve_stats {
     double  pupdate_ms, pupdate_bytes;   /* r, p read, p, q written (4 n_rows ncols s) */
     double  finalize_ms;                 /* alpha and beta/multiplier kernels */
     /* profile mode, outside the PCG iterations: */
-    double  residual_ms;                 /* FP64 true residual r = b - K x (operator + sign) */
-    int64_t residual_launches;           /* FP64 operator applications counted in residual_ms */
+    double  residual_ms;                 /* true residual r = b - K x: FP64 operator (FP64 mode) or
+                                            double-float operator (mixed mode) */
+    int64_t residual_launches;           /* true-residual applications counted in residual_ms */
     double  op_active_frac;              /* active columns / columns, averaged over operator launches */
+    /* the operator launches above by class k = 2 (p - 1) + (scalar field ? 1 : 0) */
+    double  op_class_ms[6];
+    int64_t op_class_launches[6];
+    double  op_class_bytes[6];
+    double  op_class_flops[6];
+    double  op_class_active_frac[6];
 } rve_stats;
 
 /* ------------------------------------------------------------------ calls */

@@ -68,10 +68,14 @@ class Stats(C.Structure):
                 ("update_ms", C.c_double), ("update_bytes", C.c_double), ("pupdate_ms", C.c_double),
                 ("pupdate_bytes", C.c_double), ("finalize_ms", C.c_double),
                 ("residual_ms", C.c_double), ("residual_launches", C.c_int64),
-                ("op_active_frac", C.c_double)]
+                ("op_active_frac", C.c_double),
+                ("op_class_ms", C.c_double * 6), ("op_class_launches", C.c_int64 * 6),
+                ("op_class_bytes", C.c_double * 6), ("op_class_flops", C.c_double * 6),
+                ("op_class_active_frac", C.c_double * 6)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        return {n: (list(v) if isinstance(v, C.Array) else v)
+                for n, v in ((n, getattr(self, n)) for n, _ in self._fields_)}
 
 
 _lib = None

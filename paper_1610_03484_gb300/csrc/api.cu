@@ -355,6 +355,72 @@ struct Solver {
         return RVE_OK;
     }
 
+    // b = -K(s) u_macro for every column: the mesh keeps K_ph u_macro per phase at
+    // unit modulus (two macro-load-only operator passes over 6 columns, once per
+    // materials, boundary condition and precision), and each batch combines them
+    // with its column scales.  FP64 mode uses the FP64 operator; mixed mode the
+    // double-float evaluation of the FP32-data operator, so that its right-hand
+    // side and true residual belong to one and the same discrete system.
+    int rhs(double* b, bool mixed) {
+        const int fid = (&f == &m->mech) ? 0 : 1;
+        const int prec = mixed ? RVE_PREC_MIXED : RVE_PREC_FP64;
+        if (!m->bph_valid[fid] || m->bph_prec[fid] != prec) {
+            const size_t n6 = (size_t)n_rows * 6;
+            RVE_TRY(m->bph[fid].ensure(2 * n6 * 8));
+            RVE_CUDA(cudaMemsetAsync(m->bph[fid].p, 0, 2 * n6 * 8, s));
+            const Launch L6 = make_launch(6, std::max<int64_t>(n_rows, m->nt), s);
+            for (int ph = 0; ph < 2; ++ph) {
+                double sc[12];
+                float sc32[12];
+                for (int c = 0; c < 6; ++c) {
+                    sc[2 * c] = sc32[2 * c] = ph == 0 ? 1.0 : 0.0;
+                    sc[2 * c + 1] = sc32[2 * c + 1] = ph == 1 ? 1.0 : 0.0;
+                }
+                double* y = m->bph[fid].as<double>() + ph * n6;
+                if (mixed) {
+                    // the double-float kernel returns -K u_macro: stored negated
+                    RVE_TRY(upload(m->dscale32, sc32, 12, s));
+                    launch_residual_df(m->p, f.nc, ev<float>(m->dscale32), nullptr, y, L6);
+                    launch_neg((int64_t)n6, y, s);
+                    *launches += 2;
+                } else {
+                    RVE_TRY(upload(m->dscale64, sc, 12, s));
+                    launch_operator<double>(m->p, f.nc, true, ev<double>(m->dscale64), nullptr, y, nullptr, L6);
+                    *launches += 1;
+                }
+            }
+            m->bph_valid[fid] = true;
+            m->bph_prec[fid] = prec;
+        }
+        launch_rhs_combine(n_rows, B, m->bph[fid].as<double>(), m->scale64.as<double>(), b, s);
+        *launches += 1;
+        return RVE_OK;
+    }
+
+    // y = b - K x in mixed mode: the double-float evaluation of the FP32-data operator
+    int residual_df(const double* x, double* y) {
+        const bool prof = m->ctx->opt.profile != 0;
+        auto& evs = m->ctx->ev;
+        while (prof && evs.size() < 2) {
+            cudaEvent_t e;
+            RVE_CUDA(cudaEventCreate(&e));
+            evs.push_back(e);
+        }
+        if (prof) RVE_CUDA(cudaEventRecord(evs[0], s));
+        RVE_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n_rows * ncols, s));
+        launch_residual_df(m->p, f.nc, ev<float>(m->scale32), x, y, L);
+        *launches += 1;
+        if (prof) {
+            RVE_CUDA(cudaEventRecord(evs[1], s));
+            RVE_CUDA(cudaEventSynchronize(evs[1]));
+            float ms = 0;
+            RVE_CUDA(cudaEventElapsedTime(&ms, evs[0], evs[1]));
+            m->ctx->prof.res_ms += ms;
+            m->ctx->prof.res_launches++;
+        }
+        return RVE_OK;
+    }
+
     // y = -(K x + macro)  (FP64): the fluctuation residual b - K x
     int residual64(const double* x, double* y) {
         const bool prof = m->ctx->opt.profile != 0;
@@ -374,8 +440,8 @@ struct Solver {
             RVE_CUDA(cudaEventSynchronize(evs[1]));
             float ms = 0;
             RVE_CUDA(cudaEventElapsedTime(&ms, evs[0], evs[1]));
-            m->ctx->res_ms += ms;
-            m->ctx->res_launches++;
+            m->ctx->prof.res_ms += ms;
+            m->ctx->prof.res_launches++;
         }
         return RVE_OK;
     }
@@ -487,17 +553,27 @@ struct Solver {
                                ? (double)ms : 0.0;
                 };
                 for (int k = 0; k < check; ++k) {
-                    m->ctx->op_ms += el(k, 0, 1);
-                    m->ctx->op_launches++;
-                    m->ctx->op_bytes += bytes;
-                    m->ctx->op_flops += flops;
-                    m->ctx->op_cols += na;
-                    m->ctx->op_cols_all += ncols;
-                    m->ctx->fin_ms += el(k, 1, 2) + el(k, 3, 4);
-                    m->ctx->upd_ms += el(k, 2, 3);
-                    m->ctx->upd_bytes += 6 * vb;
-                    m->ctx->pup_ms += el(k, 4, 5);
-                    m->ctx->pup_bytes += 4 * vb;
+                    m->ctx->prof.op_ms += el(k, 0, 1);
+                    ProfCounters& pc = m->ctx->prof;
+                    const double op_ms = el(k, 0, 1);
+                    pc.op_ms += op_ms;
+                    pc.op_launches++;
+                    pc.op_bytes += bytes;
+                    pc.op_flops += flops;
+                    pc.op_cols += na;
+                    pc.op_cols_all += ncols;
+                    const int cl = 2 * (m->p - 1) + (nc == 3 ? 0 : 1);
+                    pc.cls_ms[cl] += op_ms;
+                    pc.cls_launches[cl]++;
+                    pc.cls_bytes[cl] += bytes;
+                    pc.cls_flops[cl] += flops;
+                    pc.cls_cols[cl] += na;
+                    pc.cls_cols_all[cl] += ncols;
+                    pc.fin_ms += el(k, 1, 2) + el(k, 3, 4);
+                    pc.upd_ms += el(k, 2, 3);
+                    pc.upd_bytes += 6 * vb;
+                    pc.pup_ms += el(k, 4, 5);
+                    pc.pup_bytes += 4 * vb;
                 }
             }
             if (n_act == 0) {
@@ -548,7 +624,7 @@ struct Solver {
         double* x64 = m->x64.as<double>();
         double* r64 = m->r64.as<double>();
         double* b64 = m->b64.as<double>();
-        RVE_TRY(residual64(nullptr, b64));   // b = -(macro load): the operator skips the gathers
+        RVE_TRY(rhs(b64, mixed));
         RVE_CUDA(cudaMemcpyAsync(r64, b64, nv * 8, cudaMemcpyDeviceToDevice, s));
         // reference norms (b, P b); r64 becomes the projected right-hand side
         std::vector<double> bn(ncols, 1.0);
@@ -606,21 +682,20 @@ struct Solver {
                     launch_axpy_f2d((int64_t)nv, y32, r64, s);      // r0 -= K_deg v
                     *launches += 3;
                     bool any_alpha = false;
-                    std::vector<double> sc64((size_t)ncols * 2);
                     for (int c = 0; c < ncols; ++c)
                         for (int ph = 0; ph < 2; ++ph) {
-                            sc64[2 * c + ph] = -warm->alpha[c] * warm->degrade[ph];
-                            any_alpha |= sc64[2 * c + ph] != 0.0;
+                            sc32[2 * c + ph] = (float)(warm->alpha[c] * warm->degrade[ph]);
+                            any_alpha |= sc32[2 * c + ph] != 0.0f;
                         }
                     if (any_alpha) {
-                        // r0 -= alpha K_deg u_macro (macro load only: the cheap FP64 path)
-                        RVE_TRY(upload(m->dscale64, sc64.data(), sc64.size(), s));
-                        launch_operator<double>(m->p, f.nc, true, ev<double>(m->dscale64), nullptr, r64, nullptr, L);
+                        // r0 -= alpha K_deg u_macro (macro load only, double-float)
+                        RVE_TRY(upload(m->dscale32, sc32.data(), sc32.size(), s));
+                        launch_residual_df(m->p, f.nc, ev<float>(m->dscale32), nullptr, r64, L);
                         *launches += 1;
                     }
                 }
             } else {
-                RVE_TRY(residual64(x64, r64));
+                RVE_TRY(mixed ? residual_df(x64, r64) : residual64(x64, r64));
             }
             RVE_TRY(zero_noise_columns());
             RVE_TRY(rel_residual(r64, bn, rel));
@@ -666,7 +741,7 @@ struct Solver {
                     launch_axpy_f2d((int64_t)nv, x32, x64, s);
                     *launches += 1;
                 }
-                RVE_TRY(residual64(x64, r64));
+                RVE_TRY(residual_df(x64, r64));
                 RVE_TRY(zero_noise_columns());
                 RVE_TRY(rel_residual(r64, bn, out.rel_res));
                 out.sweeps = sw + 1;
@@ -1185,6 +1260,7 @@ int rve_set_materials(rve_ctx c, rve_mesh m, const rve_matrix_props* mp, const r
     m->c_wt = c_wt;
     m->t_h = t_h;
     m->have_materials = true;
+    m->bph_valid[0] = m->bph_valid[1] = false;
     RVE_TRY(build_diagonals(m));
     return RVE_OK;
 }
@@ -1195,6 +1271,7 @@ int rve_set_bc(rve_ctx c, rve_mesh m, int bc) {
         set_error("rve_set_bc: invalid argument");
         return RVE_ERR_INVALID_ARGUMENT;
     }
+    m->bph_valid[0] = m->bph_valid[1] = false;
     const bool fold_changes = (bc == RVE_BC_PERIODIC) != (m->bc == RVE_BC_PERIODIC);
     const int old = m->bc;
     m->bc = bc;
@@ -1213,6 +1290,31 @@ int rve_set_bc(rve_ctx c, rve_mesh m, int bc) {
     RVE_TRY(build_field_data(m));
     if (m->have_materials) RVE_TRY(build_diagonals(m));
     return RVE_OK;
+}
+
+// Profile counters accumulated between two snapshots, into the caller's stats.
+static void fill_profile(const ProfCounters& a, const ProfCounters& b, rve_stats* st) {
+    st->op_ms = b.op_ms - a.op_ms;
+    st->op_launches = b.op_launches - a.op_launches;
+    st->op_bytes = b.op_bytes - a.op_bytes;
+    st->op_flops = b.op_flops - a.op_flops;
+    st->update_ms = b.upd_ms - a.upd_ms;
+    st->update_bytes = b.upd_bytes - a.upd_bytes;
+    st->pupdate_ms = b.pup_ms - a.pup_ms;
+    st->pupdate_bytes = b.pup_bytes - a.pup_bytes;
+    st->finalize_ms = b.fin_ms - a.fin_ms;
+    st->residual_ms = b.res_ms - a.res_ms;
+    st->residual_launches = b.res_launches - a.res_launches;
+    const double cols = b.op_cols_all - a.op_cols_all;
+    st->op_active_frac = cols > 0 ? (b.op_cols - a.op_cols) / cols : 0.0;
+    for (int k = 0; k < 6; ++k) {
+        st->op_class_ms[k] = b.cls_ms[k] - a.cls_ms[k];
+        st->op_class_launches[k] = b.cls_launches[k] - a.cls_launches[k];
+        st->op_class_bytes[k] = b.cls_bytes[k] - a.cls_bytes[k];
+        st->op_class_flops[k] = b.cls_flops[k] - a.cls_flops[k];
+        const double cc = b.cls_cols_all[k] - a.cls_cols_all[k];
+        st->op_class_active_frac[k] = cc > 0 ? (b.cls_cols[k] - a.cls_cols[k]) / cc : 0.0;
+    }
 }
 
 int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_stats* st) {
@@ -1238,29 +1340,13 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
     RVE_CUDA(cudaMemcpyAsync(d + 2, th, 8, cudaMemcpyHostToDevice, s));
     launch_degradation(1, d, d + 1, d + 2, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, d + 3, s);
     c->launches++;
-    const double op0 = c->op_ms, ob0 = c->op_bytes, of0 = c->op_flops;
-    const double u0 = c->upd_ms, ub0 = c->upd_bytes, pu0 = c->pup_ms, pb0 = c->pup_bytes, f0 = c->fin_ms;
-    const double rs0 = c->res_ms;
-    const double oc0 = c->op_cols, oa0 = c->op_cols_all;
-    const int64_t rl0 = c->res_launches;
-    const int64_t on0 = c->op_launches;
+    const ProfCounters pc0 = c->prof;
     int rc = homogenise_batch(m, 1, d + 3, C, K, D, st);
     RVE_CUDA(cudaStreamSynchronize(s));
     if (st) {
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st->kernel_launches = c->launches - l0;
-        st->op_ms = c->op_ms - op0;
-        st->op_launches = c->op_launches - on0;
-        st->op_bytes = c->op_bytes - ob0;
-        st->op_flops = c->op_flops - of0;
-        st->update_ms = c->upd_ms - u0;
-        st->update_bytes = c->upd_bytes - ub0;
-        st->pupdate_ms = c->pup_ms - pu0;
-        st->pupdate_bytes = c->pup_bytes - pb0;
-        st->finalize_ms = c->fin_ms - f0;
-        st->residual_ms = c->res_ms - rs0;
-        st->residual_launches = c->res_launches - rl0;
-        st->op_active_frac = c->op_cols_all > oa0 ? (c->op_cols - oc0) / (c->op_cols_all - oa0) : 0.0;
+        fill_profile(pc0, c->prof, st);
     }
     return rc;
 }
@@ -1383,30 +1469,14 @@ int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshe
         std::memset(st, 0, sizeof(*st));
         st->converged = 1;
     }
-    const double op0 = c->op_ms, ob0 = c->op_bytes, of0 = c->op_flops;
-    const double u0 = c->upd_ms, ub0 = c->upd_bytes, pu0 = c->pup_ms, pb0 = c->pup_bytes, f0 = c->fin_ms;
-    const double rs0 = c->res_ms;
-    const double oc0 = c->op_cols, oa0 = c->op_cols_all;
-    const int64_t rl0 = c->res_launches;
-    const int64_t on0 = c->op_launches;
+    const ProfCounters pc0 = c->prof;
     int rc = macro_update_impl(c, meshes, n_meshes, G, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev,
                                D_dev, status_dev, st);
     if (st) {
         cudaStreamSynchronize(c->stream);
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st->kernel_launches = c->launches - l0;
-        st->op_ms = c->op_ms - op0;
-        st->op_launches = c->op_launches - on0;
-        st->op_bytes = c->op_bytes - ob0;
-        st->op_flops = c->op_flops - of0;
-        st->update_ms = c->upd_ms - u0;
-        st->update_bytes = c->upd_bytes - ub0;
-        st->pupdate_ms = c->pup_ms - pu0;
-        st->pupdate_bytes = c->pup_bytes - pb0;
-        st->finalize_ms = c->fin_ms - f0;
-        st->residual_ms = c->res_ms - rs0;
-        st->residual_launches = c->res_launches - rl0;
-        st->op_active_frac = c->op_cols_all > oa0 ? (c->op_cols - oc0) / (c->op_cols_all - oa0) : 0.0;
+        fill_profile(pc0, c->prof, st);
     }
     return rc;
 }

@@ -93,6 +93,21 @@ struct FieldDev {
 
 }  // namespace rve
 
+namespace rve {
+// Profile-mode counters of a context (summed device times from CUDA events and the
+// algorithmic bytes / flops of the timed launches).  Operator classes are indexed
+// by 2 (p - 1) + (scalar field ? 1 : 0).
+struct ProfCounters {
+    double op_ms = 0, op_bytes = 0, op_flops = 0, op_cols = 0, op_cols_all = 0;
+    int64_t op_launches = 0;
+    double upd_ms = 0, upd_bytes = 0, pup_ms = 0, pup_bytes = 0, fin_ms = 0;
+    double res_ms = 0;
+    int64_t res_launches = 0;
+    double cls_ms[6] = {}, cls_bytes[6] = {}, cls_flops[6] = {}, cls_cols[6] = {}, cls_cols_all[6] = {};
+    int64_t cls_launches[6] = {};
+};
+}  // namespace rve
+
 struct rve_ctx_s {
     rve_options opt;
     cudaStream_t stream = nullptr;
@@ -102,13 +117,7 @@ struct rve_ctx_s {
     int64_t launches = 0;
     // profile mode: event pairs around every operator launch of a captured body
     std::vector<cudaEvent_t> ev;
-    double op_ms = 0;
-    int64_t op_launches = 0;
-    double op_bytes = 0, op_flops = 0;
-    double upd_ms = 0, upd_bytes = 0, pup_ms = 0, pup_bytes = 0, fin_ms = 0;
-    double res_ms = 0;          // FP64 true-residual operator applications
-    double op_cols = 0, op_cols_all = 0;   // active and total columns over operator launches
-    int64_t res_launches = 0;
+    rve::ProfCounters prof;
     ~rve_ctx_s() {
         for (auto e : ev) cudaEventDestroy(e);
     }
@@ -143,6 +152,11 @@ struct rve_mesh_s {
     // warm start: the previous batch's FP64 solutions per field and their factors
     rve::DevBuf warm[2], warm_r[2], warm_map, warm_coef, warm_dcoef;
     rve::DevBuf dscale32, dscale64;   // per-column phase scales of the warm-start residual
+    // per field: K_ph u_macro for each phase at unit modulus, [2][n_rows][6] (FP64),
+    // so that a batch's right-hand side is a per-column combination of them
+    rve::DevBuf bph[2];
+    bool bph_valid[2] = {false, false};
+    int bph_prec[2] = {0, 0};         // precision the cached loads were formed in
     int warm_cols[2] = {0, 0};
     std::vector<double> warm_w[2];
 };

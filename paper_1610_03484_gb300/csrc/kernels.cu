@@ -339,6 +339,240 @@ template void launch_operator<float>(int, int, bool, const ElemView<float>&, con
 template void launch_operator<double>(int, int, bool, const ElemView<double>&, const double*,
                                       double*, double*, const Launch&, const int32_t*);
 
+// ------------------------------------- double-float residual (mixed precision)
+// r += -K32 (x + u_macro) for FP64 x (x = nullptr: zero), where K32 is the operator with exactly the
+// FP32 element data and tables of the FP32 kernel above, evaluated in
+// double-float arithmetic: every FP32 x FP32 product is split exactly
+// (p + e = a b with e = fma(a, b, -p)) and every sum carries its rounding error
+// in a second FP32 word (Knuth's two-sum).  Relative accuracy is about 2^-44 per
+// stage, against 2^-53 in FP64 at 1/64 of the FP32 arithmetic rate on this GPU.
+// x enters as x_h + x_l (two FP32 words; the FP64 remainder below 2^-48 |x| is
+// dropped).  The result is scattered with FP64 atomics.
+
+// s += a * (bh + bl) for an exact FP32 a; the low word collects the error terms.
+// The _rn intrinsics keep the compiler from contracting a product and a sum into
+// one FMA, which would break the exact error terms.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float a, float bh, float bl) {
+    const float ph = __fmul_rn(a, bh);
+    const float pl = fmaf(a, bh, -ph);
+    const float t = __fadd_rn(sh, ph);
+    const float bb = __fsub_rn(t, sh);
+    const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(ph, bb));
+    sh = t;
+    sl += e + fmaf(a, bl, pl);
+}
+// s += (bh + bl)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+    const float t = __fadd_rn(sh, bh);
+    const float bb = __fsub_rn(t, sh);
+    const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(bh, bb));
+    sh = t;
+    sl += e + bl;
+}
+// (h, l) <- (h + l) renormalised so that |l| <= ulp(h) / 2
+__device__ __forceinline__ void df_norm(float& h, float& l) {
+    const float t = __fadd_rn(h, l);
+    l = __fsub_rn(l, __fsub_rn(t, h));
+    h = t;
+}
+__device__ __forceinline__ void df_split(double v, float& h, float& l) {
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - (double)h);
+}
+
+template <int P, int NC>
+__global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, const double* __restrict__ x,
+                                                        double* __restrict__ r, int ncols, int cpb) {
+    constexpr int NE = Order<P>::NE;
+    constexpr int NM = Order<P>::NM;
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    const int field = (col % 6) >= 3 ? 1 : 0;
+    const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
+    for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < ev.nt; e += (int64_t)gridDim.y * rows) {
+        const int32_t* ed = ev.edofs + e * NE;
+        float Vh[NM][3][NC], Vl[NM][3][NC];
+        if (x == nullptr) {   // macro load only
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) Vh[m][k][c] = Vl[m][k][c] = 0.f;
+        } else {
+            const int d0 = __ldg(ed);
+            double x0[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) x0[c] = x[((int64_t)d0 * NC + c) * ncols + col];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int dk = __ldg(ed + k + 1);
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    df_split(x[((int64_t)dk * NC + c) * ncols + col] - x0[c], Vh[0][k][c], Vl[0][k][c]);
+            }
+#pragma unroll
+            for (int m = 1; m < NM; ++m)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) Vh[m][k][c] = Vl[m][k][c] = 0.f;
+        }
+#pragma unroll
+        for (int j = 4; j < NE; ++j) {
+            if (x == nullptr) break;
+            const int dj = __ldg(ed + j);
+            float xh[NC], xl[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) df_split(x[((int64_t)dj * NC + c) * ncols + col], xh[c], xl[c]);
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float a = basis_a<P, float>((k * NM + m) * NE + j);
+                    if (a != 0.f)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) df_mac(Vh[m][k][c], Vl[m][k][c], a, xh[c], xl[c]);
+                }
+        }
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) df_norm(Vh[m][k][c], Vl[m][k][c]);
+        // element data exactly as the FP32 kernel forms it
+        float G[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) G[i] = __ldg(ev.geo + e * 10 + i);
+        const float sv = __ldg(ev.scale + col * 2 + __ldg(ev.phase + e)) * __ldg(ev.geo + e * 10 + 9);
+        constexpr int NMAT = NC == 3 ? 21 : 6;
+        float Dm[NMAT];
+#pragma unroll
+        for (int i = 0; i < NMAT; ++i)
+            Dm[i] = sv * __ldg(ev.mat + e * (NC == 3 ? 21 : 12) + (NC == 3 ? 0 : 6 * field) + i);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            float Hh[NC][3], Hl[NC][3];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    Hh[c][l] = Hl[c][l] = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) df_mac(Hh[c][l], Hl[c][l], G[3 * k + l], Vh[m][k][c], Vl[m][k][c]);
+                }
+            if (m == 0) {
+                if constexpr (NC == 3) {
+                    if (macro_id < 3) {
+                        df_add(Hh[macro_id][macro_id], Hl[macro_id][macro_id], 1.f, 0.f);
+                    } else {
+                        const int a = macro_id == 3 ? 0 : (macro_id == 4 ? 1 : 2);
+                        const int b = macro_id == 3 ? 1 : (macro_id == 4 ? 2 : 0);
+                        df_add(Hh[a][b], Hl[a][b], 0.5f, 0.f);
+                        df_add(Hh[b][a], Hl[b][a], 0.5f, 0.f);
+                    }
+                } else {
+                    df_add(Hh[0][macro_id], Hl[0][macro_id], 1.f, 0.f);
+                }
+            }
+            float Sh[NC][3], Sl[NC][3];
+            if constexpr (NC == 3) {
+                float eh[6] = {Hh[0][0], Hh[1][1], Hh[2][2], Hh[0][1], Hh[1][2], Hh[2][0]};
+                float el[6] = {Hl[0][0], Hl[1][1], Hl[2][2], Hl[0][1], Hl[1][2], Hl[2][0]};
+                df_add(eh[3], el[3], Hh[1][0], Hl[1][0]);
+                df_add(eh[4], el[4], Hh[2][1], Hl[2][1]);
+                df_add(eh[5], el[5], Hh[0][2], Hl[0][2]);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) df_norm(eh[i], el[i]);
+                float gh[6], gl[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    gh[i] = gl[i] = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < 6; ++jj) df_mac(gh[i], gl[i], Dm[ut6(i, jj)], eh[jj], el[jj]);
+                }
+                const int vi[3][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}};
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        Sh[a][b] = gh[vi[a][b]];
+                        Sl[a][b] = gl[vi[a][b]];
+                    }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) df_norm(Hh[0][q], Hl[0][q]);
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    Sh[0][l] = Sl[0][l] = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) df_mac(Sh[0][l], Sl[0][l], Dm[s3(l, q)], Hh[0][q], Hl[0][q]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) df_norm(Sh[c][l], Sl[c][l]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    float wh = 0.f, wl = 0.f;
+#pragma unroll
+                    for (int l = 0; l < 3; ++l) df_mac(wh, wl, G[3 * k + l], Sh[c][l], Sl[c][l]);
+                    df_norm(wh, wl);
+                    Vh[m][k][c] = wh;
+                    Vl[m][k][c] = wl;
+                }
+        }
+        // backward and scatter of -(K (x + u_macro))
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            float sh = Vh[0][0][c], sl = Vl[0][0][c];
+            df_add(sh, sl, Vh[0][1][c], Vl[0][1][c]);
+            df_add(sh, sl, Vh[0][2][c], Vl[0][2][c]);
+            atomicAdd(r + ((int64_t)__ldg(ed) * NC + c) * ncols + col, (double)sh + (double)sl);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                atomicAdd(r + ((int64_t)__ldg(ed + k + 1) * NC + c) * ncols + col,
+                          -((double)Vh[0][k][c] + (double)Vl[0][k][c]));
+        }
+#pragma unroll
+        for (int j = 4; j < NE; ++j) {
+            float yh[NC], yl[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) yh[c] = yl[c] = 0.f;
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float a = basis_a<P, float>((k * NM + m) * NE + j);
+                    if (a != 0.f)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) df_mac(yh[c], yl[c], a, Vh[m][k][c], Vl[m][k][c]);
+                }
+            const int dj = __ldg(ed + j);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                atomicAdd(r + ((int64_t)dj * NC + c) * ncols + col, -((double)yh[c] + (double)yl[c]));
+        }
+    }
+}
+
+void launch_residual_df(int p, int nc, const ElemView<float>& ev, const double* x, double* r, const Launch& L) {
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+#define RVE_DF_CASE(PP, NCC)                                                               \
+    if (p == PP && nc == NCC) {                                                            \
+        k_residual_df<PP, NCC><<<grid, block, 0, L.stream>>>(ev, x, r, L.ncols, L.cpb);    \
+        return;                                                                            \
+    }
+    RVE_DF_CASE(1, 3) RVE_DF_CASE(2, 3) RVE_DF_CASE(3, 3)
+    RVE_DF_CASE(1, 1) RVE_DF_CASE(2, 1) RVE_DF_CASE(3, 1)
+#undef RVE_DF_CASE
+}
+
 // ------------------------------------------------------ Jacobi diagonal (K6)
 // diag[field][phase][row] = unscaled diagonal of K restricted to one phase.
 template <int P, int NC, typename T>
@@ -1182,6 +1416,28 @@ template void launch_combine_columns<double>(int64_t, int, int, const int32_t*, 
                                              double*, cudaStream_t);
 template void launch_combine_columns<float>(int64_t, int, int, const int32_t*, const double*, const double*,
                                             float*, cudaStream_t);
+
+// b[row][6r + c] = -(s0 y0[row][c] + s1 y1[row][c]) with the column's phase scales
+__global__ void k_rhs_combine(int64_t n_rows, int nrve, const double* __restrict__ y,
+                              const double* __restrict__ scale, double* __restrict__ b) {
+    const int ncols = 6 * nrve;
+    const int64_t n = n_rows * ncols;
+    const double* y1 = y + n_rows * 6;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / ncols;
+        const int col = (int)(i % ncols);
+        const int c = col % 6;
+        b[i] = -(scale[2 * col] * y[row * 6 + c] + scale[2 * col + 1] * y1[row * 6 + c]);
+    }
+}
+
+void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,
+                        cudaStream_t s) {
+    int64_t blocks = (n_rows * 6 * nrve + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_rhs_combine<<<(unsigned)blocks, 256, 0, s>>>(n_rows, nrve, y, scale, b);
+}
 
 // ---------------------------------------------------------- elementwise
 __global__ void k_cast_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {

@@ -134,6 +134,14 @@ template <typename TO>
 void launch_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* coef,
                             const double* src, TO* x, cudaStream_t s);
 
+// r += -K32 (x + u_macro) in double-float arithmetic (FP32 element data, FP64 x and r;
+// r must hold zero or a value to accumulate onto)
+void launch_residual_df(int p, int nc, const ElemView<float>& ev, const double* x, double* r, const Launch& L);
+
+// right-hand sides of a batch from the per-phase macro loads y = [2][n_rows][6]
+void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,
+                        cudaStream_t s);
+
 // elementwise helpers
 void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 void launch_axpy_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
