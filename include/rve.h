@@ -148,6 +148,9 @@ typedef struct rve_stats {
     double  op_class_bytes[6];
     double  op_class_flops[6];
     double  op_class_active_frac[6];
+    /* every call: host time spent capturing and instantiating the PCG graphs, and their number */
+    double  graph_host_ms;
+    int64_t graphs;
 } rve_stats;
 
 /* ------------------------------------------------------------------ calls */
@@ -208,6 +211,21 @@ int macro_update_gauss_points_dev(rve_ctx ctx, const rve_mesh* meshes, int n_mes
                                   const double* t_h_dev, const int32_t* mesh_id_host,
                                   double* C_dev, double* K_dev, double* D_dev,
                                   int32_t* status_dev, int mode, rve_stats* stats);
+
+/* Batch-size autotuner for one mesh (scheduling; no counterpart in the paper).
+ * Solves the n sample states (host arrays, all on mesh m) once untimed, then
+ * once per candidate batch size (candidates: n_cand sizes, or NULL / 0 for
+ * {8, 16, 32, 64, 128, 256}), times each pass on the host clock, and keeps the
+ * fastest: later calls with options.batch == 0 solve this mesh in batches of
+ * *best.  rates (optional, n_cand or 6 entries) receives each candidate's
+ * homogenisations per second (0 for one that failed).  The sample should
+ * follow the distribution of the states the mesh will see: the warm starts
+ * make the rate depend on how densely the degradation factors fall.  Fails
+ * with RVE_ERR_STATE before rve_set_materials; a candidate that does not fit
+ * in device memory ends the search with RVE_ERR_OUT_OF_MEMORY. */
+int rve_autotune_batch(rve_ctx ctx, rve_mesh m, int64_t n, const double* T_C, const double* c_wt,
+                       const double* t_h, const int32_t* candidates, int n_cand, int32_t* best,
+                       double* rates);
 
 /* ------------------------------------------------------- learned surrogate
  * No counterpart in the paper: an ensemble of MLPs (8 features -> 4 x 256

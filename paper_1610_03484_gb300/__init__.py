@@ -71,7 +71,8 @@ class Stats(C.Structure):
                 ("op_active_frac", C.c_double),
                 ("op_class_ms", C.c_double * 6), ("op_class_launches", C.c_int64 * 6),
                 ("op_class_bytes", C.c_double * 6), ("op_class_flops", C.c_double * 6),
-                ("op_class_active_frac", C.c_double * 6)]
+                ("op_class_active_frac", C.c_double * 6),
+                ("graph_host_ms", C.c_double), ("graphs", C.c_int64)]
 
     def as_dict(self):
         return {n: (list(v) if isinstance(v, C.Array) else v)
@@ -98,6 +99,8 @@ _SIGS = {
     "rve_set_bc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "rve_homogenise": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.POINTER(Stats)]),
+    "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
     "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Stats)]),
@@ -403,6 +406,21 @@ class Mesh:
 
     def set_bc(self, bc: int):
         _check(self.ctx.lib.rve_set_bc(self.ctx.h, self.h, int(bc)), "rve_set_bc")
+
+    def autotune_batch(self, T_C, c_wt, t_h, candidates=None):
+        """Time candidate batch sizes on sample states of this mesh and keep the
+        fastest for later batched calls; returns (best, {candidate: rate})."""
+        T = np.ascontiguousarray(T_C, np.float64)
+        cw = np.ascontiguousarray(c_wt, np.float64)
+        th = np.ascontiguousarray(t_h, np.float64)
+        cand = np.ascontiguousarray(candidates if candidates is not None else [8, 16, 32, 64, 128, 256],
+                                    np.int32)
+        rates = np.zeros(len(cand))
+        best = C.c_int32(0)
+        _check(self.ctx.lib.rve_autotune_batch(self.ctx.h, self.h, len(T), _ptr(T), _ptr(cw), _ptr(th),
+                                                _ptr(cand), len(cand), C.byref(best), _ptr(rates)),
+               "rve_autotune_batch")
+        return int(best.value), {int(b): float(r) for b, r in zip(cand, rates)}
 
     def homogenise(self, allow_not_converged=False) -> Result:
         Cc = np.zeros((6, 6))

@@ -270,14 +270,15 @@ struct Solver {
     FieldDev& f;
     int B, ncols;
     int64_t n_rows;
+    int fid;   // 0 mechanics, 1 scalar fields
     Launch L;
     cudaStream_t s;
     ColState cs64{};
     int64_t* launches;
 
     Solver(rve_mesh mm, FieldDev& ff, int b)
-        : m(mm), f(ff), B(b), ncols(6 * b), n_rows(ff.n_rows), s(mm->ctx->stream),
-          launches(&mm->ctx->launches) {
+        : m(mm), f(ff), B(b), ncols(6 * b), n_rows(ff.n_rows), fid(&ff == &mm->mech ? 0 : 1),
+          s(mm->ctx->stream), launches(&mm->ctx->launches) {
         L = make_launch(ncols, std::max<int64_t>(n_rows, mm->nt), s);
     }
 
@@ -316,8 +317,8 @@ struct Solver {
 
     int alloc(bool mixed) {
         const size_t nv = (size_t)n_rows * ncols;
-        RVE_TRY(m->x64.ensure(nv * 8));
-        RVE_TRY(m->r64.ensure(nv * 8));
+        RVE_TRY(m->x64f[fid].ensure(nv * 8));
+        RVE_TRY(m->r64f[fid].ensure(nv * 8));
         RVE_TRY(m->b64.ensure(nv * 8));
         if (mixed) {
             RVE_TRY(m->x32.ensure(nv * 4));
@@ -362,7 +363,6 @@ struct Solver {
     // double-float evaluation of the FP32-data operator, so that its right-hand
     // side and true residual belong to one and the same discrete system.
     int rhs(double* b, bool mixed) {
-        const int fid = (&f == &m->mech) ? 0 : 1;
         const int prec = mixed ? RVE_PREC_MIXED : RVE_PREC_FP64;
         if (!m->bph_valid[fid] || m->bph_prec[fid] != prec) {
             const size_t n6 = (size_t)n_rows * 6;
@@ -379,10 +379,13 @@ struct Solver {
                 double* y = m->bph[fid].as<double>() + ph * n6;
                 if (mixed) {
                     // the double-float kernel returns -K u_macro: stored negated
+                    float* lo = m->q32.as<float>();
                     RVE_TRY(upload(m->dscale32, sc32, 12, s));
-                    launch_residual_df(m->p, f.nc, ev<float>(m->dscale32), nullptr, y, L6);
+                    RVE_CUDA(cudaMemsetAsync(lo, 0, n6 * 4, s));
+                    launch_residual_df(m->p, f.nc, ev<float>(m->dscale32), nullptr, nullptr, y, lo, L6);
+                    launch_axpy_f2d((int64_t)n6, lo, y, s);
                     launch_neg((int64_t)n6, y, s);
-                    *launches += 2;
+                    *launches += 3;
                 } else {
                     RVE_TRY(upload(m->dscale64, sc, 12, s));
                     launch_operator<double>(m->p, f.nc, true, ev<double>(m->dscale64), nullptr, y, nullptr, L6);
@@ -407,9 +410,18 @@ struct Solver {
             evs.push_back(e);
         }
         if (prof) RVE_CUDA(cudaEventRecord(evs[0], s));
-        RVE_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n_rows * ncols, s));
-        launch_residual_df(m->p, f.nc, ev<float>(m->scale32), x, y, L);
-        *launches += 1;
+        // FP32 scratch: x32 and p32 hold the split x, q32 the low words of r
+        // (free between inner solves)
+        const size_t nv = (size_t)n_rows * ncols;
+        float* xh = m->x32.as<float>();
+        float* xl = m->p32.as<float>();
+        float* lo = m->q32.as<float>();
+        RVE_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * nv, s));
+        RVE_CUDA(cudaMemsetAsync(lo, 0, sizeof(float) * nv, s));
+        launch_split_d2ff((int64_t)nv, x, xh, xl, s);
+        launch_residual_df(m->p, f.nc, ev<float>(m->scale32), xh, xl, y, lo, L);
+        launch_axpy_f2d((int64_t)nv, lo, y, s);
+        *launches += 3;
         if (prof) {
             RVE_CUDA(cudaEventRecord(evs[1], s));
             RVE_CUDA(cudaEventSynchronize(evs[1]));
@@ -509,6 +521,7 @@ struct Solver {
         // the event pairs around each operator launch can be timed.
         cudaGraphExec_t exec = nullptr;
         if (!prof) {
+            const auto g0 = std::chrono::steady_clock::now();
             Launch Lc = L;
             Lc.stream = m->ctx->capture;
             cudaGraph_t graph = nullptr;
@@ -518,6 +531,9 @@ struct Solver {
             cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             RVE_CUDA(ge);
+            m->ctx->prof.graph_host_ms +=
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g0).count();
+            m->ctx->prof.graphs++;
         }
         struct ExecGuard {
             cudaGraphExec_t e;
@@ -602,7 +618,7 @@ struct Solver {
             launch_constraint_multipliers(f.m, m->cpart.as<double>(), cs, L);
             *launches += 4;
         }
-        launch_project_residual<double>(rvw, r, cs, m->rzp.as<double>(), L);
+        launch_project_residual(rvw, rv<float>(m->scale32), r, cs, m->rzp.as<double>(), L);
         launch_reduce_partials(L.nby, ncols, m->rzp.as<double>(), m->gsum.as<double>(), s);
         *launches += 2;
         std::vector<double> rz(ncols);
@@ -621,17 +637,17 @@ struct Solver {
         const bool mixed = precision == RVE_PREC_MIXED;
         RVE_TRY(alloc(mixed));
         const size_t nv = (size_t)n_rows * ncols;
-        double* x64 = m->x64.as<double>();
-        double* r64 = m->r64.as<double>();
+        double* x64 = m->x64f[fid].as<double>();
+        double* r64 = m->r64f[fid].as<double>();
         double* b64 = m->b64.as<double>();
         RVE_TRY(rhs(b64, mixed));
-        RVE_CUDA(cudaMemcpyAsync(r64, b64, nv * 8, cudaMemcpyDeviceToDevice, s));
-        // reference norms (b, P b); r64 becomes the projected right-hand side
+        // reference norms (b, P b); b is projected in place, which leaves the energy
+        // reductions unchanged: (P b) . u = b . u for every admissible u
         std::vector<double> bn(ncols, 1.0);
         {
             double dummy;
             std::vector<double> ones(ncols, 1.0);
-            RVE_TRY(rel_residual(r64, ones, dummy, &bn));
+            RVE_TRY(rel_residual(b64, ones, dummy, &bn));
         }
         // A column whose projected right-hand side is rounding noise (a single-phase
         // RVE, whose exact fluctuation is zero) is solved by u = 0: its (b, P b)
@@ -689,9 +705,12 @@ struct Solver {
                         }
                     if (any_alpha) {
                         // r0 -= alpha K_deg u_macro (macro load only, double-float)
+                        float* lo = m->q32.as<float>();
                         RVE_TRY(upload(m->dscale32, sc32.data(), sc32.size(), s));
-                        launch_residual_df(m->p, f.nc, ev<float>(m->dscale32), nullptr, r64, L);
-                        *launches += 1;
+                        RVE_CUDA(cudaMemsetAsync(lo, 0, nv * 4, s));
+                        launch_residual_df(m->p, f.nc, ev<float>(m->dscale32), nullptr, nullptr, r64, lo, L);
+                        launch_axpy_f2d((int64_t)nv, lo, r64, s);
+                        *launches += 2;
                     }
                 }
             } else {
@@ -700,6 +719,7 @@ struct Solver {
             RVE_TRY(zero_noise_columns());
             RVE_TRY(rel_residual(r64, bn, rel));
         } else {
+            RVE_CUDA(cudaMemcpyAsync(r64, b64, nv * 8, cudaMemcpyDeviceToDevice, s));
             RVE_CUDA(cudaMemsetAsync(x64, 0, nv * 8, s));
             RVE_TRY(zero_noise_columns());
         }
@@ -756,12 +776,9 @@ struct Solver {
         if (mixed) {
             // the volume-averaged stress is a diagnostic (Hill-Mandel): FP32 with
             // compensated sums, as the inner solve
-            float* u32 = m->x32.as<float>();
-            launch_cast_d2f((int64_t)nv, x64, u32, s);
-            launch_mean_stress<float>(m->p, f.nc, ev<float>(m->scale32), u32, m->mpart.as<double>(), L);
-            *launches += 1;
+            launch_mean_stress<float, double>(m->p, f.nc, ev<float>(m->scale32), x64, m->mpart.as<double>(), L);
         } else {
-            launch_mean_stress<double>(m->p, f.nc, ev<double>(m->scale64), x64, m->mpart.as<double>(), L);
+            launch_mean_stress<double, double>(m->p, f.nc, ev<double>(m->scale64), x64, m->mpart.as<double>(), L);
         }
         launch_reduce_partials(L.nby, ncols * 12, m->mpart.as<double>(), m->msum.as<double>(), s);
         *launches += 4;
@@ -912,12 +929,9 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
     auto keep_warm = [&](int f, FieldDev& fd) -> int {
         if (!w_host) return RVE_OK;
         const size_t nb = (size_t)fd.n_rows * 6 * B * 8;
-        RVE_TRY(m->warm[f].ensure(nb));
-        RVE_CUDA(cudaMemcpyAsync(m->warm[f].p, m->x64.p, nb, cudaMemcpyDeviceToDevice, s));
-        if (mixed) {
-            RVE_TRY(m->warm_r[f].ensure(nb));
-            RVE_CUDA(cudaMemcpyAsync(m->warm_r[f].p, m->r64.p, nb, cudaMemcpyDeviceToDevice, s));
-        }
+        (void)nb;
+        m->warm[f].swap(m->x64f[f]);
+        if (mixed) m->warm_r[f].swap(m->r64f[f]);
         m->warm_cols[f] = 6 * B;
         m->warm_w[f].assign(w_host, w_host + B);
         return RVE_OK;
@@ -1305,6 +1319,8 @@ static void fill_profile(const ProfCounters& a, const ProfCounters& b, rve_stats
     st->finalize_ms = b.fin_ms - a.fin_ms;
     st->residual_ms = b.res_ms - a.res_ms;
     st->residual_launches = b.res_launches - a.res_launches;
+    st->graph_host_ms = b.graph_host_ms - a.graph_host_ms;
+    st->graphs = b.graphs - a.graphs;
     const double cols = b.op_cols_all - a.op_cols_all;
     st->op_active_frac = cols > 0 ? (b.op_cols - a.op_cols) / cols : 0.0;
     for (int k = 0; k < 6; ++k) {
@@ -1393,7 +1409,7 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
             set_error("mesh without materials in macro_update_gauss_points");
             return RVE_ERR_STATE;
         }
-        const int Bmax = c->opt.batch > 0 ? c->opt.batch : auto_batch(m);
+        const int Bmax = c->opt.batch > 0 ? c->opt.batch : (m->tuned_batch > 0 ? m->tuned_batch : auto_batch(m));
         // order the points by degradation factor so that each batch starts from
         // the solutions of its neighbours in the previous batch; no solution is
         // carried over from an earlier call
@@ -1512,6 +1528,63 @@ int macro_update_gauss_points(rve_ctx c, const rve_mesh* meshes, int n_meshes, i
     RVE_CUDA(cudaMemcpyAsync(status, dS, G * 4, cudaMemcpyDeviceToHost, s));
     RVE_CUDA(cudaStreamSynchronize(s));
     return rc;
+}
+
+int rve_autotune_batch(rve_ctx c, rve_mesh m, int64_t n, const double* T_C, const double* c_wt,
+                       const double* t_h, const int32_t* candidates, int n_cand, int32_t* best,
+                       double* rates) {
+    RVE_TRY(check_ctx(c));
+    if (!m || n <= 0 || !T_C || !c_wt || !t_h || !best || n_cand < 0 || (n_cand > 0 && !candidates)) {
+        set_error("rve_autotune_batch: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (!m->have_materials) {
+        set_error("rve_autotune_batch: materials not set");
+        return RVE_ERR_STATE;
+    }
+    static const int32_t dflt[] = {8, 16, 32, 64, 128, 256};
+    const int32_t* cand = n_cand > 0 ? candidates : dflt;
+    const int nc = n_cand > 0 ? n_cand : 6;
+    for (int k = 0; k < nc; ++k)
+        if (cand[k] < 1) {
+            set_error("rve_autotune_batch: candidate batch sizes must be positive");
+            return RVE_ERR_INVALID_ARGUMENT;
+        }
+    std::vector<double> C((size_t)n * 36), K((size_t)n * 9), D((size_t)n * 9);
+    std::vector<int32_t> st((size_t)n), mid((size_t)n, 0);
+    const int saved = c->opt.batch;
+    rve_mesh ms[1] = {m};
+    auto run = [&](int B, double& secs) -> int {
+        c->opt.batch = B;
+        const auto t0 = std::chrono::steady_clock::now();
+        int rc = macro_update_gauss_points(c, ms, 1, n, T_C, c_wt, t_h, mid.data(), C.data(), K.data(),
+                                           D.data(), st.data(), RVE_MODE_PCG, nullptr);
+        secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return rc;
+    };
+    // one untimed pass forms the per-mesh caches and the device buffers
+    double secs = 0;
+    int rc = run(cand[0], secs);
+    int bestB = 0;
+    double bestRate = 0;
+    for (int k = 0; k < nc && (rc == RVE_OK || rc == RVE_ERR_NOT_CONVERGED); ++k) {
+        rc = run(cand[k], secs);
+        const double rate = (rc == RVE_OK && secs > 0) ? (double)n / secs : 0.0;
+        if (rates) rates[k] = rate;
+        if (rate > bestRate) {
+            bestRate = rate;
+            bestB = cand[k];
+        }
+    }
+    c->opt.batch = saved;
+    if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED) return rc;
+    if (bestB == 0) {
+        set_error("rve_autotune_batch: no candidate converged");
+        return RVE_ERR_NOT_CONVERGED;
+    }
+    m->tuned_batch = bestB;
+    *best = bestB;
+    return RVE_OK;
 }
 
 int rve_degradation_factor(rve_ctx c, int64_t n, const double* T_C, const double* c_wt,

@@ -40,6 +40,14 @@ struct DevBuf {
         o.p = nullptr;
         o.bytes = 0;
     }
+    void swap(DevBuf& o) noexcept {
+        void* tp = p;
+        p = o.p;
+        o.p = tp;
+        const size_t tb = bytes;
+        bytes = o.bytes;
+        o.bytes = tb;
+    }
     DevBuf& operator=(DevBuf&& o) noexcept {
         if (this != &o) {
             release();
@@ -103,6 +111,8 @@ struct ProfCounters {
     double upd_ms = 0, upd_bytes = 0, pup_ms = 0, pup_bytes = 0, fin_ms = 0;
     double res_ms = 0;
     int64_t res_launches = 0;
+    double graph_host_ms = 0;   // host time capturing and instantiating PCG graphs (always counted)
+    int64_t graphs = 0;
     double cls_ms[6] = {}, cls_bytes[6] = {}, cls_flops[6] = {}, cls_cols[6] = {}, cls_cols_all[6] = {};
     int64_t cls_launches[6] = {};
 };
@@ -139,6 +149,7 @@ struct rve_mesh_s {
     rve::DevBuf d_matm64, d_matm32, d_mats64, d_mats32;
     rve::FieldDev mech, scal;
     bool have_materials = false;
+    int tuned_batch = 0;   // batch size chosen by rve_autotune_batch (0: the built-in rule)
     // per phase: sum over its tets of |T| times the diagonal of D (6, mechanics) and of
     // k (3) and d (3), internal units; the energy scale of each unit load case
     double phase_voigt[2][12] = {};
@@ -146,7 +157,10 @@ struct rve_mesh_s {
     rve_degradation deg{};
     double T_C = 20, c_wt = 0, t_h = 0;
     // solve workspace
-    rve::DevBuf x64, r64, b64, p64, q64, x32, r32, p32, q32;
+    // FP64 solution and residual per field (mechanics, scalar); swapped with the
+    // warm-start buffers after a batch instead of copied
+    rve::DevBuf x64f[2], r64f[2];
+    rve::DevBuf b64, p64, q64, x32, r32, p32, q32;
     rve::DevBuf epart, rzp, cpart, gpart, mpart, gsum, msum;
     rve::DevBuf colstate, scale64, scale32, wdev;
     // warm start: the previous batch's FP64 solutions per field and their factors

@@ -153,7 +153,7 @@ __device__ __forceinline__ double block_sum(double v) {
 // the unit macro strain / gradient of the column is added to the constant mode,
 // so -y is the fluctuation problem's residual b - K x.
 template <int P, int NC, typename T, bool MACRO>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 2) ? 2 : 1) k_operator(ElemView<T> ev, const T* __restrict__ x,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof(T) == 4 && P == 2) ? 2 : 1)) k_operator(ElemView<T> ev, const T* __restrict__ x,
                                                   T* __restrict__ y, double* __restrict__ epart,
                                                   const int32_t* __restrict__ active, int ncols,
                                                   int cpb) {
@@ -340,14 +340,17 @@ template void launch_operator<double>(int, int, bool, const ElemView<double>&, c
                                       double*, double*, const Launch&, const int32_t*);
 
 // ------------------------------------- double-float residual (mixed precision)
-// r += -K32 (x + u_macro) for FP64 x (x = nullptr: zero), where K32 is the operator with exactly the
-// FP32 element data and tables of the FP32 kernel above, evaluated in
-// double-float arithmetic: every FP32 x FP32 product is split exactly
-// (p + e = a b with e = fma(a, b, -p)) and every sum carries its rounding error
-// in a second FP32 word (Knuth's two-sum).  Relative accuracy is about 2^-44 per
-// stage, against 2^-53 in FP64 at 1/64 of the FP32 arithmetic rate on this GPU.
-// x enters as x_h + x_l (two FP32 words; the FP64 remainder below 2^-48 |x| is
-// dropped).  The result is scattered with FP64 atomics.
+// r += -K32 (x + u_macro), where K32 is the operator with exactly the FP32
+// element data and tables of the FP32 kernel above, evaluated in double-float
+// arithmetic: every FP32 x FP32 product is split exactly (p + e = a b with
+// e = fma(a, b, -p)) and every sum carries its rounding error in a second FP32
+// word (Knuth's two-sum).  Relative accuracy is about 2^-44 per stage, against
+// 2^-53 in FP64 at 1/64 of the FP32 arithmetic rate on this GPU.  x enters split
+// beforehand into two FP32 words x_h + x_l (x_h = nullptr: x = 0; the FP64
+// remainder below 2^-48 |x| is dropped).  The high word of each result goes to
+// r_hi with an FP64 atomic, the low word to r_lo with an FP32 atomic (its own
+// rounding is 2^-24 of a word already 2^-24 below the high one); the caller adds
+// r_lo into r_hi afterwards.  No FP64 arithmetic runs per element.
 
 // s += a * (bh + bl) for an exact FP32 a; the low word collects the error terms.
 // The _rn intrinsics keep the compiler from contracting a product and a sum into
@@ -381,8 +384,9 @@ __device__ __forceinline__ void df_split(double v, float& h, float& l) {
 }
 
 template <int P, int NC>
-__global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, const double* __restrict__ x,
-                                                        double* __restrict__ r, int ncols, int cpb) {
+__global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, const float* __restrict__ xh,
+                                                        const float* __restrict__ xl, double* __restrict__ r,
+                                                        float* __restrict__ rlo, int ncols, int cpb) {
     constexpr int NE = Order<P>::NE;
     constexpr int NM = Order<P>::NM;
     const int rows = blockDim.x / cpb;
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
     for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < ev.nt; e += (int64_t)gridDim.y * rows) {
         const int32_t* ed = ev.edofs + e * NE;
         float Vh[NM][3][NC], Vl[NM][3][NC];
-        if (x == nullptr) {   // macro load only
+        if (xh == nullptr) {   // macro load only
 #pragma unroll
             for (int m = 0; m < NM; ++m)
 #pragma unroll
@@ -402,15 +406,23 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
                     for (int c = 0; c < NC; ++c) Vh[m][k][c] = Vl[m][k][c] = 0.f;
         } else {
             const int d0 = __ldg(ed);
-            double x0[NC];
+            float x0h[NC], x0l[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) x0[c] = x[((int64_t)d0 * NC + c) * ncols + col];
+            for (int c = 0; c < NC; ++c) {
+                const int64_t i0 = ((int64_t)d0 * NC + c) * ncols + col;
+                x0h[c] = -xh[i0];
+                x0l[c] = -xl[i0];
+            }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int dk = __ldg(ed + k + 1);
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    df_split(x[((int64_t)dk * NC + c) * ncols + col] - x0[c], Vh[0][k][c], Vl[0][k][c]);
+                for (int c = 0; c < NC; ++c) {
+                    const int64_t ik = ((int64_t)dk * NC + c) * ncols + col;
+                    Vh[0][k][c] = xh[ik];
+                    Vl[0][k][c] = xl[ik];
+                    df_add(Vh[0][k][c], Vl[0][k][c], x0h[c], x0l[c]);
+                }
             }
 #pragma unroll
             for (int m = 1; m < NM; ++m)
@@ -421,11 +433,15 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
         }
 #pragma unroll
         for (int j = 4; j < NE; ++j) {
-            if (x == nullptr) break;
+            if (xh == nullptr) break;
             const int dj = __ldg(ed + j);
-            float xh[NC], xl[NC];
+            float vh[NC], vl[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) df_split(x[((int64_t)dj * NC + c) * ncols + col], xh[c], xl[c]);
+            for (int c = 0; c < NC; ++c) {
+                const int64_t ij = ((int64_t)dj * NC + c) * ncols + col;
+                vh[c] = xh[ij];
+                vl[c] = xl[ij];
+            }
 #pragma unroll
             for (int m = 0; m < NM; ++m)
 #pragma unroll
@@ -433,7 +449,7 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
                     const float a = basis_a<P, float>((k * NM + m) * NE + j);
                     if (a != 0.f)
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) df_mac(Vh[m][k][c], Vl[m][k][c], a, xh[c], xl[c]);
+                        for (int c = 0; c < NC; ++c) df_mac(Vh[m][k][c], Vl[m][k][c], a, vh[c], vl[c]);
                 }
         }
 #pragma unroll
@@ -533,11 +549,15 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
             float sh = Vh[0][0][c], sl = Vl[0][0][c];
             df_add(sh, sl, Vh[0][1][c], Vl[0][1][c]);
             df_add(sh, sl, Vh[0][2][c], Vl[0][2][c]);
-            atomicAdd(r + ((int64_t)__ldg(ed) * NC + c) * ncols + col, (double)sh + (double)sl);
+            const int64_t i0 = ((int64_t)__ldg(ed) * NC + c) * ncols + col;
+            atomicAdd(r + i0, (double)sh);
+            atomicAdd(rlo + i0, sl);
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                atomicAdd(r + ((int64_t)__ldg(ed + k + 1) * NC + c) * ncols + col,
-                          -((double)Vh[0][k][c] + (double)Vl[0][k][c]));
+            for (int k = 0; k < 3; ++k) {
+                const int64_t ik = ((int64_t)__ldg(ed + k + 1) * NC + c) * ncols + col;
+                atomicAdd(r + ik, (double)-Vh[0][k][c]);
+                atomicAdd(rlo + ik, -Vl[0][k][c]);
+            }
         }
 #pragma unroll
         for (int j = 4; j < NE; ++j) {
@@ -555,18 +575,40 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
                 }
             const int dj = __ldg(ed + j);
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-                atomicAdd(r + ((int64_t)dj * NC + c) * ncols + col, -((double)yh[c] + (double)yl[c]));
+            for (int c = 0; c < NC; ++c) {
+                const int64_t ij = ((int64_t)dj * NC + c) * ncols + col;
+                atomicAdd(r + ij, (double)-yh[c]);
+                atomicAdd(rlo + ij, -yl[c]);
+            }
         }
     }
 }
 
-void launch_residual_df(int p, int nc, const ElemView<float>& ev, const double* x, double* r, const Launch& L) {
+// x = x_h + x_l, two FP32 words per FP64 entry (the double-float kernel's input)
+__global__ void k_split_d2ff(int64_t n, const double* __restrict__ x, float* __restrict__ xh,
+                             float* __restrict__ xl) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float h, l;
+        df_split(x[i], h, l);
+        xh[i] = h;
+        xl[i] = l;
+    }
+}
+
+void launch_split_d2ff(int64_t n, const double* x, float* xh, float* xl, cudaStream_t s) {
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    k_split_d2ff<<<(unsigned)b, 256, 0, s>>>(n, x, xh, xl);
+}
+
+void launch_residual_df(int p, int nc, const ElemView<float>& ev, const float* xh, const float* xl,
+                        double* r, float* rlo, const Launch& L) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
-#define RVE_DF_CASE(PP, NCC)                                                               \
-    if (p == PP && nc == NCC) {                                                            \
-        k_residual_df<PP, NCC><<<grid, block, 0, L.stream>>>(ev, x, r, L.ncols, L.cpb);    \
-        return;                                                                            \
+#define RVE_DF_CASE(PP, NCC)                                                                          \
+    if (p == PP && nc == NCC) {                                                                       \
+        k_residual_df<PP, NCC><<<grid, block, 0, L.stream>>>(ev, xh, xl, r, rlo, L.ncols, L.cpb);     \
+        return;                                                                                       \
     }
     RVE_DF_CASE(1, 3) RVE_DF_CASE(2, 3) RVE_DF_CASE(3, 3)
     RVE_DF_CASE(1, 1) RVE_DF_CASE(2, 1) RVE_DF_CASE(3, 1)
@@ -843,18 +885,50 @@ template void launch_column_scales<float>(int, const double*, int, bool, float*,
 template void launch_column_scales<double>(int, const double*, int, bool, double*, cudaStream_t);
 
 // ------------------------------------------------------------- PCG pieces
+// Jacobi preconditioner entry of one row for one column: the per-phase diagonals
+// combined with the column's phase scales (an explicit FMA, so that every kernel
+// forms exactly the same value), zero on Dirichlet-masked rows.
+template <typename T>
+__device__ __forceinline__ T jacobi_inv(T s0, T d0, T s1, T d1) {
+    T d;
+    if constexpr (sizeof(T) == 4) {
+        d = fmaf(s0, d0, __fmul_rn(s1, d1));
+        return d > 0.f ? __frcp_rn(d) : 0.f;   // correctly rounded reciprocal
+    } else {
+        d = fma(s0, d0, __dmul_rn(s1, d1));
+        return d > 0.0 ? 1.0 / d : 0.0;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T inv_diag(const RowView<T>& rv, int64_t row, int col, int ncols) {
     const int64_t dof = row / rv.nc;
     if (rv.mask && rv.mask[dof]) return T(0);
     const int f = (rv.nfield == 2 && (col % 6) >= 3) ? 1 : 0;
-    const T d = rv.scale[2 * col] * rv.diag[(int64_t)(2 * f) * rv.n_rows + row] +
-                rv.scale[2 * col + 1] * rv.diag[(int64_t)(2 * f + 1) * rv.n_rows + row];
-    if constexpr (sizeof(T) == 4)
-        return d > T(0) ? __frcp_rn(d) : T(0);   // correctly rounded reciprocal
-    else
-        return d > T(0) ? T(1) / d : T(0);
+    return jacobi_inv<T>(rv.scale[2 * col], rv.diag[(int64_t)(2 * f) * rv.n_rows + row], rv.scale[2 * col + 1],
+                         rv.diag[(int64_t)(2 * f + 1) * rv.n_rows + row]);
 }
+
+// The same for a fixed column, with its scales and diagonal rows held in registers.
+template <typename T, int NC>
+struct ColJacobi {
+    const T* d0;
+    const T* d1;
+    const uint8_t* mask;
+    T s0, s1;
+    __device__ __forceinline__ ColJacobi(const RowView<T>& rv, int col) {
+        const int f = (rv.nfield == 2 && (col % 6) >= 3) ? 1 : 0;
+        d0 = rv.diag + (int64_t)(2 * f) * rv.n_rows;
+        d1 = d0 + rv.n_rows;
+        mask = rv.mask;
+        s0 = rv.scale[2 * col];
+        s1 = rv.scale[2 * col + 1];
+    }
+    __device__ __forceinline__ T inv(int64_t row) const {
+        if (mask && mask[row / NC]) return T(0);
+        return jacobi_inv<T>(s0, __ldg(d0 + row), s1, __ldg(d1 + row));
+    }
+};
 
 // One block per column: alpha = (r, z) / (p, K p) with (p, K p) summed in parallel.
 __global__ void __launch_bounds__(256) k_finalize_alpha(const double* __restrict__ ep, int nby, int ncols,
@@ -886,9 +960,11 @@ template void launch_finalize_alpha<float>(const double*, ColState, const Launch
 template void launch_finalize_alpha<double>(const double*, ColState, const Launch&);
 
 // x += alpha p, r -= alpha q (when apply), partial (r, M^-1 r) per column and,
-// on constraint-support rows, the partial constraint products C M^-1 r
-// (m <= 12 rows), written to cp[(blockIdx.y * m + k) * ncols + col].
-template <typename T>
+// on constraint-support rows (HAS_C), the partial constraint products C M^-1 r
+// (m <= 12 rows), written to cp[(blockIdx.y * m + k) * ncols + col].  Instances
+// without constraint rows carry no constraint accumulators (fewer registers,
+// more resident warps for this memory-bound pass).
+template <typename T, int NC, bool HAS_C>
 __global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x, T* __restrict__ r,
                                                 const T* __restrict__ p, const T* __restrict__ q,
                                                 ColState cs, double* __restrict__ rzp,
@@ -897,22 +973,25 @@ __global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x
     const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
     const int col = blockIdx.x * cpb + cl;
     const T a = apply ? (T)cs.alpha[col] : T(0);
-    const int m = rv.m;
+    const ColJacobi<T, NC> jac(rv, col);
     PartialSum<T> acc;
-    PartialSum<T> cacc[12];
+    PartialSum<T> cacc[HAS_C ? 12 : 1];
+    const int m = HAS_C ? rv.m : 0;
     // a converged column keeps x and r; its partials stay zero
     const int64_t i_end = (apply && !cs.active[col]) ? 0 : rv.n_rows;
-    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += (int64_t)gridDim.y * rows) {
+    const int64_t stride = (int64_t)gridDim.y * rows;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += stride) {
         const int64_t idx = i * ncols + col;
         T rv_ = r[idx];
         if (a != T(0)) {
-            x[idx] = fma(a, p[idx], x[idx]);
-            rv_ = fma(-a, q[idx], rv_);
+            const T pv = p[idx], qv = q[idx], xv = x[idx];
+            x[idx] = fma(a, pv, xv);
+            rv_ = fma(-a, qv, rv_);
             r[idx] = rv_;
         }
-        const T w = inv_diag(rv, i, col, ncols) * rv_;
+        const T w = jac.inv(i) * rv_;
         acc.add(rv_ * w);
-        if (m > 0) {
+        if constexpr (HAS_C) {
             const int32_t sidx = rv.sup_of_row[i];
             if (sidx >= 0) {
 #pragma unroll
@@ -923,17 +1002,19 @@ __global__ void __launch_bounds__(256) k_update(RowView<T> rv, T* __restrict__ x
     }
     double accs[1] = {acc.value()};
     block_column_reduce<1>(accs, rzp, ncols, cpb, col);
-    if (m > 0 && cp) {
-        __shared__ double buf[256];
-        for (int k = 0; k < m; ++k) {
-            buf[threadIdx.x] = cacc[k].value();
-            __syncthreads();
-            if (rr == 0) {
-                double sacc = 0.0;
-                for (int qq = 0; qq < rows; ++qq) sacc += buf[qq * cpb + cl];
-                cp[((int64_t)blockIdx.y * m + k) * ncols + col] = sacc;
+    if constexpr (HAS_C) {
+        if (cp) {
+            __shared__ double buf[256];
+            for (int k = 0; k < m; ++k) {
+                buf[threadIdx.x] = cacc[k].value();
+                __syncthreads();
+                if (rr == 0) {
+                    double sacc = 0.0;
+                    for (int qq = 0; qq < rows; ++qq) sacc += buf[qq * cpb + cl];
+                    cp[((int64_t)blockIdx.y * m + k) * ncols + col] = sacc;
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
 }
@@ -942,8 +1023,15 @@ template <typename T>
 void launch_update(const RowView<T>& rv, T* x, T* r, const T* p, const T* q, ColState cs,
                    double* rz_partial, bool apply_update, const Launch& L, double* c_partial) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
-    k_update<T><<<grid, block, 0, L.stream>>>(rv, x, r, p, q, cs, rz_partial, c_partial, L.ncols, L.cpb,
-                                               apply_update ? 1 : 0);
+    const int ap = apply_update ? 1 : 0;
+#define RVE_UPD_CASE(NCC, HC)                                                                           \
+    if (rv.nc == NCC && (rv.m > 0) == HC) {                                                             \
+        k_update<T, NCC, HC><<<grid, block, 0, L.stream>>>(rv, x, r, p, q, cs, rz_partial, c_partial,   \
+                                                           L.ncols, L.cpb, ap);                        \
+        return;                                                                                         \
+    }
+    RVE_UPD_CASE(3, false) RVE_UPD_CASE(3, true) RVE_UPD_CASE(1, false) RVE_UPD_CASE(1, true)
+#undef RVE_UPD_CASE
 }
 template void launch_update<float>(const RowView<float>&, float*, float*, const float*, const float*,
                                    ColState, double*, bool, const Launch&, double*);
@@ -1063,43 +1151,56 @@ void launch_constraint_multipliers(int m, const double* c_partial, ColState cs, 
 // Residual reset r <- r - C^T mu on the constraint support (the part of the
 // residual that the constraint forces carry), and partial (r, M^-1 r) of the
 // projected residual, computed without cancellation.
-template <typename T>
-__global__ void __launch_bounds__(256) k_project_residual(RowView<T> rv, T* __restrict__ r, ColState cs,
+// r <- r - C^T mu on the constraint support (FP64), and per column the partial
+// (r, M^-1 r) of the result.  The norm only steers the stopping test, so it is
+// formed from the FP32 preconditioner and FP32-rounded r with compensated FP32
+// sums (relative accuracy ~1e-7), which keeps this FP64-vector pass off the
+// FP64 pipe apart from one conversion per entry.
+template <int NC, bool HAS_C>
+__global__ void __launch_bounds__(256) k_project_residual(RowView<double> rv, RowView<float> rv32,
+                                                          double* __restrict__ r, ColState cs,
                                                           double* __restrict__ rzp, int ncols, int cpb) {
     const int rows = blockDim.x / cpb;
     const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
     const int col = blockIdx.x * cpb + cl;
-    const int m = rv.m;
-    double acc = 0.0;
+    const int m = HAS_C ? rv.m : 0;
+    const ColJacobi<float, NC> jac(rv32, col);
+    PartialSum<float> acc;
     for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < rv.n_rows; i += (int64_t)gridDim.y * rows) {
         const int64_t idx = i * ncols + col;
-        T v = r[idx];
-        if (m > 0) {
+        double v = r[idx];
+        if constexpr (HAS_C) {
             const int32_t sidx = rv.sup_of_row[i];
             if (sidx >= 0) {
                 double corr = 0.0;
                 for (int k = 0; k < m; ++k)
                     corr += rv.sup_coef[(int64_t)sidx * m + k] * cs.mu[(int64_t)k * ncols + col];
-                v = (T)((double)v - corr);
+                v -= corr;
                 r[idx] = v;
             }
         }
-        acc += (double)v * (double)(inv_diag(rv, i, col, ncols) * v);
+        const float vf = (float)v;
+        acc.add(vf * (jac.inv(i) * vf));
     }
-    double accs[1] = {acc};
+    double accs[1] = {acc.value()};
     block_column_reduce<1>(accs, rzp, ncols, cpb, col);
 }
 
-template <typename T>
-void launch_project_residual(const RowView<T>& rv, T* r, ColState cs, double* rz_partial, const Launch& L) {
+void launch_project_residual(const RowView<double>& rv, const RowView<float>& rv32, double* r, ColState cs,
+                             double* rz_partial, const Launch& L) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
-    k_project_residual<T><<<grid, block, 0, L.stream>>>(rv, r, cs, rz_partial, L.ncols, L.cpb);
+#define RVE_PR_CASE(NCC, HC)                                                                          \
+    if (rv.nc == NCC && (rv.m > 0) == HC) {                                                           \
+        k_project_residual<NCC, HC><<<grid, block, 0, L.stream>>>(rv, rv32, r, cs, rz_partial, L.ncols, \
+                                                                  L.cpb);                             \
+        return;                                                                                       \
+    }
+    RVE_PR_CASE(3, false) RVE_PR_CASE(3, true) RVE_PR_CASE(1, false) RVE_PR_CASE(1, true)
+#undef RVE_PR_CASE
 }
-template void launch_project_residual<double>(const RowView<double>&, double*, ColState, double*,
-                                              const Launch&);
 
 // p = M^-1 (r - C^T mu) + beta p ; q = 0
-template <typename T>
+template <typename T, int NC, bool HAS_C>
 __global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, T* __restrict__ r,
                                                  T* __restrict__ p, T* __restrict__ q, ColState cs,
                                                  int ncols, int cpb, int first) {
@@ -1108,11 +1209,13 @@ __global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, T* __restrict__ 
     const int col = blockIdx.x * cpb + cl;
     const bool act = cs.active[col] != 0;
     const T beta = first ? T(0) : (T)cs.beta[col];
-    const int m = rv.m;
+    const ColJacobi<T, NC> jac(rv, col);
+    const int m = HAS_C ? rv.m : 0;
     // converged columns are left alone (the operator and update skip them too),
     // except on the first pass, which clears p and q of columns with b = 0
     const int64_t i_end = (!act && !first) ? 0 : rv.n_rows;
-    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += (int64_t)gridDim.y * rows) {
+    const int64_t stride = (int64_t)gridDim.y * rows;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += stride) {
         const int64_t idx = i * ncols + col;
         q[idx] = T(0);
         if (!act) {
@@ -1120,18 +1223,19 @@ __global__ void __launch_bounds__(256) k_pupdate(RowView<T> rv, T* __restrict__ 
             continue;
         }
         T rr_ = r[idx];
-        if (m > 0) {
-            const int32_t s = rv.sup_of_row[i];
-            if (s >= 0) {
+        const T pold = first ? T(0) : p[idx];
+        if constexpr (HAS_C) {
+            const int32_t sidx = rv.sup_of_row[i];
+            if (sidx >= 0) {
                 T corr = T(0);
                 for (int k = 0; k < m; ++k)
-                    corr = fma((T)rv.sup_coef[(int64_t)s * m + k], (T)cs.mu[(int64_t)k * ncols + col], corr);
+                    corr = fma((T)rv.sup_coef[(int64_t)sidx * m + k], (T)cs.mu[(int64_t)k * ncols + col], corr);
                 rr_ -= corr;
                 r[idx] = rr_;   // residual reset: keeps r in the projected space
             }
         }
-        const T z = inv_diag(rv, i, col, ncols) * rr_;
-        p[idx] = first ? z : fma(beta, p[idx], z);
+        const T z = jac.inv(i) * rr_;
+        p[idx] = first ? z : fma(beta, pold, z);
     }
 }
 
@@ -1139,7 +1243,14 @@ template <typename T>
 void launch_pupdate(const RowView<T>& rv, T* r, T* p, T* q, ColState cs, bool first,
                     const Launch& L) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
-    k_pupdate<T><<<grid, block, 0, L.stream>>>(rv, r, p, q, cs, L.ncols, L.cpb, first ? 1 : 0);
+    const int fi = first ? 1 : 0;
+#define RVE_PUP_CASE(NCC, HC)                                                                           \
+    if (rv.nc == NCC && (rv.m > 0) == HC) {                                                             \
+        k_pupdate<T, NCC, HC><<<grid, block, 0, L.stream>>>(rv, r, p, q, cs, L.ncols, L.cpb, fi);       \
+        return;                                                                                         \
+    }
+    RVE_PUP_CASE(3, false) RVE_PUP_CASE(3, true) RVE_PUP_CASE(1, false) RVE_PUP_CASE(1, true)
+#undef RVE_PUP_CASE
 }
 template void launch_pupdate<float>(const RowView<float>&, float*, float*, float*, ColState, bool,
                                     const Launch&);
@@ -1238,8 +1349,8 @@ void launch_gram(int64_t n_rows, const double* b, const double* u, const double*
 // and int sigma(eps_bar) (the Voigt term), 6 + 6 values (3 + 3 for scalars).
 // Only the constant gradient mode enters an element mean (the higher modes
 // integrate to zero).  T = float keeps per-thread compensated sums.
-template <int P, int NC, typename T>
-__global__ void __launch_bounds__(256) k_mean_stress(ElemView<T> ev, const T* __restrict__ u,
+template <int P, int NC, typename T, typename TU>
+__global__ void __launch_bounds__(256) k_mean_stress(ElemView<T> ev, const TU* __restrict__ u,
                                                      double* __restrict__ part, int ncols, int cpb) {
     constexpr int NE = Order<P>::NE;
     constexpr int NM = Order<P>::NM;
@@ -1263,7 +1374,7 @@ __global__ void __launch_bounds__(256) k_mean_stress(ElemView<T> ev, const T* __
             const int dk = __ldg(ed + k + 1);
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                V[k][c] = u[((int64_t)dk * NC + c) * ncols + col] - u[((int64_t)d0 * NC + c) * ncols + col];
+                V[k][c] = (T)(u[((int64_t)dk * NC + c) * ncols + col] - u[((int64_t)d0 * NC + c) * ncols + col]);
         }
 #pragma unroll
         for (int j = 4; j < NE; ++j) {
@@ -1273,7 +1384,7 @@ __global__ void __launch_bounds__(256) k_mean_stress(ElemView<T> ev, const T* __
                 const T a = basis_a<P, T>((k * NM + 0) * NE + j);
                 if (a != T(0))
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) V[k][c] = fma(a, u[((int64_t)dj * NC + c) * ncols + col], V[k][c]);
+                    for (int c = 0; c < NC; ++c) V[k][c] = fma(a, (T)u[((int64_t)dj * NC + c) * ncols + col], V[k][c]);
             }
         }
         T H[NC][3];
@@ -1311,23 +1422,23 @@ __global__ void __launch_bounds__(256) k_mean_stress(ElemView<T> ev, const T* __
     block_column_reduce<12>(out, part, ncols, cpb, col);
 }
 
-template <typename T>
-void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const T* u, double* partial,
+template <typename T, typename TU>
+void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const TU* u, double* partial,
                         const Launch& L) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
-#define RVE_MS_CASE(PP, NCC)                                                                  \
-    if (p == PP && nc == NCC) {                                                               \
-        k_mean_stress<PP, NCC, T><<<grid, block, 0, L.stream>>>(ev, u, partial, L.ncols, L.cpb); \
-        return;                                                                               \
+#define RVE_MS_CASE(PP, NCC)                                                                      \
+    if (p == PP && nc == NCC) {                                                                   \
+        k_mean_stress<PP, NCC, T, TU><<<grid, block, 0, L.stream>>>(ev, u, partial, L.ncols, L.cpb); \
+        return;                                                                                   \
     }
     RVE_MS_CASE(1, 3) RVE_MS_CASE(2, 3) RVE_MS_CASE(3, 3)
     RVE_MS_CASE(1, 1) RVE_MS_CASE(2, 1) RVE_MS_CASE(3, 1)
 #undef RVE_MS_CASE
 }
-template void launch_mean_stress<double>(int, int, const ElemView<double>&, const double*, double*,
-                                         const Launch&);
-template void launch_mean_stress<float>(int, int, const ElemView<float>&, const float*, double*,
-                                        const Launch&);
+template void launch_mean_stress<double, double>(int, int, const ElemView<double>&, const double*, double*,
+                                                 const Launch&);
+template void launch_mean_stress<float, double>(int, int, const ElemView<float>&, const double*, double*,
+                                                const Launch&);
 
 // out[w] = sum_b part[b][w]: one block per output value (up to 128 outputs per
 // block row are handled by grid-striding over w).

@@ -107,17 +107,18 @@ template <typename T>
 void launch_pupdate(const RowView<T>& rv, T* r, T* p, T* q, ColState cs, bool first,
                     const Launch& L);
 void launch_constraint_multipliers(int m, const double* c_partial, ColState cs, const Launch& L);
-template <typename T>
-void launch_project_residual(const RowView<T>& rv, T* r, ColState cs, double* rz_partial,
-                             const Launch& L);
+// FP64 r projected in place; (r, M^-1 r) partials from the FP32 preconditioner view rv32
+void launch_project_residual(const RowView<double>& rv, const RowView<float>& rv32, double* r, ColState cs,
+                             double* rz_partial, const Launch& L);
 template <typename T>
 void launch_schur(const RowView<T>& rv, ColState cs, const Launch& L);
 
 // reductions for the homogenised tensors
 void launch_gram(int64_t n_rows, const double* b, const double* u, const double* r,
                  double* partial, const Launch& L);
-template <typename T>
-void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const T* u, double* partial,
+// element data in T, the solution in TU (converted on load)
+template <typename T, typename TU>
+void launch_mean_stress(int p, int nc, const ElemView<T>& ev, const TU* u, double* partial,
                         const Launch& L);
 void launch_reduce_partials(int nby, int width, const double* partial, double* out,
                             cudaStream_t s);
@@ -134,9 +135,12 @@ template <typename TO>
 void launch_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* coef,
                             const double* src, TO* x, cudaStream_t s);
 
-// r += -K32 (x + u_macro) in double-float arithmetic (FP32 element data, FP64 x and r;
-// r must hold zero or a value to accumulate onto)
-void launch_residual_df(int p, int nc, const ElemView<float>& ev, const double* x, double* r, const Launch& L);
+// r_hi + r_lo += -K32 (x_h + x_l + u_macro) in double-float arithmetic (FP32 element
+// data; x_h = nullptr: x = 0); the caller adds r_lo (FP32) into r_hi (FP64) afterwards
+void launch_residual_df(int p, int nc, const ElemView<float>& ev, const float* xh, const float* xl,
+                        double* r_hi, float* r_lo, const Launch& L);
+// x = x_h + x_l (two FP32 words per FP64 entry)
+void launch_split_d2ff(int64_t n, const double* x, float* xh, float* xl, cudaStream_t s);
 
 // right-hand sides of a batch from the per-phase macro loads y = [2][n_rows][6]
 void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,

@@ -1,0 +1,67 @@
+"""Batch scheduling: the batch-size autotuner (scheduling of the batched cell
+solves; no counterpart in the paper).  Through the C ABI on the GPU."""
+import numpy as np
+import pytest
+
+import rve_inputs as ri
+from oracle import fem
+from oracle import materials as mt
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rve():
+    import paper_1610_03484_gb300 as pkg
+    from paper_1610_03484_gb300 import _build
+    _build.build()
+    pkg.load_library()
+    return pkg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def test_autotune_batch_picks_a_candidate_and_is_used(rve):
+    grid, p = (6, 6, 4), 2
+    xyz, tets, phase, tangent = ri.weave_rve(*grid)
+    Ts, cs, ts, _, _ = ri.gauss_point_states(24, seed=21)     # tuning sample
+    T, c, t, _, _ = ri.gauss_point_states(20, seed=22)        # the call that uses it
+    with rve.Context(precision=rve.PREC_MIXED, rtol=1e-8, inner_rtol=1e-6) as ctx:
+        mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
+        with pytest.raises(rve.RveError) as e:
+            mesh.autotune_batch(Ts, cs, ts, [4, 8])
+        assert e.value.code == -9                              # materials not set
+        mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+        mesh.set_bc(1)
+        with pytest.raises(rve.RveError) as e:
+            mesh.autotune_batch(Ts, cs, ts, [4, 0])
+        assert e.value.code == -1
+        best, rates = mesh.autotune_batch(Ts, cs, ts, [4, 8])
+        assert best in (4, 8)
+        assert all(r > 0 for r in rates.values())
+        assert rates[best] == max(rates.values())
+        Ct, Kt, Dt, st, stats, rc = ctx.macro_update([mesh], T, c, t, np.zeros(20, np.int32))
+        assert (st == 0).all()
+        mesh.free()
+    # the same points with the chosen batch size set explicitly
+    with rve.Context(precision=rve.PREC_MIXED, rtol=1e-8, inner_rtol=1e-6, batch=best) as ctx:
+        mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
+        mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+        mesh.set_bc(1)
+        Ce, Ke, De, st, stats, rc = ctx.macro_update([mesh], T, c, t, np.zeros(20, np.int32))
+        mesh.free()
+    for g in range(20):
+        assert rel(Ct[g], Ce[g]) < 1e-8
+        assert rel(Kt[g], Ke[g]) < 1e-8
+    # and against the oracle on two points
+    for g in (0, 19):
+        w = float(mt.one_minus_omega(T[g], c[g], t[g]))
+        m = ri.MatrixProps(E=ri.NOMINAL_MATRIX.E * w, nu=ri.NOMINAL_MATRIX.nu, k=ri.NOMINAL_MATRIX.k,
+                           d=ri.NOMINAL_MATRIX.d)
+        D, K, Dd = mt.element_tensors(phase, tangent, m, ri.NOMINAL_YARN)
+        Co, Ko, Do = fem.homogenise(xyz, tets, grid, p, 1, D, K, Dd)
+        assert rel(Ct[g], Co) < 1e-6
+        assert rel(Kt[g], Ko) < 1e-6
+        assert rel(Dt[g], Do) < 1e-6
