@@ -34,8 +34,9 @@ UNIT = "homogenisations/s"
 G_POINTS = 4096
 SEED = 2
 WORKLOAD = ("batched FE2 evaluation: 4096 macro Gauss points per GPU, plain-weave RVEs on "
-            "16x16x6 / 24x24x8 / 32x32x10 Kuhn grids, p in {1,2}, periodic BC, 12 load cases "
-            "per RVE (6 mech + 3 thermal + 3 moisture), degradation state per point from the "
+            "16x16x6 / 24x24x8 / 32x32x10 Kuhn grids, p in {1,2}, periodic BC, C, K, D per point: "
+            "6 mechanical load cases per point (degraded matrix), 3 thermal + 3 moisture load "
+            "cases once per mesh and call (transport is not degraded), degradation state per point from the "
             "Sec. 4 law, FP32 operator and inner PCG, double-float true residual, FP64 reductions")
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 RTOL = 1e-5          # FP64 outer (true-residual) tolerance of every cell solve

@@ -71,7 +71,7 @@ typedef struct rve_options {
     int     max_iter;        /* PCG iteration cap per solve (default 20000) */
     double  inner_rtol;      /* MIXED: relative tolerance of each FP32 inner solve (default 1e-6) */
     int     max_refine;      /* MIXED: maximum FP64 refinement sweeps (default 4) */
-    int     check_every;     /* iterations between host convergence checks (default 16) */
+    int     check_every;     /* unused: the PCG loop tests convergence on the device every iteration */
     int     batch;           /* RVEs solved together in macro_update_gauss_points, 0 = auto */
     void*   stream;          /* cudaStream_t to run on; NULL = library-created stream */
     int     profile;         /* 1: time every operator launch with CUDA events (rve_stats.op_*) */

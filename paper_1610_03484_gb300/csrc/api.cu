@@ -235,15 +235,6 @@ Launch make_launch(int ncols, int64_t work, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------- the solver
-struct SolveOut {
-    std::vector<double> tensor;    // [B][6][6] energy form (internal units)
-    std::vector<double> sig;       // [B][6][6] sigma form (diagnostic)
-    int iterations = 0;
-    int sweeps = 0;
-    bool converged = true;
-    double rel_res = 0;
-    bool numeric = false;
-};
 
 // Starting data for a warm-started batch: the previous batch's solutions u_k
 // (factors w_k) and, in mixed precision, their final projected FP64 residuals r_k.
@@ -464,7 +455,6 @@ struct Solver {
         // profile mode launches one iteration at a time so that the byte and flop
         // counts follow the set of columns still iterating
         const bool prof = m->ctx->opt.profile != 0;
-        const int check = prof ? 1 : std::max(1, m->ctx->opt.check_every);
         ColState cs = cs64;
         cs.tol = tol;
         RowView<T> rvw = rv<T>(scale);
@@ -475,7 +465,6 @@ struct Solver {
         launch_pupdate<T>(rvw, r, p, q, cs, true, L);
         *launches += 5;
         std::vector<int32_t> act(ncols);
-        int it = 0;
         conv = false;
         int n_act = ncols;
         auto read_active = [&]() -> int {
@@ -486,70 +475,85 @@ struct Solver {
             for (int c = 0; c < ncols; ++c) n_act += act[c] != 0;
             return RVE_OK;
         };
-        if (prof) RVE_TRY(read_active());
-        // `check` iterations are captured once into a CUDA graph (on the private
-        // capture stream) and replayed on the context stream until every column
-        // has converged; the host reads the convergence flags between replays.
-        // profile mode: 6 events per iteration bracket operator, alpha, update,
-        // beta and p-update launches
-        if (prof && (int)m->ctx->ev.size() < 6 * check) {
-            for (int k = (int)m->ctx->ev.size(); k < 6 * check; ++k) {
+        // profile mode: 6 events bracket the operator, alpha, update, beta and
+        // p-update launches of an iteration
+        if (prof && (int)m->ctx->ev.size() < 6) {
+            for (int k = (int)m->ctx->ev.size(); k < 6; ++k) {
                 cudaEvent_t e;
                 RVE_CUDA(cudaEventCreate(&e));
                 m->ctx->ev.push_back(e);
             }
         }
-        auto evr = [&](int k, int i, cudaStream_t st) {
-            if (prof) cudaEventRecord(m->ctx->ev[6 * k + i], st);
+        auto evr = [&](int i, cudaStream_t st) {
+            if (prof) cudaEventRecord(m->ctx->ev[i], st);
         };
-        auto body = [&](const Launch& Lx) {
-            for (int k = 0; k < check; ++k) {
-                evr(k, 0, Lx.stream);
-                launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active);
-                evr(k, 1, Lx.stream);
-                launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
-                evr(k, 2, Lx.stream);
-                launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx, m->cpart.as<double>());
-                evr(k, 3, Lx.stream);
-                launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, Lx);
-                evr(k, 4, Lx.stream);
-                launch_pupdate<T>(rvw, r, p, q, cs, false, Lx);
-                evr(k, 5, Lx.stream);
-            }
+        auto iteration = [&](const Launch& Lx) {
+            evr(0, Lx.stream);
+            launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active);
+            evr(1, Lx.stream);
+            launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
+            evr(2, Lx.stream);
+            launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx, m->cpart.as<double>());
+            evr(3, Lx.stream);
+            launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, Lx);
+            evr(4, Lx.stream);
+            launch_pupdate<T>(rvw, r, p, q, cs, false, Lx);
+            evr(5, Lx.stream);
         };
-        // Profile mode launches the body directly on the context stream so that
-        // the event pairs around each operator launch can be timed.
-        cudaGraphExec_t exec = nullptr;
         if (!prof) {
+            // The iterations run as one CUDA graph whose conditional WHILE node
+            // repeats the iteration's five kernels plus k_pcg_continue, which
+            // ends the loop on the device once no column is active or max_iter
+            // iterations have run: no host round trip and no idle iterations.
             const auto g0 = std::chrono::steady_clock::now();
+            cudaGraph_t graph = nullptr;
+            RVE_CUDA(cudaGraphCreate(&graph, 0));
+            struct GraphGuard {
+                cudaGraph_t g;
+                ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+            } gguard{graph};
+            cudaGraphConditionalHandle handle;
+            RVE_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = handle;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            RVE_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+            cudaGraph_t body = np.conditional.phGraph_out[0];
             Launch Lc = L;
             Lc.stream = m->ctx->capture;
-            cudaGraph_t graph = nullptr;
-            RVE_CUDA(cudaStreamBeginCapture(Lc.stream, cudaStreamCaptureModeThreadLocal));
-            body(Lc);
-            RVE_CUDA(cudaStreamEndCapture(Lc.stream, &graph));
-            cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            RVE_CUDA(ge);
+            RVE_CUDA(cudaStreamBeginCaptureToGraph(Lc.stream, body, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal));
+            iteration(Lc);
+            launch_pcg_continue(handle, cs.active, ncols, cs.flags + 1, max_iter, Lc.stream);
+            RVE_CUDA(cudaStreamEndCapture(Lc.stream, &body));
+            cudaGraphExec_t exec = nullptr;
+            RVE_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+            struct ExecGuard {
+                cudaGraphExec_t e;
+                ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+            } eguard{exec};
             m->ctx->prof.graph_host_ms +=
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g0).count();
             m->ctx->prof.graphs++;
-        }
-        struct ExecGuard {
-            cudaGraphExec_t e;
-            ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
-        } guard{exec};
-        while (it < max_iter) {
-            if (prof)
-                body(L);
-            else
-                RVE_CUDA(cudaGraphLaunch(exec, s));
-            it += check;
-            *launches += (int64_t)check * 5;
+            RVE_CUDA(cudaMemsetAsync(cs.flags + 1, 0, sizeof(int32_t), s));   // loop counter
+            RVE_CUDA(cudaGraphLaunch(exec, s));
             RVE_CUDA(cudaGetLastError());
-            const int n_act_run = n_act;    // columns the iteration just run worked on
+            int32_t loops = 0;
+            RVE_CUDA(cudaMemcpyAsync(&loops, cs.flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             RVE_TRY(read_active());
-            if (prof) {
+            *launches += (int64_t)loops * 6;
+            conv = n_act == 0;
+        } else {
+            RVE_TRY(read_active());
+            for (int it = 0; it < max_iter && n_act > 0; ++it) {
+                iteration(L);
+                *launches += 5;
+                RVE_CUDA(cudaGetLastError());
+                const int n_act_run = n_act;    // columns the iteration just run worked on
+                RVE_TRY(read_active());
                 // algorithmic bytes / flops of one operator launch of this solve:
                 // vectors and flops of the columns still active, element data once
                 const int ne = n_local(m->p), nmod = n_modes(m->p), nc = f.nc;
@@ -563,39 +567,33 @@ struct Solver {
                 const double fma = 2.0 * table_nonzeros(m->p) * nc + nmod * (18.0 * nc + (nc == 3 ? 36 : 9));
                 const double flops = 2.0 * fma * (double)m->nt * na;
                 const double vb = (double)n_rows * na * sz;
-                auto el = [&](int k, int a2, int b2) {
+                auto el = [&](int a2, int b2) {
                     float ms = 0;
-                    return cudaEventElapsedTime(&ms, m->ctx->ev[6 * k + a2], m->ctx->ev[6 * k + b2]) == cudaSuccess
-                               ? (double)ms : 0.0;
+                    return cudaEventElapsedTime(&ms, m->ctx->ev[a2], m->ctx->ev[b2]) == cudaSuccess ? (double)ms
+                                                                                                    : 0.0;
                 };
-                for (int k = 0; k < check; ++k) {
-                    m->ctx->prof.op_ms += el(k, 0, 1);
-                    ProfCounters& pc = m->ctx->prof;
-                    const double op_ms = el(k, 0, 1);
-                    pc.op_ms += op_ms;
-                    pc.op_launches++;
-                    pc.op_bytes += bytes;
-                    pc.op_flops += flops;
-                    pc.op_cols += na;
-                    pc.op_cols_all += ncols;
-                    const int cl = 2 * (m->p - 1) + (nc == 3 ? 0 : 1);
-                    pc.cls_ms[cl] += op_ms;
-                    pc.cls_launches[cl]++;
-                    pc.cls_bytes[cl] += bytes;
-                    pc.cls_flops[cl] += flops;
-                    pc.cls_cols[cl] += na;
-                    pc.cls_cols_all[cl] += ncols;
-                    pc.fin_ms += el(k, 1, 2) + el(k, 3, 4);
-                    pc.upd_ms += el(k, 2, 3);
-                    pc.upd_bytes += 6 * vb;
-                    pc.pup_ms += el(k, 4, 5);
-                    pc.pup_bytes += 4 * vb;
-                }
+                ProfCounters& pc = m->ctx->prof;
+                const double op_ms = el(0, 1);
+                pc.op_ms += op_ms;
+                pc.op_launches++;
+                pc.op_bytes += bytes;
+                pc.op_flops += flops;
+                pc.op_cols += na;
+                pc.op_cols_all += ncols;
+                const int cl = 2 * (m->p - 1) + (nc == 3 ? 0 : 1);
+                pc.cls_ms[cl] += op_ms;
+                pc.cls_launches[cl]++;
+                pc.cls_bytes[cl] += bytes;
+                pc.cls_flops[cl] += flops;
+                pc.cls_cols[cl] += na;
+                pc.cls_cols_all[cl] += ncols;
+                pc.fin_ms += el(1, 2) + el(3, 4);
+                pc.upd_ms += el(2, 3);
+                pc.upd_bytes += 6 * vb;
+                pc.pup_ms += el(4, 5);
+                pc.pup_bytes += 4 * vb;
             }
-            if (n_act == 0) {
-                conv = true;
-                break;
-            }
+            conv = n_act == 0;
         }
         std::vector<int32_t> its(ncols);
         RVE_CUDA(cudaMemcpyAsync(its.data(), cs.iters, sizeof(int32_t) * ncols,
@@ -947,19 +945,36 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
         }
         RVE_TRY(keep_warm(0, m->mech));
     }
-    launch_column_scales<double>(B, d_w, 0, false, m->scale64.as<double>(), s);
-    launch_column_scales<float>(B, d_w, 0, false, m->scale32.as<float>(), s);
-    m->ctx->launches += 2;
-    {
-        Solver sv(m, m->scal, B);
-        if (warm_ready(1)) {
-            WarmStart ws;
-            RVE_TRY(build_warm(1, ws));
-            RVE_TRY(sv.run(prec, osc, &ws));
-        } else {
-            RVE_TRY(sv.run(prec, osc));
+    // thermal and moisture: transport is not degraded (Sec. 5), so these cell
+    // problems are the same for every point of the mesh.  In the batched call
+    // they are solved once per mesh (one RVE, six columns) and their tensors
+    // are used for all of the mesh's points; a single homogenisation solves them.
+    const bool reuse_scalar = w_host != nullptr;
+    if (reuse_scalar && m->scal_cached) {
+        osc = m->scal_out;
+        osc.iterations = 0;
+        osc.sweeps = 0;
+    } else {
+        const int Bs = reuse_scalar ? 1 : B;
+        launch_column_scales<double>(Bs, d_w, 0, false, m->scale64.as<double>(), s);
+        launch_column_scales<float>(Bs, d_w, 0, false, m->scale32.as<float>(), s);
+        m->ctx->launches += 2;
+        Solver sv(m, m->scal, Bs);
+        RVE_TRY(sv.run(prec, osc));
+        if (reuse_scalar) {
+            m->scal_out = osc;
+            m->scal_cached = true;
         }
-        RVE_TRY(keep_warm(1, m->scal));
+    }
+    if (reuse_scalar) {
+        // every RVE of the batch gets the mesh's scalar tensors
+        const std::vector<double> t1 = osc.tensor, s1 = osc.sig;
+        osc.tensor.resize((size_t)B * 36);
+        osc.sig.resize((size_t)B * 36);
+        for (int b = 0; b < B; ++b) {
+            std::memcpy(&osc.tensor[(size_t)b * 36], t1.data(), 36 * sizeof(double));
+            std::memcpy(&osc.sig[(size_t)b * 36], s1.data(), 36 * sizeof(double));
+        }
     }
     double hm_m = 0, hm_s = 0;
     for (int b = 0; b < B; ++b) {
@@ -1437,6 +1452,7 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
         m->warm_cols[0] = m->warm_cols[1] = 0;
         m->warm_w[0].clear();
         m->warm_w[1].clear();
+        m->scal_cached = false;
         RVE_TRY(upload(d_idx, grp.data(), grp.size(), s));
         for (size_t off = 0; off < grp.size(); off += Bmax) {
             const int B = (int)std::min<size_t>(Bmax, grp.size() - off);

@@ -105,6 +105,17 @@ namespace rve {
 // Profile-mode counters of a context (summed device times from CUDA events and the
 // algorithmic bytes / flops of the timed launches).  Operator classes are indexed
 // by 2 (p - 1) + (scalar field ? 1 : 0).
+// Result of one field's solve over a batch of B RVEs.
+struct SolveOut {
+    std::vector<double> tensor;    // [B][6][6] energy form (internal units)
+    std::vector<double> sig;       // [B][6][6] sigma form (diagnostic)
+    int iterations = 0;
+    int sweeps = 0;
+    bool converged = true;
+    double rel_res = 0;
+    bool numeric = false;
+};
+
 struct ProfCounters {
     double op_ms = 0, op_bytes = 0, op_flops = 0, op_cols = 0, op_cols_all = 0;
     int64_t op_launches = 0;
@@ -150,6 +161,10 @@ struct rve_mesh_s {
     rve::FieldDev mech, scal;
     bool have_materials = false;
     int tuned_batch = 0;   // batch size chosen by rve_autotune_batch (0: the built-in rule)
+    // batched call: the scalar-field solution of this mesh (independent of the
+    // degradation state), formed by the call's first batch of the mesh
+    bool scal_cached = false;
+    rve::SolveOut scal_out;
     // per phase: sum over its tets of |T| times the diagonal of D (6, mechanics) and of
     // k (3) and d (3), internal units; the energy scale of each unit load case
     double phase_voigt[2][12] = {};

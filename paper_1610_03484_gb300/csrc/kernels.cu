@@ -1079,6 +1079,28 @@ template void launch_constraint_dot<float>(const RowView<float>&, const float*, 
 template void launch_constraint_dot<double>(const RowView<double>&, const double*, double*,
                                             const Launch&);
 
+// Loop control of the device-side PCG loop (the body of a conditional WHILE graph
+// node): counts the iteration and keeps the loop going while some column is active
+// and fewer than max_iter iterations have run.  One block; exactly one thread sets
+// the condition.
+__global__ void __launch_bounds__(256) k_pcg_continue(cudaGraphConditionalHandle h,
+                                                      const int32_t* __restrict__ active, int ncols,
+                                                      int32_t* __restrict__ counter, int max_iter) {
+    int any = 0;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) any |= active[c] != 0;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        const int n = *counter + 1;
+        *counter = n;
+        cudaGraphSetConditional(h, (any && n < max_iter) ? 1u : 0u);
+    }
+}
+
+void launch_pcg_continue(cudaGraphConditionalHandle h, const int32_t* active, int ncols, int32_t* counter,
+                         int max_iter, cudaStream_t s) {
+    k_pcg_continue<<<1, 256, 0, s>>>(h, active, ncols, counter, max_iter);
+}
+
 // mu = S^-1 w, rz = (r, M^-1 r) - w . mu, beta, convergence.
 // first: 0 = iteration, 1 = initial residual, 2 = multipliers only (no state change).
 // One block per column: the partial sums are reduced in parallel, then thread 0
