@@ -19,6 +19,12 @@ Contents
                      coordinates with exact monomial integration.  It spans the
                      same space as the paper's hierarchic basis (Sec. 1, Sec. 7),
                      so homogenised tensors must agree.
+* ``macro``       -- the coupled macro time step: linear-tetrahedron heat and
+                     moisture transport (Eqs. Eq_field, Eq_field_disc) with one
+                     backward-Euler step, and the degradation field 1 - omega at
+                     the macro Gauss points by backward Euler of the rate form
+                     (Eq. Eq_Model_RateForm), plus the equivalent exposure time
+                     that hands a Gauss point to the RVE path.
 * ``fem``         -- assembly, the three RVE boundary conditions of Sec. 2 in
                      fluctuation form (Eq. micro_disp), sparse direct / CG solves,
                      energy-form tensors (Eqs. Hill_prin, Eq_C_stress,

@@ -229,3 +229,29 @@ __all__ = [
     "P_CLASSES", "gauss_point_states", "weave_rve", "random_unit_vectors",
 ]
 
+
+
+# ------------------------------------------------------------ macro plate
+PLATE_LENGTHS = (0.5, 0.1, 0.01)      # m
+
+
+@dataclass(frozen=True)
+class PlateExposure:
+    """Synthetic coupled macro problem: a composite plate with one hot, wet
+    face (z = 0), the rest insulated and sealed; everything starts dry at
+    room temperature.  rho_cp is a typical glass/polyester value."""
+    T0_C: float = 20.0
+    c0_wt: float = 0.0
+    T_face_C: float = 60.0
+    c_face_wt: float = 1.5
+    rho_cp: float = 1.9e6             # J / (m^3 K)
+    total_h: float = 1.0e4
+    n_steps: int = 100
+
+
+def plate(nx: int, ny: int, nz: int, lengths=PLATE_LENGTHS):
+    """Kuhn-split hex grid of the plate; returns xyz [m], tets and the node mask
+    of the exposed face z = 0."""
+    xyz, tets = kuhn_grid(nx, ny, nz, lengths)
+    face = xyz[:, 2] <= 1e-12 * lengths[2]
+    return xyz, tets, face
