@@ -18,7 +18,9 @@ What it computes, in the paper's terms:
   W^{n+1} = W^n / (1 + dt_days lambda), lambda = c beta ln(1 - T_K / T_g,K);
 * the equivalent exposure time t_eq = -24 ln(W) / lambda [h], for which the
   closed form (Eq. Eq_Model_final1) at the point's current T and c gives W, so
-  that a macro Gauss point can be handed to the RVE path as (T, c, t_eq).
+  that a macro Gauss point can be handed to the RVE path as (T, c, t_eq); where
+  there is no moisture now the closed form cannot reach W < 1, and t_eq = 0
+  hands the point over undegraded (its error, 1 - W, is reported).
 
 The linear systems are solved with a sparse direct factorisation.
 """
@@ -96,13 +98,20 @@ def degradation_step(W, T_C, c_wt, dt_h, deg=None):
 
 
 def equivalent_time(W, T_C, c_wt, deg=None):
-    """t_eq [h] with exp(-lambda t_eq / 24) = W; 0 where lambda = 0 and W = 1;
-    NaN where lambda = 0 but W < 1 (no exposure time reproduces W)."""
+    """t_eq [h] with exp(-lambda t_eq / 24) = W where lambda > 0.  Where there is
+    no moisture now (lambda = 0) no exposure time reproduces a W < 1: t_eq = 0
+    hands the point over as undegraded, with the error of handover_error."""
     lam = degradation_rate(T_C, c_wt, deg)
     W = np.asarray(W, float)
     with np.errstate(divide="ignore", invalid="ignore"):
-        t = np.where(lam > 0, -24.0 * np.log(W) / lam, np.where(W >= 1.0, 0.0, np.nan))
+        t = np.where(lam > 0, -24.0 * np.log(W) / lam, 0.0)
     return t
+
+
+def handover_error(W, T_C, c_wt, deg=None):
+    """|closed form at (T, c, t_eq) - W|: 1 - W where lambda = 0, else 0."""
+    lam = degradation_rate(T_C, c_wt, deg)
+    return np.where(lam > 0, 0.0, 1.0 - np.asarray(W, float))
 
 
 def march(xyz, tets, face, KT, rho_cp, Dc, T0, c0, T_face, c_face, dt_h, n_steps, deg=None):

@@ -95,8 +95,12 @@ def test_degradation_backward_euler(T_C, c_wt):
 def test_dry_points_do_not_degrade_and_equivalent_time_edge_cases():
     W = mo.degradation_step(np.ones(3), np.array([60.0, 60.0, 20.0]), np.array([0.0, 1.5, 0.0]), 500.0)
     assert W[0] == 1.0 and W[2] == 1.0 and W[1] < 1.0
-    t = mo.equivalent_time(np.array([1.0, 0.9]), np.array([60.0, 60.0]), np.array([0.0, 0.0]))
-    assert t[0] == 0.0 and np.isnan(t[1])
+    # no moisture now: handed over as undegraded, the miss is 1 - W
+    T, c, Wd = np.array([60.0, 60.0]), np.array([0.0, -1e-4]), np.array([1.0, 0.9])
+    t = mo.equivalent_time(Wd, T, c)
+    assert (t == 0.0).all()
+    assert np.allclose(mo.handover_error(Wd, T, c), [0.0, 0.1])
+    assert np.allclose(mt.one_minus_omega(T, c, t), 1.0)
 
 
 def test_march_moisture_front_and_thermal_equilibrium():
