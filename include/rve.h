@@ -80,6 +80,11 @@ typedef struct rve_options {
                                 batch of the same call: 1 the nearest solution, 2 (default) the
                                 line and 3 the parabola in the factor through 2 or 3 of them;
                                 0 starts every batch from zero */
+    int     transport_once;  /* macro_update_gauss_points: 1 solves the thermal and moisture cell
+                                problems once per mesh and call and gives all the mesh's points
+                                those K and D (transport is not degraded, Sec. 5, so they are the
+                                same problems); 0 (default) solves all twelve load cases for
+                                every point */
 } rve_options;
 
 /* Isotropic matrix phase (Sec. 1, Sec. 7). */
@@ -284,6 +289,74 @@ int macro_update_gauss_points_surrogate(rve_ctx ctx, const rve_mesh* meshes,
                                         const double* t_h, const int32_t* mesh_id, double* C,
                                         double* K, double* D, int32_t* status, uint8_t* fallback,
                                         rve_stats* stats);
+
+/* ------------------------------------------------------ coupled macro step
+ * The macro level of the paper's framework (Secs. 3, 4 and 5): heat and
+ * moisture transport through the structure with the homogenised conductivity
+ * and diffusivity (Eq. Eq_field, discretised with linear tetrahedra as
+ * Eq. Eq_field_disc, consistent capacity matrix), advanced by one implicit
+ * (backward Euler) step at a time, with one exposed face held at a prescribed
+ * temperature and moisture content and zero flux elsewhere; then, at the four
+ * Gauss points of every tetrahedron, the degradation field 1 - omega advanced
+ * by backward Euler of the rate form (Eq. Eq_Model_RateForm) at the new T and c.
+ * Each Gauss point is handed to the RVE path as (T, c, t_eq), t_eq being the
+ * exposure time for which the closed form (Eq. Eq_Model_final1) at the point's
+ * current T and c gives its 1 - omega, so that macro_update_gauss_points[_dev]
+ * or the surrogate refresh its C, K, D.  A point with no moisture now (the
+ * consistent-capacity transport undershoots slightly ahead of the front) gets
+ * t_eq = 0, i.e. is handed over undegraded; the stats count such points that
+ * had degraded and report the largest 1 - omega missed.  Nodes: xyz [nv][3] in m; tets
+ * [nt][4] with positive orientation.  Temperatures in deg C, moisture in wt%,
+ * time in hours.  FP64 throughout. */
+typedef struct rve_macro_s* rve_macro;
+
+typedef struct rve_macro_stats {
+    int32_t iterations_T;       /* PCG iterations of the heat solve */
+    int32_t iterations_c;       /* PCG iterations of the moisture solve */
+    int32_t converged;          /* 1 if both reached rtol */
+    int32_t gauss_points_unencodable; /* points with 1 - omega < 1 but no moisture now: t_eq = 0 hands
+                                         them over as undegraded */
+    double  rel_residual_T, rel_residual_c;
+    double  seconds;
+    double  handover_max_err;   /* largest 1 - omega among those points (the hand-over error) */
+} rve_macro_stats;
+
+/* Copies the mesh and its geometry to the device.  RVE_ERR_BAD_MESH for an
+ * out-of-range index or a non-positive tetrahedron volume. */
+int rve_macro_create(rve_ctx ctx, const double* xyz, int64_t nv, const int32_t* tets, int64_t nt,
+                     rve_macro* out);
+int rve_macro_free(rve_ctx ctx, rve_macro m);
+
+/* Homogenised thermal conductivity K_T [3][3] (W/mK) with volumetric heat
+ * capacity rho_cp (J/m^3K), and moisture diffusivity D_c [3][3] (m^2/s, unit
+ * capacity).  RVE_ERR_NOT_SPD unless both are symmetric positive definite. */
+int rve_macro_set_transport(rve_ctx ctx, rve_macro m, const double K_T[9], double rho_cp, const double D_c[9]);
+
+/* The exposed face: node_mask[nv] (non-zero = held) and its temperature and
+ * moisture content. */
+int rve_macro_set_face(rve_ctx ctx, rve_macro m, const uint8_t* node_mask, double T_C, double c_wt);
+
+/* Uniform initial temperature and moisture; 1 - omega = 1 at every Gauss point. */
+int rve_macro_reset(rve_ctx ctx, rve_macro m, double T0_C, double c0_wt);
+
+/* One coupled step of dt_h hours: both transport solves (Jacobi PCG to the
+ * relative preconditioned residual rtol, at most max_iter iterations), then
+ * the Gauss-point states.  deg NULL = paper constants.  RVE_ERR_STATE before
+ * set_transport, set_face and reset; RVE_ERR_NOT_CONVERGED (fields still
+ * advanced) if rtol was not reached. */
+int rve_macro_step(rve_ctx ctx, rve_macro m, double dt_h, const rve_degradation* deg, double rtol, int max_iter,
+                   rve_macro_stats* stats);
+
+/* Device pointers to the Gauss-point arrays [nt * 4] (tet-major): temperature,
+ * moisture, 1 - omega and t_eq.  Valid until the next step or free; any output
+ * may be NULL.  They can be passed straight to macro_update_gauss_points_dev. */
+int rve_macro_gauss_dev(rve_ctx ctx, rve_macro m, const double** T_gp, const double** c_gp, const double** W_gp,
+                        const double** t_eq_gp);
+
+/* Host copies of the nodal fields [nv] and the Gauss-point arrays [nt * 4];
+ * any output may be NULL. */
+int rve_macro_get(rve_ctx ctx, rve_macro m, double* T_nodal, double* c_nodal, double* T_gp, double* c_gp,
+                  double* W_gp, double* t_eq_gp);
 
 /* ---------------------------------------------------- inspection entry points
  * These expose single steps of the path for parity tests. */

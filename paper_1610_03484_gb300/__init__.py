@@ -36,7 +36,7 @@ class Options(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_iter", C.c_int), ("inner_rtol", C.c_double), ("max_refine", C.c_int),
                 ("check_every", C.c_int), ("batch", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("warm_start", C.c_int)]
+                ("warm_start", C.c_int), ("transport_once", C.c_int)]
 
 
 class MatrixProps(C.Structure):
@@ -50,6 +50,15 @@ class YarnProps(C.Structure):
 class Degradation(C.Structure):
     _fields_ = [("beta", C.c_double), ("Tg_C", C.c_double), ("c_sat_wt", C.c_double),
                 ("apply_to_yarn", C.c_int)]
+
+
+class MacroStats(C.Structure):
+    _fields_ = [("iterations_T", C.c_int32), ("iterations_c", C.c_int32), ("converged", C.c_int32),
+                ("gauss_points_unencodable", C.c_int32), ("rel_residual_T", C.c_double),
+                ("rel_residual_c", C.c_double), ("seconds", C.c_double), ("handover_max_err", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class MeshStats(C.Structure):
@@ -99,6 +108,18 @@ _SIGS = {
     "rve_set_bc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "rve_homogenise": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.POINTER(Stats)]),
+    "rve_macro_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                   C.POINTER(C.c_void_p)]),
+    "rve_macro_free": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rve_macro_set_transport": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    "rve_macro_set_face": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
+    "rve_macro_reset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
+    "rve_macro_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.c_int,
+                                 C.POINTER(MacroStats)]),
+    "rve_macro_gauss_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "rve_macro_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
     "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
@@ -186,7 +207,7 @@ class Context:
 
     def __init__(self, precision=PREC_FP64, rtol=1e-10, max_iter=20000, inner_rtol=1e-6,
                  max_refine=4, check_every=16, batch=0, stream=None, device=0, profile=False,
-                 warm_start=2):
+                 warm_start=2, transport_once=False):
         lib = load_library()
         o = default_options()
         o.device, o.precision, o.rtol, o.max_iter = device, precision, rtol, max_iter
@@ -194,6 +215,7 @@ class Context:
         o.stream = stream
         o.profile = int(profile)
         o.warm_start = (2 if warm_start else 0) if isinstance(warm_start, bool) else int(warm_start)
+        o.transport_once = int(transport_once)
         h = C.c_void_p()
         _check(lib.rve_create(C.byref(h), C.byref(o)), "rve_create")
         self.h = h
@@ -233,6 +255,14 @@ class Context:
         _check(self.lib.rve_mesh_load(self.h, _ptr(xyz), len(xyz), _ptr(tets), len(tets), _ptr(ph), _ptr(fd),
                                       int(p), C.byref(h)), "rve_mesh_load")
         return Mesh(self, h, len(tets), int(p))
+
+    def macro_load(self, xyz, tets) -> "Macro":
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        tets = np.ascontiguousarray(tets, np.int32)
+        h = C.c_void_p()
+        _check(self.lib.rve_macro_create(self.h, _ptr(xyz), len(xyz), _ptr(tets), len(tets), C.byref(h)),
+               "rve_macro_create")
+        return Macro(self, h, len(xyz), len(tets))
 
     def degradation_factor(self, T_C, c_wt, t_h, beta=-0.001682, Tg_C=126.0, c_sat_wt=1.5):
         T = np.ascontiguousarray(T_C, np.float64)
@@ -466,3 +496,52 @@ class Mesh:
 
 __all__ = ["Context", "Mesh", "Surrogate", "RveError", "load_library", "exported_symbols", "BC_DIRICHLET", "BC_PERIODIC",
            "BC_NEUMANN", "PREC_FP64", "PREC_MIXED", "Options", "Stats"]
+
+
+class Macro:
+    """The coupled macro step (heat and moisture transport, Gauss-point degradation)."""
+
+    def __init__(self, ctx: "Context", h, nv: int, nt: int):
+        self.ctx, self.h, self.nv, self.nt = ctx, h, nv, nt
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.rve_macro_free(self.ctx.h, self.h)
+            self.h = None
+
+    def set_transport(self, K_T, rho_cp, D_c):
+        KT = np.ascontiguousarray(K_T, np.float64).reshape(9)
+        Dc = np.ascontiguousarray(D_c, np.float64).reshape(9)
+        _check(self.ctx.lib.rve_macro_set_transport(self.ctx.h, self.h, _ptr(KT), float(rho_cp), _ptr(Dc)),
+               "rve_macro_set_transport")
+
+    def set_face(self, mask, T_C, c_wt):
+        m = np.ascontiguousarray(mask, np.uint8)
+        _check(self.ctx.lib.rve_macro_set_face(self.ctx.h, self.h, _ptr(m), float(T_C), float(c_wt)),
+               "rve_macro_set_face")
+
+    def reset(self, T0_C, c0_wt):
+        _check(self.ctx.lib.rve_macro_reset(self.ctx.h, self.h, float(T0_C), float(c0_wt)), "rve_macro_reset")
+
+    def step(self, dt_h, rtol=1e-12, max_iter=5000, beta=-0.001682, Tg_C=126.0, c_sat_wt=1.5):
+        dg = Degradation(beta, Tg_C, c_sat_wt, 0)
+        st = MacroStats()
+        _check(self.ctx.lib.rve_macro_step(self.ctx.h, self.h, float(dt_h), C.byref(dg), float(rtol),
+                                           int(max_iter), C.byref(st)), "rve_macro_step")
+        return st.as_dict()
+
+    def gauss_dev(self):
+        """Device addresses of the Gauss-point T, c, 1 - omega and t_eq arrays [nt * 4]."""
+        ptrs = [C.c_void_p() for _ in range(4)]
+        _check(self.ctx.lib.rve_macro_gauss_dev(self.ctx.h, self.h, *[C.byref(p) for p in ptrs]),
+               "rve_macro_gauss_dev")
+        return [p.value for p in ptrs]
+
+    def get(self):
+        T = np.zeros(self.nv)
+        c = np.zeros(self.nv)
+        g = [np.zeros(self.nt * 4) for _ in range(4)]
+        _check(self.ctx.lib.rve_macro_get(self.ctx.h, self.h, _ptr(T), _ptr(c), *[_ptr(a) for a in g]),
+               "rve_macro_get")
+        return dict(T=T, c=c, Tg=g[0].reshape(-1, 4), cg=g[1].reshape(-1, 4), W=g[2].reshape(-1, 4),
+                    t_eq=g[3].reshape(-1, 4))

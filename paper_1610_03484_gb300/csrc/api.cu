@@ -773,8 +773,12 @@ struct Solver {
         launch_reduce_partials(L.nby, ncols * 12, m->gpart.as<double>(), m->gsum.as<double>(), s);
         if (mixed) {
             // the volume-averaged stress is a diagnostic (Hill-Mandel): FP32 with
-            // compensated sums, as the inner solve
-            launch_mean_stress<float, double>(m->p, f.nc, ev<float>(m->scale32), x64, m->mpart.as<double>(), L);
+            // compensated sums, as the inner solve, on the FP32-rounded solution
+            // (one conversion per entry instead of one per gathered value)
+            float* u32 = m->x32.as<float>();
+            launch_cast_d2f((int64_t)nv, x64, u32, s);
+            launch_mean_stress<float, float>(m->p, f.nc, ev<float>(m->scale32), u32, m->mpart.as<double>(), L);
+            *launches += 1;
         } else {
             launch_mean_stress<double, double>(m->p, f.nc, ev<double>(m->scale64), x64, m->mpart.as<double>(), L);
         }
@@ -946,10 +950,11 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
         RVE_TRY(keep_warm(0, m->mech));
     }
     // thermal and moisture: transport is not degraded (Sec. 5), so these cell
-    // problems are the same for every point of the mesh.  In the batched call
-    // they are solved once per mesh (one RVE, six columns) and their tensors
-    // are used for all of the mesh's points; a single homogenisation solves them.
-    const bool reuse_scalar = w_host != nullptr;
+    // problems are the same for every point of the mesh.  With transport_once
+    // the batched call solves them once per mesh (one RVE, six columns) and
+    // gives all of the mesh's points their tensors; otherwise every batch solves
+    // them (warm-started from the previous batch's solutions).
+    const bool reuse_scalar = w_host != nullptr && m->ctx->opt.transport_once != 0;
     if (reuse_scalar && m->scal_cached) {
         osc = m->scal_out;
         osc.iterations = 0;
@@ -960,10 +965,18 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
         launch_column_scales<float>(Bs, d_w, 0, false, m->scale32.as<float>(), s);
         m->ctx->launches += 2;
         Solver sv(m, m->scal, Bs);
-        RVE_TRY(sv.run(prec, osc));
+        if (!reuse_scalar && warm_ready(1)) {
+            WarmStart ws;
+            RVE_TRY(build_warm(1, ws));
+            RVE_TRY(sv.run(prec, osc, &ws));
+        } else {
+            RVE_TRY(sv.run(prec, osc));
+        }
         if (reuse_scalar) {
             m->scal_out = osc;
             m->scal_cached = true;
+        } else {
+            RVE_TRY(keep_warm(1, m->scal));
         }
     }
     if (reuse_scalar) {
@@ -1059,6 +1072,7 @@ void rve_default_options(rve_options* o) {
     o->stream = nullptr;
     o->profile = 0;
     o->warm_start = 2;
+    o->transport_once = 0;
 }
 
 int rve_create(rve_ctx* out, const rve_options* opts) {

@@ -1461,6 +1461,8 @@ template void launch_mean_stress<double, double>(int, int, const ElemView<double
                                                  const Launch&);
 template void launch_mean_stress<float, double>(int, int, const ElemView<float>&, const double*, double*,
                                                 const Launch&);
+template void launch_mean_stress<float, float>(int, int, const ElemView<float>&, const float*, double*,
+                                               const Launch&);
 
 // out[w] = sum_b part[b][w]: one block per output value (up to 128 outputs per
 // block row are handled by grid-striding over w).

@@ -1,13 +1,16 @@
 """Batched homogenisation of a single RVE class, for profiling.
 
-    python -m paper_1610_03484_gb300.profile_batch 32,32,10 2 8 [n_points] [rtol] [calls]
+    python -m paper_1610_03484_gb300.profile_batch 32,32,10 2 8 [n_points] [rtol] [calls] [profile]
 
 loads the plain-weave RVE on the given grid at order p, periodic BC, nominal
 constituents, and runs macro_update_gauss_points `calls` times (default 1) on the
 same n_points seeded Gauss points (default: one batch) in batches of B, mixed
 precision; prints the wall time and the solver statistics of each call.  With
 more than one batch the later batches are warm-started, as in the batched
-workload; the first call also forms the per-mesh caches.
+workload; the first call also forms the per-mesh caches.  With profile = 1 the
+PCG iterations are launched one by one from the host (the context's profile
+mode) instead of as the device-side graph loop, so that a profiler that does not
+follow kernels inside conditional graph nodes sees every launch.
 """
 import os
 import sys
@@ -28,7 +31,9 @@ def main(argv):
     n = int(argv[4]) if len(argv) > 4 else B
     rtol = float(argv[5]) if len(argv) > 5 else 1e-8
     calls = int(argv[6]) if len(argv) > 6 else 1
-    ctx = rve.Context(precision=rve.PREC_MIXED, rtol=rtol, inner_rtol=min(1e-5, rtol), batch=B)
+    profile = bool(int(argv[7])) if len(argv) > 7 else False
+    ctx = rve.Context(precision=rve.PREC_MIXED, rtol=rtol, inner_rtol=min(1e-5, rtol), batch=B,
+                      profile=profile)
     xyz, tets, ph, tg = ri.weave_rve(*grid)
     m = ctx.mesh_load(xyz, tets, p, ph, tg)
     m.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)

@@ -65,3 +65,28 @@ def test_autotune_batch_picks_a_candidate_and_is_used(rve):
         assert rel(Ct[g], Co) < 1e-6
         assert rel(Kt[g], Ko) < 1e-6
         assert rel(Dt[g], Do) < 1e-6
+
+
+def test_transport_once_matches_per_point_solves(rve):
+    """Thermal and moisture cell problems do not depend on the degradation
+    state (transport is not degraded): solving them once per mesh gives the
+    same K and D, and the same C, as solving all twelve load cases per point."""
+    grid, p = (6, 6, 4), 2
+    xyz, tets, phase, tangent = ri.weave_rve(*grid)
+    T, c, t, _, _ = ri.gauss_point_states(20, seed=23)
+    out = {}
+    for once in (False, True):
+        with rve.Context(precision=rve.PREC_MIXED, rtol=1e-8, inner_rtol=1e-6, batch=4,
+                         transport_once=once) as ctx:
+            mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
+            mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+            mesh.set_bc(1)
+            Cb, Kb, Db, st, stats, rc = ctx.macro_update([mesh], T, c, t, np.zeros(20, np.int32))
+            assert (st == 0).all()
+            out[once] = (Cb, Kb, Db)
+            mesh.free()
+    for a, b in zip(out[True], out[False]):
+        for g in range(20):
+            assert rel(a[g], b[g]) < 1e-6
+    # every point of the mesh carries the same transport tensors
+    assert np.abs(out[True][1] - out[True][1][0]).max() <= 1e-12 * np.abs(out[True][1][0]).max()
