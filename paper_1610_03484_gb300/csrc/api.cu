@@ -331,7 +331,7 @@ struct Solver {
         // col state: rz, rz0, alpha, beta (4*ncols) + mu (12*ncols) + schur (144*ncols) doubles,
         // then active, iters (ints) and flags
         const size_t nd = (size_t)ncols * (4 + 12 + 144);
-        RVE_TRY(m->colstate.ensure(nd * 8 + (size_t)ncols * 8 + 64));
+        RVE_TRY(m->colstate.ensure(nd * 8 + (size_t)ncols * 12 + 64));
         double* base = m->colstate.as<double>();
         cs64.rz = base;
         cs64.rz0 = base + ncols;
@@ -342,7 +342,9 @@ struct Solver {
         int32_t* ib = reinterpret_cast<int32_t*>(base + nd);
         cs64.active = ib;
         cs64.iters = ib + ncols;
-        cs64.flags = ib + 2 * ncols;
+        cs64.flags = ib + 2 * ncols;            // [0] numeric flag, [1] loop counter
+        cs64.n_list = ib + 2 * ncols + 4;
+        cs64.list = ib + 2 * ncols + 16;
         RVE_CUDA(cudaMemsetAsync(cs64.flags, 0, sizeof(int32_t), s));
         return RVE_OK;
     }
@@ -462,8 +464,9 @@ struct Solver {
         launch_schur<T>(rvw, cs, L);
         launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), false, L, m->cpart.as<double>());
         launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, true, L);
+        launch_compact_active(cs.active, ncols, cs.list, cs.n_list, s);
         launch_pupdate<T>(rvw, r, p, q, cs, true, L);
-        *launches += 5;
+        *launches += 6;
         std::vector<int32_t> act(ncols);
         conv = false;
         int n_act = ncols;
@@ -489,13 +492,15 @@ struct Solver {
         };
         auto iteration = [&](const Launch& Lx) {
             evr(0, Lx.stream);
-            launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active);
+            launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active, cs.list,
+                               cs.n_list);
             evr(1, Lx.stream);
             launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
             evr(2, Lx.stream);
             launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx, m->cpart.as<double>());
             evr(3, Lx.stream);
             launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, Lx);
+            launch_compact_active(cs.active, ncols, cs.list, cs.n_list, Lx.stream);
             evr(4, Lx.stream);
             launch_pupdate<T>(rvw, r, p, q, cs, false, Lx);
             evr(5, Lx.stream);
@@ -544,13 +549,13 @@ struct Solver {
             int32_t loops = 0;
             RVE_CUDA(cudaMemcpyAsync(&loops, cs.flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             RVE_TRY(read_active());
-            *launches += (int64_t)loops * 6;
+            *launches += (int64_t)loops * 7;
             conv = n_act == 0;
         } else {
             RVE_TRY(read_active());
             for (int it = 0; it < max_iter && n_act > 0; ++it) {
                 iteration(L);
-                *launches += 5;
+                *launches += 6;
                 RVE_CUDA(cudaGetLastError());
                 const int n_act_run = n_act;    // columns the iteration just run worked on
                 RVE_TRY(read_active());

@@ -156,17 +156,31 @@ template <int P, int NC, typename T, bool MACRO>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof(T) == 4 && P == 2) ? 2 : 1)) k_operator(ElemView<T> ev, const T* __restrict__ x,
                                                   T* __restrict__ y, double* __restrict__ epart,
                                                   const int32_t* __restrict__ active, int ncols,
-                                                  int cpb) {
+                                                  int cpb, const int32_t* __restrict__ list,
+                                                  const int32_t* __restrict__ n_list) {
     constexpr int NE = Order<P>::NE;
     constexpr int NM = Order<P>::NM;
-    const int rows = blockDim.x / cpb;
-    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
-    const int col = blockIdx.x * cpb + cl;
+    // With a column list the block's threads are spread over the listed (active)
+    // columns only: rows per block grow as columns converge, and no lane is spent
+    // on a converged column.  Otherwise thread (cl, rr) owns column blockIdx.x * cpb
+    // + cl and converged columns skip the element loop (their step length is zero).
+    int cpb_e = cpb, col;
+    bool live;
+    if (list != nullptr) {
+        const int na = *n_list;
+        cpb_e = na > 0 ? na : 1;
+        live = na > 0 && (int)(threadIdx.x / cpb_e) < (int)(blockDim.x / cpb_e);
+        col = live ? list[threadIdx.x % cpb_e] : 0;
+    } else {
+        col = blockIdx.x * cpb + threadIdx.x % cpb;
+        live = !(active && !active[col]);
+    }
+    const int rows = blockDim.x / cpb_e;
+    const int rr = threadIdx.x / cpb_e;
     const int field = (col % 6) >= 3 ? 1 : 0;   // scalar solve: thermal / moisture
     const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
     PartialSum<T> energy;
-    // converged columns skip the element loop (their step length is zero)
-    const int64_t e_end = (active && !active[col]) ? 0 : ev.nt;
+    const int64_t e_end = live ? ev.nt : 0;
 
     for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < e_end; e += (int64_t)gridDim.y * rows) {
         const int32_t* ed = ev.edofs + e * NE;
@@ -314,18 +328,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
     }
     if (epart) {
         double acc[1] = {energy.value()};
-        block_column_reduce<1>(acc, epart, ncols, cpb, col);
+        block_column_reduce<1>(acc, epart, ncols, cpb_e, col);
     }
 }
 
 template <typename T>
 void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
-                     double* energy_partial, const Launch& L, const int32_t* active) {
+                     double* energy_partial, const Launch& L, const int32_t* active, const int32_t* list,
+                     const int32_t* n_list) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+    if (grid.x != 1) list = n_list = nullptr;   // the list maps one block column
 #define RVE_OP_CASE(PP, NCC, MM)                                                                \
     if (p == PP && nc == NCC && macro == MM) {                                                  \
         k_operator<PP, NCC, T, MM><<<grid, block, 0, L.stream>>>(ev, x, y, energy_partial,      \
-                                                                 active, L.ncols, L.cpb);      \
+                                                                 active, L.ncols, L.cpb, list, \
+                                                                 n_list);                      \
         return;                                                                                 \
     }
     RVE_OP_CASE(1, 3, false) RVE_OP_CASE(2, 3, false) RVE_OP_CASE(3, 3, false)
@@ -335,9 +352,40 @@ void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* 
 #undef RVE_OP_CASE
 }
 template void launch_operator<float>(int, int, bool, const ElemView<float>&, const float*, float*,
-                                     double*, const Launch&, const int32_t*);
+                                     double*, const Launch&, const int32_t*, const int32_t*, const int32_t*);
 template void launch_operator<double>(int, int, bool, const ElemView<double>&, const double*,
-                                      double*, double*, const Launch&, const int32_t*);
+                                      double*, double*, const Launch&, const int32_t*, const int32_t*,
+                                      const int32_t*);
+
+// list[0 .. n) = the columns with active != 0 in ascending order: each warp ballots
+// 32 flags, the warp counts are scanned in shared memory, lanes write in order.
+__global__ void __launch_bounds__(256) k_compact_active(const int32_t* __restrict__ active, int ncols,
+                                                        int32_t* __restrict__ list, int32_t* __restrict__ n_list) {
+    __shared__ int counts[8];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < ncols; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const bool a = c < ncols && active[c] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, a);
+        if (lane == 0) counts[warp] = __popc(m);
+        __syncthreads();
+        int off = base;
+        for (int w = 0; w < warp; ++w) off += counts[w];
+        if (a) list[off + __popc(m & ((1u << lane) - 1u))] = c;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) base += counts[w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_list = base;
+}
+
+void launch_compact_active(const int32_t* active, int ncols, int32_t* list, int32_t* n_list, cudaStream_t s) {
+    k_compact_active<<<1, 256, 0, s>>>(active, ncols, list, n_list);
+}
 
 // ------------------------------------- double-float residual (mixed precision)
 // r += -K32 (x + u_macro), where K32 is the operator with exactly the FP32

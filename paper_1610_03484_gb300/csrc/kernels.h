@@ -58,6 +58,8 @@ struct ColState {
     int32_t* active;  // 1 while the column iterates
     int32_t* iters;   // iterations taken
     int32_t* flags;   // [1] bit0: numeric error
+    int32_t* list;    // [ncols] the active columns in ascending order (compacted)
+    int32_t* n_list;  // [1] their number
     double tol;       // relative tolerance on sqrt(rz / rz0)
 };
 
@@ -66,8 +68,13 @@ void upload_basis_tables();
 // y += K x (+ macro load when macro != 0); energy partials x.Kx per column.
 // active (optional, [ncols]): columns with active == 0 are skipped.
 template <typename T>
+// list / n_list (optional, single block column only): the block's threads are spread
+// over the listed (active) columns only, so converged columns cost no lanes.
 void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
-                     double* energy_partial, const Launch& L, const int32_t* active = nullptr);
+                     double* energy_partial, const Launch& L, const int32_t* active = nullptr,
+                     const int32_t* list = nullptr, const int32_t* n_list = nullptr);
+// list[0 .. n) = the columns with active != 0, ascending (one block)
+void launch_compact_active(const int32_t* active, int ncols, int32_t* list, int32_t* n_list, cudaStream_t s);
 
 template <typename T>
 void launch_diag(int p, int nc, int64_t n_rows, const ElemView<T>& ev, T* diag, cudaStream_t s);
