@@ -25,6 +25,8 @@ Contents
                      the macro Gauss points by backward Euler of the rate form
                      (Eq. Eq_Model_RateForm), plus the equivalent exposure time
                      that hands a Gauss point to the RVE path.
+* ``fibre``       -- yarn directions from the potential flow along each yarn
+                     (Sec. 6): Laplace problem per yarn, unit gradient per tet.
 * ``fem``         -- assembly, the three RVE boundary conditions of Sec. 2 in
                      fluctuation form (Eq. micro_disp), sparse direct / CG solves,
                      energy-form tensors (Eqs. Hill_prin, Eq_C_stress,

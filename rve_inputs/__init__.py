@@ -134,6 +134,23 @@ def plain_weave(xyz, tets, geom: WeaveGeometry = WeaveGeometry(), lengths=(1.0, 
     return phase, tangent
 
 
+def plain_weave_yarns(xyz, tets, geom: WeaveGeometry = WeaveGeometry(), lengths=(1.0, 1.0, 1.0)):
+    """Which yarn each tet belongs to (int32, -1 for matrix; same centroid test and
+    tie-break as plain_weave) and each yarn's axis (0 = x for warp, 1 = y for weft)."""
+    c = centroids(xyz, tets) / np.asarray(lengths, dtype=np.float64)
+    yid = np.full(c.shape[0], -1, dtype=np.int32)
+    axes = []
+    hw, ht = 0.5 * geom.width, 0.5 * geom.thickness
+    for k, (axis, pos, sgn) in enumerate(_yarns(geom)):
+        s = c[:, axis]
+        q = c[:, 1 - axis]
+        zc = geom.z_mid + sgn * geom.amplitude * np.sin(2 * np.pi * s)
+        inside = ((q - pos) / hw) ** 2 + ((c[:, 2] - zc) / ht) ** 2 <= 1.0
+        yid[inside & (yid < 0)] = k
+        axes.append(axis)
+    return yid, np.array(axes, dtype=np.int32)
+
+
 def layered(xyz, tets, layer_phase, nz: int, lz: float = 1.0):
     """Laminate along z: tet in z-cell k gets phase layer_phase[k % len]."""
     zc = centroids(xyz, tets)[:, 2]
