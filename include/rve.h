@@ -336,6 +336,10 @@ int rve_macro_set_transport(rve_ctx ctx, rve_macro m, const double K_T[9], doubl
  * moisture content. */
 int rve_macro_set_face(rve_ctx ctx, rve_macro m, const uint8_t* node_mask, double T_C, double c_wt);
 
+/* Held nodes with their own values: values[node * 2 + field] (field 0 temperature,
+ * 1 moisture) for the nodes with node_mask != 0.  Replaces set_face. */
+int rve_macro_set_held(rve_ctx ctx, rve_macro m, const uint8_t* node_mask, const double* values);
+
 /* Uniform initial temperature and moisture; 1 - omega = 1 at every Gauss point. */
 int rve_macro_reset(rve_ctx ctx, rve_macro m, double T0_C, double c0_wt);
 
@@ -346,6 +350,27 @@ int rve_macro_reset(rve_ctx ctx, rve_macro m, double T0_C, double c0_wt);
  * advanced) if rtol was not reached. */
 int rve_macro_step(rve_ctx ctx, rve_macro m, double dt_h, const rve_degradation* deg, double rtol, int max_iter,
                    rve_macro_stats* stats);
+
+/* The steady problem K psi = 0 with the held values (both fields), no time
+ * derivative and no degradation update: the potential solve of the yarn
+ * directions below, or a macro steady state.  Same convergence rule as a step. */
+int rve_macro_solve_steady(rve_ctx ctx, rve_macro m, double rtol, int max_iter, rve_macro_stats* stats);
+
+/* Gradient of one field (0 temperature / potential, 1 moisture) per tetrahedron
+ * [nt][3] (host array), constant on each linear element. */
+int rve_macro_gradients(rve_ctx ctx, rve_macro m, int field, double* grad);
+
+/* Yarn directions from potential flow (Sec. 6): for each yarn y the Laplace
+ * problem grad^2 phi = 0 is solved on its own tetrahedra (yarn_of_tet[e] == y;
+ * -1 = matrix), with phi = 0 on the nodes at the yarn's lower end along its
+ * axis yarn_axis[y] (0 x, 1 y, 2 z), phi = 1 at its upper end and zero flux on
+ * its lateral surface (linear tetrahedra, the GPU PCG of the macro step to rtol).
+ * dir[e][3] (host, in/out) receives grad phi / |grad phi| for every yarn
+ * tetrahedron; matrix tetrahedra, and any with zero gradient, keep their input
+ * value.  The result can be passed as fibre_dir to rve_mesh_load. */
+int rve_fibre_directions(rve_ctx ctx, const double* xyz, int64_t nv, const int32_t* tets, int64_t nt,
+                         const int32_t* yarn_of_tet, int n_yarn, const int32_t* yarn_axis, double rtol,
+                         double* dir);
 
 /* Device pointers to the Gauss-point arrays [nt * 4] (tet-major): temperature,
  * moisture, 1 - omega and t_eq.  Valid until the next step or free; any output

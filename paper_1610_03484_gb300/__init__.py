@@ -120,6 +120,11 @@ _SIGS = {
                                       C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "rve_macro_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
+    "rve_macro_set_held": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_macro_solve_steady": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(MacroStats)]),
+    "rve_macro_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "rve_fibre_directions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                       C.c_int, C.c_void_p, C.c_double, C.c_void_p]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
     "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
@@ -263,6 +268,18 @@ class Context:
         _check(self.lib.rve_macro_create(self.h, _ptr(xyz), len(xyz), _ptr(tets), len(tets), C.byref(h)),
                "rve_macro_create")
         return Macro(self, h, len(xyz), len(tets))
+
+    def fibre_directions(self, xyz, tets, yarn_of_tet, yarn_axis, dir_in, rtol=1e-12):
+        """Yarn directions from potential flow along each yarn (Sec. 6); matrix
+        tetrahedra keep dir_in."""
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        tets = np.ascontiguousarray(tets, np.int32)
+        yid = np.ascontiguousarray(yarn_of_tet, np.int32)
+        ax = np.ascontiguousarray(yarn_axis, np.int32)
+        d = np.array(dir_in, np.float64, copy=True, order="C")
+        _check(self.lib.rve_fibre_directions(self.h, _ptr(xyz), len(xyz), _ptr(tets), len(tets), _ptr(yid), len(ax),
+                                             _ptr(ax), float(rtol), _ptr(d)), "rve_fibre_directions")
+        return d
 
     def degradation_factor(self, T_C, c_wt, t_h, beta=-0.001682, Tg_C=126.0, c_sat_wt=1.5):
         T = np.ascontiguousarray(T_C, np.float64)
@@ -519,6 +536,22 @@ class Macro:
         m = np.ascontiguousarray(mask, np.uint8)
         _check(self.ctx.lib.rve_macro_set_face(self.ctx.h, self.h, _ptr(m), float(T_C), float(c_wt)),
                "rve_macro_set_face")
+
+    def set_held(self, mask, values):
+        m = np.ascontiguousarray(mask, np.uint8)
+        v = np.ascontiguousarray(values, np.float64).reshape(-1)
+        _check(self.ctx.lib.rve_macro_set_held(self.ctx.h, self.h, _ptr(m), _ptr(v)), "rve_macro_set_held")
+
+    def solve_steady(self, rtol=1e-12, max_iter=20000):
+        st = MacroStats()
+        _check(self.ctx.lib.rve_macro_solve_steady(self.ctx.h, self.h, float(rtol), int(max_iter), C.byref(st)),
+               "rve_macro_solve_steady")
+        return st.as_dict()
+
+    def gradients(self, field=0):
+        g = np.zeros((self.nt, 3))
+        _check(self.ctx.lib.rve_macro_gradients(self.ctx.h, self.h, int(field), _ptr(g)), "rve_macro_gradients")
+        return g
 
     def reset(self, T0_C, c0_wt):
         _check(self.ctx.lib.rve_macro_reset(self.ctx.h, self.h, float(T0_C), float(c0_wt)), "rve_macro_reset")

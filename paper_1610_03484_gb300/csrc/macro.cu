@@ -22,13 +22,12 @@
 struct rve_macro_s {
     rve_ctx ctx = nullptr;
     int64_t nv = 0, nt = 0;
-    rve::DevBuf tets, geo, mask, diag, x, b, r, z, p, q, acc, gp, W, flags;
+    rve::DevBuf tets, geo, mask, hold, diag, x, b, r, z, p, q, acc, gp, W, flags;
     std::vector<double> vol_h, grad_h;    // host copies of the geometry
     std::vector<int32_t> tets_h;
     std::vector<uint8_t> mask_h;
     double KT[6] = {}, Dc[6] = {};          // symmetric (xx, yy, zz, xy, yz, zx)
     double rho_cp = 0;
-    double face[2] = {0, 0};
     bool have_transport = false, have_face = false, have_state = false;
     double diag_dt = -1;                    // dt [s] the diagonal was formed for
 };
@@ -196,13 +195,31 @@ __global__ void __launch_bounds__(256) k_macro_pupdate(int64_t n, const double* 
     }
 }
 
-// held rows take the face values
-__global__ void k_macro_hold(int64_t nv, const uint8_t* __restrict__ mask, double T, double c, double* __restrict__ x) {
+// held rows take their prescribed values (hold[node * 2 + field])
+__global__ void k_macro_hold(int64_t nv, const uint8_t* __restrict__ mask, const double* __restrict__ hold,
+                             double* __restrict__ x) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
         if (mask[i]) {
-            x[i * 2] = T;
-            x[i * 2 + 1] = c;
+            x[i * 2] = hold[i * 2];
+            x[i * 2 + 1] = hold[i * 2 + 1];
         }
+}
+
+// grad psi of one field per tetrahedron (constant on a linear element)
+__global__ void k_macro_gradient(int64_t nt, const int32_t* __restrict__ tets, const double* __restrict__ geo,
+                                 const double* __restrict__ x, int field, double* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        const double* g = geo + e * 13 + 1;
+        double gr[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double v = x[(int64_t)tets[e * 4 + a] * 2 + field];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) gr[i] += g[a * 3 + i] * v;
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) out[e * 3 + i] = gr[i];
+    }
 }
 
 __global__ void k_macro_fill(int64_t nv, double T, double c, double* __restrict__ x) {
@@ -428,11 +445,25 @@ int rve_macro_set_face(rve_ctx c, rve_macro m, const uint8_t* node_mask, double 
         set_error("rve_macro_set_face: invalid argument");
         return RVE_ERR_INVALID_ARGUMENT;
     }
+    std::vector<double> hold((size_t)m->nv * 2);
+    for (int64_t i = 0; i < m->nv; ++i) {
+        hold[(size_t)i * 2] = T_C;
+        hold[(size_t)i * 2 + 1] = c_wt;
+    }
+    return rve_macro_set_held(c, m, node_mask, hold.data());
+}
+
+int rve_macro_set_held(rve_ctx c, rve_macro m, const uint8_t* node_mask, const double* values) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !node_mask || !values) {
+        set_error("rve_macro_set_held: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
     m->mask_h.assign(node_mask, node_mask + m->nv);
     for (auto& v : m->mask_h) v = v ? 1 : 0;
     RVE_TRY(upload(m->mask, m->mask_h.data(), m->mask_h.size(), c->stream));
-    m->face[0] = T_C;
-    m->face[1] = c_wt;
+    RVE_TRY(upload(m->hold, values, (size_t)m->nv * 2, c->stream));
+    RVE_CUDA(cudaStreamSynchronize(c->stream));
     m->have_face = true;
     return RVE_OK;
 }
@@ -453,50 +484,40 @@ int rve_macro_reset(rve_ctx c, rve_macro m, double T0_C, double c0_wt) {
     return RVE_OK;
 }
 
-int rve_macro_step(rve_ctx c, rve_macro m, double dt_h, const rve_degradation* deg, double rtol, int max_iter,
-                   rve_macro_stats* st) {
-    RVE_TRY(check_ctx(c));
-    if (!m || !(dt_h > 0) || !(rtol > 0) || max_iter < 1) {
-        set_error("rve_macro_step: invalid argument");
-        return RVE_ERR_INVALID_ARGUMENT;
-    }
-    if (!m->have_transport || !m->have_face || !m->have_state) {
-        set_error("rve_macro_step: set transport, face and initial state first");
-        return RVE_ERR_STATE;
-    }
-    const auto t0 = std::chrono::steady_clock::now();
-    rve_degradation dg{-0.001682, 126.0, 1.5, 0};
-    if (deg) dg = *deg;
-    cudaStream_t s = c->stream;
-    const double dt_s = dt_h * 3600.0;
-    if (m->diag_dt != dt_s) RVE_TRY(build_diag(m, dt_s));
-    const int64_t n = m->nv * 2;
-    double* x = m->x.as<double>();
-    double* b = m->b.as<double>();
-    double* r = m->r.as<double>();
-    double* z = m->z.as<double>();
-    double* p = m->p.as<double>();
-    double* q = m->q.as<double>();
-    double* acc = m->acc.as<double>();
-    const uint8_t* mask = m->mask.as<uint8_t>();
-    const double* diag = m->diag.as<double>();
-    const unsigned ge = grid_for(m->nt), gv = grid_for(n);
+// One implicit transport solve over both fields: (C/dt + K) x' = C/dt x with the
+// held rows at their values; dt_s = infinity gives the steady problem K x = 0.
+// Returns the iterations and final relative residuals per field.
+static int transport_solve(rve_macro mm, double dt_s, double rtol, int max_iter, int its[2], double rel[2],
+                           bool& conv) {
+    cudaStream_t s = mm->ctx->stream;
+    if (mm->diag_dt != dt_s) RVE_TRY(build_diag(mm, dt_s));
+    const int64_t n = mm->nv * 2;
+    double* x = mm->x.as<double>();
+    double* b = mm->b.as<double>();
+    double* r = mm->r.as<double>();
+    double* z = mm->z.as<double>();
+    double* p = mm->p.as<double>();
+    double* q = mm->q.as<double>();
+    double* acc = mm->acc.as<double>();
+    const uint8_t* mask = mm->mask.as<uint8_t>();
+    const double* diag = mm->diag.as<double>();
+    const unsigned ge = grid_for(mm->nt), gv = grid_for(n);
     MacroParams prm;
-    std::memcpy(prm.KT, m->KT, sizeof(prm.KT));
-    std::memcpy(prm.Dc, m->Dc, sizeof(prm.Dc));
-    prm.capT = m->rho_cp / dt_s;
+    std::memcpy(prm.KT, mm->KT, sizeof(prm.KT));
+    std::memcpy(prm.Dc, mm->Dc, sizeof(prm.Dc));
+    prm.capT = mm->rho_cp / dt_s;
     prm.capC = 1.0 / dt_s;
-    // b = C/dt x^n; start from x^n with the face values held
+    // b = C/dt x^n; start from x^n with the held values in place
     MacroParams mass = prm;
     mass.stiff = 0;
     prm.stiff = 1;
     RVE_CUDA(cudaMemsetAsync(b, 0, n * 8, s));
-    k_macro_apply<<<ge, 256, 0, s>>>(m->nt, m->tets.as<int32_t>(), m->geo.as<double>(), x, b, mass);
-    k_macro_hold<<<grid_for(m->nv), 256, 0, s>>>(m->nv, mask, m->face[0], m->face[1], x);
+    k_macro_apply<<<ge, 256, 0, s>>>(mm->nt, mm->tets.as<int32_t>(), mm->geo.as<double>(), x, b, mass);
+    k_macro_hold<<<grid_for(mm->nv), 256, 0, s>>>(mm->nv, mask, mm->hold.as<double>(), x);
     // r = b - A x, z = M^-1 r, (r, z)
     RVE_CUDA(cudaMemsetAsync(q, 0, n * 8, s));
     RVE_CUDA(cudaMemsetAsync(acc, 0, 16 * 8, s));
-    k_macro_apply<<<ge, 256, 0, s>>>(m->nt, m->tets.as<int32_t>(), m->geo.as<double>(), x, q, prm);
+    k_macro_apply<<<ge, 256, 0, s>>>(mm->nt, mm->tets.as<int32_t>(), mm->geo.as<double>(), x, q, prm);
     k_macro_residual<<<gv, 256, 0, s>>>(n, b, q, mask, diag, r, z, acc);
     const double tol2 = rtol * rtol;
     double h[16];
@@ -513,12 +534,13 @@ int rve_macro_step(rve_ctx c, rve_macro m, double dt_h, const rve_degradation* d
     h[0] = h[1] = h[2] = h[3] = 0.0;
     RVE_CUDA(cudaMemcpyAsync(acc, h, 16 * 8, cudaMemcpyHostToDevice, s));
     k_macro_pupdate<<<gv, 256, 0, s>>>(n, z, p, q, acc, 1);
-    int it = 0, its[2] = {0, 0};
+    int it = 0;
+    its[0] = its[1] = 0;
     bool active[2] = {h[12] != 0.0, h[13] != 0.0};
     while ((active[0] || active[1]) && it < max_iter) {
         const int chunk = std::min(8, max_iter - it);
         for (int k = 0; k < chunk; ++k) {
-            k_macro_apply<<<ge, 256, 0, s>>>(m->nt, m->tets.as<int32_t>(), m->geo.as<double>(), p, q, prm);
+            k_macro_apply<<<ge, 256, 0, s>>>(mm->nt, mm->tets.as<int32_t>(), mm->geo.as<double>(), p, q, prm);
             k_macro_dot<<<gv, 256, 0, s>>>(n, p, q, acc);
             k_macro_alpha<<<1, 1, 0, s>>>(acc);
             k_macro_update<<<gv, 256, 0, s>>>(n, mask, diag, x, r, z, p, q, acc);
@@ -534,6 +556,33 @@ int rve_macro_step(rve_ctx c, rve_macro m, double dt_h, const rve_degradation* d
             active[f] = h[12 + f] != 0.0;
         }
     }
+    conv = !(active[0] || active[1]);
+    rel[0] = h[6] > 0 ? std::sqrt(std::max(h[4], 0.0) / h[6]) : 0.0;
+    rel[1] = h[7] > 0 ? std::sqrt(std::max(h[5], 0.0) / h[7]) : 0.0;
+    return RVE_OK;
+}
+
+int rve_macro_step(rve_ctx c, rve_macro m, double dt_h, const rve_degradation* deg, double rtol, int max_iter,
+                   rve_macro_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !(dt_h > 0) || !(rtol > 0) || max_iter < 1) {
+        set_error("rve_macro_step: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (!m->have_transport || !m->have_face || !m->have_state) {
+        set_error("rve_macro_step: set transport, face and initial state first");
+        return RVE_ERR_STATE;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    rve_degradation dg{-0.001682, 126.0, 1.5, 0};
+    if (deg) dg = *deg;
+    const double dt_s = dt_h * 3600.0;
+    int its[2] = {0, 0};
+    double rel[2] = {0, 0};
+    bool conv = false;
+    RVE_TRY(transport_solve(m, dt_s, rtol, max_iter, its, rel, conv));
+    cudaStream_t s = c->stream;
+    double* x = m->x.as<double>();
     // Gauss-point states and the degradation update
     RVE_CUDA(cudaMemsetAsync(m->flags.p, 0, 16, s));
     k_macro_gauss<<<grid_for(m->nt * 4), 256, 0, s>>>(m->nt, m->tets.as<int32_t>(), x, m->W.as<double>(),
@@ -546,12 +595,11 @@ int rve_macro_step(rve_ctx c, rve_macro m, double dt_h, const rve_degradation* d
     RVE_CUDA(cudaMemcpyAsync(&herr, m->flags.as<char>() + 8, 8, cudaMemcpyDeviceToHost, s));
     RVE_CUDA(cudaStreamSynchronize(s));
     RVE_CUDA(cudaGetLastError());
-    const bool conv = !(active[0] || active[1]);
     if (st) {
         st->iterations_T = its[0];
         st->iterations_c = its[1];
-        st->rel_residual_T = h[6] > 0 ? std::sqrt(std::max(h[4], 0.0) / h[6]) : 0.0;
-        st->rel_residual_c = h[7] > 0 ? std::sqrt(std::max(h[5], 0.0) / h[7]) : 0.0;
+        st->rel_residual_T = rel[0];
+        st->rel_residual_c = rel[1];
         st->converged = conv ? 1 : 0;
         st->gauss_points_unencodable = bad;
         st->handover_max_err = herr;
@@ -577,6 +625,127 @@ int rve_macro_gauss_dev(rve_ctx c, rve_macro m, const double** T_gp, const doubl
     if (c_gp) *c_gp = g + n;
     if (W_gp) *W_gp = g + 2 * n;
     if (t_eq_gp) *t_eq_gp = g + 3 * n;
+    return RVE_OK;
+}
+
+int rve_macro_solve_steady(rve_ctx c, rve_macro m, double rtol, int max_iter, rve_macro_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !(rtol > 0) || max_iter < 1) {
+        set_error("rve_macro_solve_steady: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (!m->have_transport || !m->have_face || !m->have_state) {
+        set_error("rve_macro_solve_steady: set transport, held values and initial state first");
+        return RVE_ERR_STATE;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    int its[2] = {0, 0};
+    double rel[2] = {0, 0};
+    bool conv = false;
+    RVE_TRY(transport_solve(m, HUGE_VAL, rtol, max_iter, its, rel, conv));
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->iterations_T = its[0];
+        st->iterations_c = its[1];
+        st->rel_residual_T = rel[0];
+        st->rel_residual_c = rel[1];
+        st->converged = conv ? 1 : 0;
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!conv) {
+        set_error("rve_macro_solve_steady: PCG did not reach rtol within max_iter");
+        return RVE_ERR_NOT_CONVERGED;
+    }
+    return RVE_OK;
+}
+
+int rve_macro_gradients(rve_ctx c, rve_macro m, int field, double* grad) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !grad || (field != 0 && field != 1)) {
+        set_error("rve_macro_gradients: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    cudaStream_t s = c->stream;
+    DevBuf g;
+    RVE_TRY(g.ensure((size_t)m->nt * 3 * 8));
+    k_macro_gradient<<<grid_for(m->nt), 256, 0, s>>>(m->nt, m->tets.as<int32_t>(), m->geo.as<double>(),
+                                                     m->x.as<double>(), field, g.as<double>());
+    RVE_CUDA(cudaGetLastError());
+    RVE_CUDA(cudaMemcpyAsync(grad, g.p, (size_t)m->nt * 3 * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    return RVE_OK;
+}
+
+int rve_fibre_directions(rve_ctx c, const double* xyz, int64_t nv, const int32_t* tets, int64_t nt,
+                         const int32_t* yarn_of_tet, int n_yarn, const int32_t* yarn_axis, double rtol,
+                         double* dir) {
+    RVE_TRY(check_ctx(c));
+    if (!xyz || !tets || !yarn_of_tet || !yarn_axis || !dir || nv < 4 || nt < 1 || n_yarn < 0 || !(rtol > 0)) {
+        set_error("rve_fibre_directions: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    for (int y = 0; y < n_yarn; ++y)
+        if (yarn_axis[y] < 0 || yarn_axis[y] > 2) {
+            set_error("rve_fibre_directions: yarn axis must be 0, 1 or 2");
+            return RVE_ERR_INVALID_ARGUMENT;
+        }
+    for (int y = 0; y < n_yarn; ++y) {
+        // the yarn's own tetrahedra, nodes renumbered
+        std::vector<int64_t> sel;
+        for (int64_t e = 0; e < nt; ++e)
+            if (yarn_of_tet[e] == y) sel.push_back(e);
+        if (sel.empty()) continue;
+        std::vector<int32_t> local(nv, -1), sub_tets(sel.size() * 4);
+        std::vector<double> sub_xyz;
+        int32_t nn = 0;
+        for (size_t i = 0; i < sel.size(); ++i)
+            for (int a = 0; a < 4; ++a) {
+                const int32_t v = tets[sel[i] * 4 + a];
+                if (v < 0 || v >= nv) {
+                    set_error("rve_fibre_directions: vertex index out of range");
+                    return RVE_ERR_BAD_MESH;
+                }
+                if (local[v] < 0) {
+                    local[v] = nn++;
+                    sub_xyz.insert(sub_xyz.end(), xyz + (int64_t)v * 3, xyz + (int64_t)v * 3 + 3);
+                }
+                sub_tets[i * 4 + a] = local[v];
+            }
+        // inlet (phi = 0) and outlet (phi = 1): the yarn's ends along its axis
+        const int ax = yarn_axis[y];
+        double lo = HUGE_VAL, hi = -HUGE_VAL;
+        for (int32_t k = 0; k < nn; ++k) {
+            lo = std::min(lo, sub_xyz[(size_t)k * 3 + ax]);
+            hi = std::max(hi, sub_xyz[(size_t)k * 3 + ax]);
+        }
+        const double tol = 1e-9 * std::max(1.0, hi - lo);
+        std::vector<uint8_t> held(nn, 0);
+        std::vector<double> vals((size_t)nn * 2, 0.0);
+        for (int32_t k = 0; k < nn; ++k) {
+            const double sk = sub_xyz[(size_t)k * 3 + ax];
+            if (sk <= lo + tol || sk >= hi - tol) {
+                held[k] = 1;
+                vals[(size_t)k * 2] = sk >= hi - tol ? 1.0 : 0.0;
+            }
+        }
+        rve_macro m = nullptr;
+        RVE_TRY(rve_macro_create(c, sub_xyz.data(), nn, sub_tets.data(), (int64_t)sel.size(), &m));
+        static const double eye[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        int rc = rve_macro_set_transport(c, m, eye, 1.0, eye);
+        if (rc == RVE_OK) rc = rve_macro_set_held(c, m, held.data(), vals.data());
+        if (rc == RVE_OK) rc = rve_macro_reset(c, m, 0.0, 0.0);
+        if (rc == RVE_OK) rc = rve_macro_solve_steady(c, m, rtol, 20000, nullptr);
+        std::vector<double> g(sel.size() * 3);
+        if (rc == RVE_OK) rc = rve_macro_gradients(c, m, 0, g.data());
+        rve_macro_free(c, m);
+        if (rc != RVE_OK) return rc;
+        for (size_t i = 0; i < sel.size(); ++i) {
+            const double* gi = &g[i * 3];
+            const double nrm = std::sqrt(gi[0] * gi[0] + gi[1] * gi[1] + gi[2] * gi[2]);
+            if (nrm > 0)
+                for (int k = 0; k < 3; ++k) dir[sel[i] * 3 + k] = gi[k] / nrm;
+        }
+    }
     return RVE_OK;
 }
 
