@@ -11,6 +11,7 @@
 #include <memory>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "api_internal.h"
@@ -265,11 +266,11 @@ struct Solver {
     Launch L;
     cudaStream_t s;
     ColState cs64{};
-    int64_t* launches;
+    std::atomic<int64_t>* launches;
 
     Solver(rve_mesh mm, FieldDev& ff, int b)
         : m(mm), f(ff), B(b), ncols(6 * b), n_rows(ff.n_rows), fid(&ff == &mm->mech ? 0 : 1),
-          s(mm->ctx->stream), launches(&mm->ctx->launches) {
+          s(mm->on_own_streams ? mm->stream : mm->ctx->stream), launches(&mm->ctx->launches) {
         L = make_launch(ncols, std::max<int64_t>(n_rows, mm->nt), s);
     }
 
@@ -345,6 +346,7 @@ struct Solver {
         cs64.flags = ib + 2 * ncols;            // [0] numeric flag, [1] loop counter
         cs64.n_list = ib + 2 * ncols + 4;
         cs64.list = ib + 2 * ncols + 16;
+        cs64.tol = reinterpret_cast<const double*>(ib + 2 * ncols + 8);   // 8-byte aligned slot
         RVE_CUDA(cudaMemsetAsync(cs64.flags, 0, sizeof(int32_t), s));
         return RVE_OK;
     }
@@ -458,7 +460,7 @@ struct Solver {
         // counts follow the set of columns still iterating
         const bool prof = m->ctx->opt.profile != 0;
         ColState cs = cs64;
-        cs.tol = tol;
+        RVE_CUDA(cudaMemcpyAsync(const_cast<double*>(cs.tol), &tol, sizeof(double), cudaMemcpyHostToDevice, s));
         RowView<T> rvw = rv<T>(scale);
         ElemView<T> evw = ev<T>(scale);
         launch_schur<T>(rvw, cs, L);
@@ -510,39 +512,70 @@ struct Solver {
             // repeats the iteration's five kernels plus k_pcg_continue, which
             // ends the loop on the device once no column is active or max_iter
             // iterations have run: no host round trip and no idle iterations.
-            const auto g0 = std::chrono::steady_clock::now();
-            cudaGraph_t graph = nullptr;
-            RVE_CUDA(cudaGraphCreate(&graph, 0));
-            struct GraphGuard {
-                cudaGraph_t g;
-                ~GraphGuard() { if (g) cudaGraphDestroy(g); }
-            } gguard{graph};
-            cudaGraphConditionalHandle handle;
-            RVE_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-            cudaGraphNodeParams np = {};
-            np.type = cudaGraphNodeTypeConditional;
-            np.conditional.handle = handle;
-            np.conditional.type = cudaGraphCondTypeWhile;
-            np.conditional.size = 1;
-            cudaGraphNode_t node;
-            RVE_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
-            cudaGraph_t body = np.conditional.phGraph_out[0];
-            Launch Lc = L;
-            Lc.stream = m->ctx->capture;
-            RVE_CUDA(cudaStreamBeginCaptureToGraph(Lc.stream, body, nullptr, nullptr, 0,
-                                                   cudaStreamCaptureModeThreadLocal));
-            iteration(Lc);
-            launch_pcg_continue(handle, cs.active, ncols, cs.flags + 1, max_iter, Lc.stream);
-            RVE_CUDA(cudaStreamEndCapture(Lc.stream, &body));
-            cudaGraphExec_t exec = nullptr;
-            RVE_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-            struct ExecGuard {
-                cudaGraphExec_t e;
-                ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
-            } eguard{exec};
-            m->ctx->prof.graph_host_ms +=
-                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g0).count();
-            m->ctx->prof.graphs++;
+            // The instantiated graph is kept per mesh, field and precision and
+            // reused while every captured parameter is unchanged (the tolerance
+            // lives in device memory).
+            struct Key {
+                int ncols, cpb, rows, nby, p, nc, m, max_iter;
+                int64_t n_rows, n_sup, nt;
+                const void* ptr[18];
+            } key;
+            std::memset(&key, 0, sizeof(key));
+            key.ncols = L.ncols;
+            key.cpb = L.cpb;
+            key.rows = L.rows_per_block;
+            key.nby = L.nby;
+            key.p = m->p;
+            key.nc = f.nc;
+            key.m = rvw.m;
+            key.max_iter = max_iter;
+            key.n_rows = rvw.n_rows;
+            key.n_sup = rvw.n_sup;
+            key.nt = evw.nt;
+            const void* ptrs[18] = {x, r, p, q, m->epart.p, m->rzp.p, m->cpart.p, cs.rz, rvw.scale, rvw.diag,
+                                    rvw.mask, rvw.sup_row, rvw.sup_coef, rvw.sup_of_row, evw.edofs, evw.geo,
+                                    evw.mat, evw.phase};
+            std::memcpy(key.ptr, ptrs, sizeof(ptrs));
+            auto& gc = m->graph_cache[fid][sizeof(T) == 4 ? 1 : 0];
+            const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
+            const bool hit = gc.exec && gc.key.size() == sizeof(key) && std::memcmp(gc.key.data(), kb, sizeof(key)) == 0;
+            if (!hit) {
+                if (gc.exec) {
+                    cudaGraphExecDestroy(gc.exec);
+                    gc.exec = nullptr;
+                }
+                const auto g0 = std::chrono::steady_clock::now();
+                cudaGraph_t graph = nullptr;
+                RVE_CUDA(cudaGraphCreate(&graph, 0));
+                struct GraphGuard {
+                    cudaGraph_t g;
+                    ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+                } gguard{graph};
+                cudaGraphConditionalHandle handle;
+                RVE_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+                cudaGraphNodeParams np = {};
+                np.type = cudaGraphNodeTypeConditional;
+                np.conditional.handle = handle;
+                np.conditional.type = cudaGraphCondTypeWhile;
+                np.conditional.size = 1;
+                cudaGraphNode_t node;
+                RVE_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+                cudaGraph_t body = np.conditional.phGraph_out[0];
+                Launch Lc = L;
+                Lc.stream = m->on_own_streams ? m->capture : m->ctx->capture;
+                RVE_CUDA(cudaStreamBeginCaptureToGraph(Lc.stream, body, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal));
+                iteration(Lc);
+                launch_pcg_continue(handle, cs.active, ncols, cs.flags + 1, max_iter, Lc.stream);
+                RVE_CUDA(cudaStreamEndCapture(Lc.stream, &body));
+                RVE_CUDA(cudaGraphInstantiate(&gc.exec, graph, 0));
+                gc.key.assign(kb, kb + sizeof(key));
+                std::lock_guard<std::mutex> lock(m->ctx->prof_mu);
+                m->ctx->prof.graph_host_ms +=
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g0).count();
+                m->ctx->prof.graphs++;
+            }
+            cudaGraphExec_t exec = gc.exec;
             RVE_CUDA(cudaMemsetAsync(cs.flags + 1, 0, sizeof(int32_t), s));   // loop counter
             RVE_CUDA(cudaGraphLaunch(exec, s));
             RVE_CUDA(cudaGetLastError());
@@ -881,7 +914,7 @@ static int warm_sources(const std::vector<double>& pw, double w, int order, int*
 // Solve B RVEs of one mesh whose degradation factors are in d_w (device).
 int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D,
                           rve_stats* st, const double* w_host) {
-    cudaStream_t s = m->ctx->stream;
+    cudaStream_t s = m->on_own_streams ? m->stream : m->ctx->stream;
     const int ncols = 6 * B;
     RVE_TRY(m->scale64.ensure((size_t)ncols * 2 * 8));
     RVE_TRY(m->scale32.ensure((size_t)ncols * 2 * 4));
@@ -1424,9 +1457,18 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
         }
         groups[mesh_id[g]].push_back(g);
     }
-    int rc_all = RVE_OK;
-    DevBuf d_idx, d_tmp, d_res;
-    std::vector<double> res;
+    std::vector<int> work;
+    bool repeated = false;   // one mesh under two ids: its entries share state, so run in order
+    for (int mi = 0; mi < n_meshes; ++mi) {
+        if (groups[mi].empty()) continue;
+        rve_mesh m = meshes[mi];
+        if (!m || !m->have_materials) {
+            set_error("mesh without materials in macro_update_gauss_points");
+            return RVE_ERR_STATE;
+        }
+        for (int mj : work) repeated |= meshes[mj] == m;
+        work.push_back(mi);
+    }
     // host copy of the states, used only to order the points of each mesh
     std::vector<double> hT_all(G), hc_all(G), ht_all(G);
     if (G > 0) {
@@ -1435,14 +1477,11 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
         RVE_CUDA(cudaMemcpyAsync(ht_all.data(), t_dev, G * 8, cudaMemcpyDeviceToHost, s));
         RVE_CUDA(cudaStreamSynchronize(s));
     }
-    for (int mi = 0; mi < n_meshes; ++mi) {
+    // One mesh's points in warm-started batches, on stream sm; results scattered
+    // into the caller's arrays (each point written by exactly one mesh).
+    auto solve_mesh = [&](int mi, cudaStream_t sm, rve_stats* stm, std::string* err) -> int {
         auto& grp = groups[mi];
-        if (grp.empty()) continue;
         rve_mesh m = meshes[mi];
-        if (!m || !m->have_materials) {
-            set_error("mesh without materials in macro_update_gauss_points");
-            return RVE_ERR_STATE;
-        }
         const int Bmax = c->opt.batch > 0 ? c->opt.batch : (m->tuned_batch > 0 ? m->tuned_batch : auto_batch(m));
         // order the points by degradation factor so that each batch starts from
         // the solutions of its neighbours in the previous batch; no solution is
@@ -1472,34 +1511,129 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
         m->warm_w[0].clear();
         m->warm_w[1].clear();
         m->scal_cached = false;
-        RVE_TRY(upload(d_idx, grp.data(), grp.size(), s));
+        DevBuf d_idx, d_tmp, d_res;
+        std::vector<double> res;
+        int rc_mesh = RVE_OK;
+        auto fail = [&](int rc) {
+            *err = last_error();
+            return rc;
+        };
+        int rc0 = upload(d_idx, grp.data(), grp.size(), sm);
+        if (rc0 != RVE_OK) return fail(rc0);
         for (size_t off = 0; off < grp.size(); off += Bmax) {
             const int B = (int)std::min<size_t>(Bmax, grp.size() - off);
             const int64_t* idx = d_idx.as<int64_t>() + off;
-            RVE_TRY(d_tmp.ensure((size_t)B * 4 * 8));
+            rc0 = d_tmp.ensure((size_t)B * 4 * 8);
+            if (rc0 != RVE_OK) return fail(rc0);
             double* st3 = d_tmp.as<double>();
             double* dw = st3 + 3 * B;
-            launch_gather_states(B, idx, T_dev, c_dev, t_dev, st3, s);
-            launch_degradation(B, st3, st3 + B, st3 + 2 * B, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, dw, s);
+            launch_gather_states(B, idx, T_dev, c_dev, t_dev, st3, sm);
+            launch_degradation(B, st3, st3 + B, st3 + 2 * B, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, dw, sm);
             c->launches += 2;
             res.assign((size_t)B * 55, 0.0);
             std::vector<double> hC((size_t)B * 36), hK((size_t)B * 9), hD((size_t)B * 9);
-            int rc = homogenise_batch(m, B, dw, hC.data(), hK.data(), hD.data(), st,
+            int rc = homogenise_batch(m, B, dw, hC.data(), hK.data(), hD.data(), stm,
                                       c->opt.warm_start ? &wg[off] : nullptr);
-            if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return rc;
-            if (rc != RVE_OK) rc_all = rc;
+            if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return fail(rc);
+            if (rc != RVE_OK) {
+                rc_mesh = rc;
+                *err = last_error();
+            }
             for (int b = 0; b < B; ++b) {
                 std::memcpy(&res[(size_t)b * 55], &hC[(size_t)b * 36], 36 * 8);
                 std::memcpy(&res[(size_t)b * 55 + 36], &hK[(size_t)b * 9], 9 * 8);
                 std::memcpy(&res[(size_t)b * 55 + 45], &hD[(size_t)b * 9], 9 * 8);
                 res[(size_t)b * 55 + 54] = rc;
             }
-            RVE_TRY(upload(d_res, res.data(), res.size(), s));
-            launch_scatter_results(B, idx, d_res.as<double>(), C_dev, K_dev, D_dev, status_dev, s);
+            rc0 = upload(d_res, res.data(), res.size(), sm);
+            if (rc0 != RVE_OK) return fail(rc0);
+            launch_scatter_results(B, idx, d_res.as<double>(), C_dev, K_dev, D_dev, status_dev, sm);
             c->launches++;
-            RVE_CUDA(cudaGetLastError());
-            RVE_CUDA(cudaStreamSynchronize(s));   // res is reused by the next batch
+            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(sm) != cudaSuccess) {
+                set_error("macro_update_gauss_points: a batch's kernels failed");
+                return fail(RVE_ERR_CUDA);
+            }
         }
+        return rc_mesh;
+    };
+    // Meshes are independent: with more than one, each gets its own streams and host
+    // thread so that one mesh's small kernels and host round trips overlap another's
+    // work.  Profile mode keeps one stream (its event timings assume it).
+    const bool parallel = work.size() > 1 && c->opt.profile == 0 && !repeated;
+    if (!parallel) {
+        int rc_all = RVE_OK;
+        for (int mi : work) {
+            std::string err;
+            const int rc = solve_mesh(mi, s, st, &err);
+            if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return rc;
+            if (rc != RVE_OK) rc_all = rc;
+        }
+        return rc_all;
+    }
+    cudaEvent_t ready;
+    RVE_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    struct EventGuard {
+        cudaEvent_t e;
+        ~EventGuard() { cudaEventDestroy(e); }
+    } eg{ready};
+    RVE_CUDA(cudaEventRecord(ready, s));
+    for (int mi : work) {
+        rve_mesh m = meshes[mi];
+        if (!m->stream) RVE_CUDA(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
+        if (!m->capture) RVE_CUDA(cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking));
+        RVE_CUDA(cudaStreamWaitEvent(m->stream, ready, 0));
+    }
+    struct OwnStreams {   // back to the context's streams however this call ends
+        const rve_mesh* ms;
+        const std::vector<int>& w;
+        ~OwnStreams() {
+            for (int mi : w) ms[mi]->on_own_streams = false;
+        }
+    } own{meshes, work};
+    for (int mi : work) meshes[mi]->on_own_streams = true;
+    const size_t nw = work.size();
+    std::vector<int> rcs(nw, RVE_OK);
+    std::vector<std::string> errs(nw);
+    std::vector<rve_stats> sts(nw);
+    for (auto& x : sts) {
+        std::memset(&x, 0, sizeof(x));
+        x.converged = 1;
+    }
+    {
+        std::vector<std::thread> threads;
+        for (size_t k = 0; k < nw; ++k)
+            threads.emplace_back([&, k]() {
+                cudaSetDevice(c->device);
+                rcs[k] = solve_mesh(work[k], meshes[work[k]]->stream, st ? &sts[k] : nullptr, &errs[k]);
+            });
+        for (auto& t : threads) t.join();
+    }
+    // the caller's stream continues after every mesh's work
+    for (int mi : work) {
+        rve_mesh m = meshes[mi];
+        cudaEvent_t done;
+        RVE_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        cudaEventRecord(done, m->stream);
+        cudaStreamWaitEvent(s, done, 0);
+        cudaEventDestroy(done);
+    }
+    if (st)
+        for (const auto& x : sts) {
+            st->iterations_mech = std::max(st->iterations_mech, x.iterations_mech);
+            st->iterations_scalar = std::max(st->iterations_scalar, x.iterations_scalar);
+            st->refine_sweeps = std::max(st->refine_sweeps, x.refine_sweeps);
+            st->converged = st->converged && x.converged;
+            st->rel_residual_mech = std::max(st->rel_residual_mech, x.rel_residual_mech);
+            st->rel_residual_scalar = std::max(st->rel_residual_scalar, x.rel_residual_scalar);
+            st->hill_mandel_mech = std::max(st->hill_mandel_mech, x.hill_mandel_mech);
+            st->hill_mandel_scalar = std::max(st->hill_mandel_scalar, x.hill_mandel_scalar);
+        }
+    int rc_all = RVE_OK;
+    for (size_t k = 0; k < nw; ++k) {
+        if (rcs[k] == RVE_OK) continue;
+        set_error(errs[k]);
+        if (rcs[k] != RVE_ERR_NOT_CONVERGED && rcs[k] != RVE_ERR_NUMERIC) return rcs[k];
+        rc_all = rcs[k];
     }
     return rc_all;
 }

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -135,10 +137,11 @@ struct rve_ctx_s {
     cudaStream_t capture = nullptr;   // private stream used only to capture graphs
     bool own_stream = false;
     int device = 0;
-    int64_t launches = 0;
+    std::atomic<int64_t> launches{0};
     // profile mode: event pairs around every operator launch of a captured body
     std::vector<cudaEvent_t> ev;
     rve::ProfCounters prof;
+    std::mutex prof_mu;   // guards prof against the batched call's per-mesh threads
     ~rve_ctx_s() {
         for (auto e : ev) cudaEventDestroy(e);
     }
@@ -146,6 +149,24 @@ struct rve_ctx_s {
 
 struct rve_mesh_s {
     rve_ctx ctx = nullptr;
+    // the mesh's own streams, used (on_own_streams) only while the batched call
+    // solves several meshes concurrently, one host thread per mesh; every other
+    // call runs on the context's streams
+    cudaStream_t stream = nullptr, capture = nullptr;
+    bool on_own_streams = false;
+    // instantiated PCG iteration graphs per field and precision, reused while the
+    // captured launch parameters (kept as raw bytes in key) stay the same
+    struct GraphCache {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<unsigned char> key;
+    } graph_cache[2][2];
+    ~rve_mesh_s() {
+        for (auto& row : graph_cache)
+            for (auto& g : row)
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (stream) cudaStreamDestroy(stream);
+        if (capture) cudaStreamDestroy(capture);
+    }
     int p = 1;
     int bc = RVE_BC_DIRICHLET;
     int64_t nv = 0, nt = 0;

@@ -1204,7 +1204,8 @@ __global__ void __launch_bounds__(256) k_finalize_beta(int m, const double* __re
     }
     cs.beta[col] = rz / cs.rz[col];
     cs.rz[col] = rz;
-    if (rz <= cs.tol * cs.tol * cs.rz0[col]) cs.active[col] = 0;
+    const double tol = *cs.tol;
+    if (rz <= tol * tol * cs.rz0[col]) cs.active[col] = 0;
 }
 
 void launch_finalize_beta(int m, const double* rz_partial, const double* c_partial, ColState cs,

@@ -60,7 +60,8 @@ struct ColState {
     int32_t* flags;   // [1] bit0: numeric error
     int32_t* list;    // [ncols] the active columns in ascending order (compacted)
     int32_t* n_list;  // [1] their number
-    double tol;       // relative tolerance on sqrt(rz / rz0)
+    const double* tol;  // [1] relative tolerance on sqrt(rz / rz0), in device memory so that a
+                        // captured iteration graph can be reused with another tolerance
 };
 
 void upload_basis_tables();

@@ -90,3 +90,41 @@ def test_transport_once_matches_per_point_solves(rve):
             assert rel(a[g], b[g]) < 1e-6
     # every point of the mesh carries the same transport tensors
     assert np.abs(out[True][1] - out[True][1][0]).max() <= 1e-12 * np.abs(out[True][1][0]).max()
+
+
+def test_meshes_solved_concurrently_match_separate_calls(rve):
+    """Points on several meshes in one call (one host thread and stream per mesh)
+    give what each mesh gives on its own, and the oracle."""
+    specs = [((6, 6, 4), 1), ((6, 6, 4), 2), ((4, 4, 3), 2)]
+    T, c, t, _, _ = ri.gauss_point_states(30, seed=31)
+    mid = np.arange(30, dtype=np.int32) % len(specs)
+    with rve.Context(precision=rve.PREC_MIXED, rtol=1e-8, inner_rtol=1e-6, batch=4) as ctx:
+        meshes = []
+        for grid, p in specs:
+            xyz, tets, phase, tangent = ri.weave_rve(*grid)
+            m = ctx.mesh_load(xyz, tets, p, phase, tangent)
+            m.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+            m.set_bc(1)
+            meshes.append(m)
+        Ca, Ka, Da, st, stats, rc = ctx.macro_update(meshes, T, c, t, mid)
+        assert (st == 0).all()
+        for k, m in enumerate(meshes):
+            sel = np.nonzero(mid == k)[0]
+            Cs, Ks, Ds, st2, _, _ = ctx.macro_update([m], T[sel], c[sel], t[sel], np.zeros(len(sel), np.int32))
+            assert (st2 == 0).all()
+            for i, g in enumerate(sel):
+                assert rel(Ca[g], Cs[i]) < 1e-8
+                assert rel(Ka[g], Ks[i]) < 1e-8
+        for m in meshes:
+            m.free()
+    # one point of each mesh against the oracle
+    for k, (grid, p) in enumerate(specs):
+        g = int(np.nonzero(mid == k)[0][0])
+        xyz, tets, phase, tangent = ri.weave_rve(*grid)
+        w = float(mt.one_minus_omega(T[g], c[g], t[g]))
+        mat = ri.MatrixProps(E=ri.NOMINAL_MATRIX.E * w, nu=ri.NOMINAL_MATRIX.nu, k=ri.NOMINAL_MATRIX.k,
+                             d=ri.NOMINAL_MATRIX.d)
+        D, K, Dd = mt.element_tensors(phase, tangent, mat, ri.NOMINAL_YARN)
+        Co, Ko, Do = fem.homogenise(xyz, tets, grid, p, 1, D, K, Dd)
+        assert rel(Ca[g], Co) < 1e-6
+        assert rel(Ka[g], Ko) < 1e-6
