@@ -20,7 +20,15 @@ What it computes, in the paper's terms:
   closed form (Eq. Eq_Model_final1) at the point's current T and c gives W, so
   that a macro Gauss point can be handed to the RVE path as (T, c, t_eq); where
   there is no moisture now the closed form cannot reach W < 1, and t_eq = 0
-  hands the point over undegraded (its error, 1 - W, is reported).
+  hands the point over undegraded (its error, 1 - W, is reported);
+* the macro mechanical problem of the fully nested FE^2 step (Sec. 5): linear
+  elasticity on the same linear tetrahedra with the homogenised stiffness
+  C_bar given per macro Gauss point, K = sum_T sum_g |T| / 4 B^T C_g B (the
+  4-point rule; C_g taken by its symmetric part, since the homogenised
+  stiffness is symmetric and only rounding makes it otherwise), the load a
+  uniform traction on a set of boundary faces (consistent nodal forces
+  t |F| / 3 on each face node), displacements prescribed per degree of freedom
+  (symmetry rollers), and the Gauss-point stresses sigma_g = C_g B u.
 
 The linear systems are solved with a sparse direct factorisation.
 """
@@ -133,3 +141,83 @@ def march(xyz, tets, face, KT, rho_cp, Dc, T0, c0, T_face, c_face, dt_h, n_steps
         out.append(dict(T=T.copy(), c=c.copy(), Tg=Tg, cg=cg, W=W.copy(),
                         t_eq=equivalent_time(W, Tg, cg, deg)))
     return out
+
+
+# ------------------------------------------------ macro mechanics (Sec. 5)
+def strain_operator(g):
+    """B [nt, 6, 12]: the Voigt strain of a linear tetrahedron (order of
+    materials.VOIGT, engineering shear) from its nodal displacements, DOF
+    a * 3 + i for node a and component i; g are the barycentric gradients."""
+    nt = len(g)
+    B = np.zeros((nt, 6, 12))
+    for a in range(4):
+        for J, (i, j) in enumerate(mt.VOIGT):
+            if i == j:
+                B[:, J, a * 3 + i] = g[:, a, i]
+            else:                       # 2 eps_ij = du_i/dx_j + du_j/dx_i
+                B[:, J, a * 3 + i] += g[:, a, j]
+                B[:, J, a * 3 + j] += g[:, a, i]
+    return B
+
+
+def _sym(C_gp):
+    C = np.asarray(C_gp, float)
+    return 0.5 * (C + np.swapaxes(C, -1, -2))
+
+
+def elastic_assemble(xyz, tets, C_gp):
+    """Macro stiffness from the Gauss-point stiffness C_gp [nt, 4, 6, 6]:
+    K = sum over tetrahedra and their 4 Gauss points of |T| / 4 B^T C_g B,
+    3 DOFs per node (node * 3 + component)."""
+    vol, g = p1_geometry(xyz, tets)
+    B = strain_operator(g)
+    C = _sym(C_gp)
+    Ke = np.zeros((len(tets), 12, 12))
+    for q in range(4):
+        Ke += np.einsum("t,tJa,tJK,tKb->tab", vol / 4.0, B, C[:, q], B)
+    dof = (tets[:, :, None] * 3 + np.arange(3)[None, None, :]).reshape(len(tets), 12)
+    rows = np.repeat(dof, 12, axis=1).reshape(-1)
+    cols = np.tile(dof, (1, 12)).reshape(-1)
+    n = len(xyz) * 3
+    return sp.csr_matrix((Ke.reshape(-1), (rows, cols)), shape=(n, n))
+
+
+# local vertex triples of the four faces of a tetrahedron
+_FACES = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
+
+
+def traction_load(xyz, tets, face_nodes, t):
+    """Nodal forces [nv * 3] of a uniform traction t [3] (force per area) on
+    every tetrahedron face whose three vertices are all in face_nodes: each
+    of the three receives t |F| / 3, |F| the triangle's area."""
+    f = np.zeros(len(xyz) * 3)
+    t = np.asarray(t, float)
+    for e in range(len(tets)):
+        for tri in _FACES:
+            v = tets[e, list(tri)]
+            if face_nodes[v].all():
+                X = xyz[v]
+                area = 0.5 * np.linalg.norm(np.cross(X[1] - X[0], X[2] - X[0]))
+                for k in v:
+                    f[k * 3:k * 3 + 3] += t * area / 3.0
+    return f
+
+
+def elastic_solve(K, f, fixed, values=None):
+    """u with K u = f on the free DOFs and u = values on the fixed ones."""
+    u = np.zeros(K.shape[0]) if values is None else np.where(fixed, values, 0.0).astype(float)
+    free = np.nonzero(~fixed)[0]
+    fix = np.nonzero(fixed)[0]
+    K = K.tocsr()
+    rhs = f[free] - K[free][:, fix] @ u[fix]
+    u[free] = spla.splu(K[free][:, free].tocsc()).solve(rhs)
+    return u
+
+
+def gauss_stress(xyz, tets, u, C_gp):
+    """sigma_g = C_g B u_T at each Gauss point [nt, 4, 6] (B constant per tet)."""
+    _, g = p1_geometry(xyz, tets)
+    B = strain_operator(g)
+    ue = u.reshape(-1, 3)[tets].reshape(len(tets), 12)
+    eps = np.einsum("tJa,ta->tJ", B, ue)
+    return np.einsum("tqJK,tK->tqJ", _sym(C_gp), eps)
