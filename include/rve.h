@@ -383,6 +383,53 @@ int rve_macro_gauss_dev(rve_ctx ctx, rve_macro m, const double** T_gp, const dou
 int rve_macro_get(rve_ctx ctx, rve_macro m, double* T_nodal, double* c_nodal, double* T_gp, double* c_gp,
                   double* W_gp, double* t_eq_gp);
 
+/* ------------------------------------------------- macro mechanics (FE^2)
+ * The macro mechanical problem of the fully nested FE^2 step (Sec. 5): linear
+ * elasticity on the macro mesh of rve_macro_create with the homogenised
+ * stiffness C_bar of every macro Gauss point.  Linear tetrahedra, 3 DOFs per
+ * node (u[node * 3 + component], m), K = sum over tetrahedra and Gauss points
+ * of |T| / 4 B^T C_g B, FP64 Jacobi PCG on the device. */
+
+typedef struct rve_macro_mech_stats {
+    int32_t iterations;         /* PCG iterations */
+    int32_t converged;          /* 1 if rtol was reached */
+    double  rel_residual;       /* sqrt((r, M^-1 r) / max((f, M^-1 f), (r0, M^-1 r0))), free DOFs */
+    double  seconds;
+} rve_macro_mech_stats;
+
+/* Prescribed displacements: fixed[nv * 3] (host; non-zero = held DOF) at
+ * values[nv * 3] (host, m; NULL = 0, e.g. symmetry rollers).  The first call
+ * also sets the starting displacement to zero. */
+int rve_macro_mech_set_bc(rve_ctx ctx, rve_macro m, const uint8_t* fixed, const double* values);
+
+/* The displacement the next solve starts from: u[nv * 3] (host, m), NULL =
+ * zero.  A restart from a saved state, or a solve from rest. */
+int rve_macro_mech_set_u(rve_ctx ctx, rve_macro m, const double* u);
+
+/* The load: a uniform traction t[3] (Pa) on every element face whose three
+ * vertices are all marked in face_nodes[nv] (host); each of those vertices
+ * receives t |F| / 3 (the consistent nodal force).  Only boundary faces may
+ * have all three vertices marked (a plane face of the body, say).  add = 0
+ * replaces the load, add = 1 adds to it (several loaded faces). */
+int rve_macro_mech_set_traction(rve_ctx ctx, rve_macro m, const uint8_t* face_nodes, const double t[3], int add);
+
+/* Solves K u = f with the held DOFs at their values, starting from the
+ * previous solution (a warm start across macro time steps), then forms the
+ * Gauss-point stresses sigma_g = C_g B u.  C_gp[nt * 4][6][6] (Pa) is tet-major
+ * in the Gauss-point order of rve_macro_gauss_dev, Voigt [xx, yy, zz, xy, yz,
+ * zx] with engineering shear as the C output of macro_update_gauss_points*;
+ * on the device if C_on_device (read during the call only), else a host array.
+ * Each C_g enters by its symmetric part.  RVE_ERR_STATE before set_bc and
+ * set_traction; RVE_ERR_NOT_CONVERGED (u and stresses still written) if rtol
+ * was not reached within max_iter. */
+int rve_macro_mech_solve(rve_ctx ctx, rve_macro m, const double* C_gp, int C_on_device, double rtol, int max_iter,
+                         rve_macro_mech_stats* stats);
+
+/* Host copies of u[nv * 3], the Gauss-point stresses [nt * 4][6] (Pa, Voigt
+ * as above) and the nodal load [nv * 3] (N); any output may be NULL.
+ * RVE_ERR_STATE for an output that has not been set or solved yet. */
+int rve_macro_mech_get(rve_ctx ctx, rve_macro m, double* u, double* stress_gp, double* load);
+
 /* ---------------------------------------------------- inspection entry points
  * These expose single steps of the path for parity tests. */
 

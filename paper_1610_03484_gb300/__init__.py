@@ -61,6 +61,14 @@ class MacroStats(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class MacroMechStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class MeshStats(C.Structure):
     _fields_ = [("n_vertices", C.c_int64), ("n_edges", C.c_int64), ("n_faces", C.c_int64),
                 ("n_tets", C.c_int64), ("n_scalar_dofs", C.c_int64), ("n_constrained", C.c_int64),
@@ -123,6 +131,12 @@ _SIGS = {
     "rve_macro_set_held": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_macro_solve_steady": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(MacroStats)]),
     "rve_macro_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "rve_macro_mech_set_bc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_macro_mech_set_u": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_macro_mech_set_traction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rve_macro_mech_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
+                                       C.POINTER(MacroMechStats)]),
+    "rve_macro_mech_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_fibre_directions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                        C.c_int, C.c_void_p, C.c_double, C.c_void_p]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -578,3 +592,51 @@ class Macro:
                "rve_macro_get")
         return dict(T=T, c=c, Tg=g[0].reshape(-1, 4), cg=g[1].reshape(-1, 4), W=g[2].reshape(-1, 4),
                     t_eq=g[3].reshape(-1, 4))
+
+    # macro mechanics of the nested FE^2 step (Sec. 5)
+    def mech_set_bc(self, fixed, values=None):
+        """fixed [nv, 3] (held DOFs) at values [nv, 3] (m; None = 0)."""
+        f = np.ascontiguousarray(fixed, np.uint8).reshape(-1)
+        v = None if values is None else np.ascontiguousarray(values, np.float64).reshape(-1)
+        if f.size != self.nv * 3 or (v is not None and v.size != self.nv * 3):
+            raise ValueError("fixed and values must have nv * 3 entries")
+        _check(self.ctx.lib.rve_macro_mech_set_bc(self.ctx.h, self.h, _ptr(f), _ptr(v) if v is not None else None),
+               "rve_macro_mech_set_bc")
+
+    def mech_set_u(self, u=None):
+        """Starting displacement of the next solve ([nv, 3], m; None = rest)."""
+        v = None if u is None else np.ascontiguousarray(u, np.float64).reshape(-1)
+        if v is not None and v.size != self.nv * 3:
+            raise ValueError("u must have nv * 3 entries")
+        _check(self.ctx.lib.rve_macro_mech_set_u(self.ctx.h, self.h, _ptr(v)), "rve_macro_mech_set_u")
+
+    def mech_set_traction(self, face_nodes, t, add=False):
+        m = np.ascontiguousarray(face_nodes, np.uint8).reshape(-1)
+        tv = np.ascontiguousarray(t, np.float64).reshape(3)
+        if m.size != self.nv:
+            raise ValueError("face_nodes must have nv entries")
+        _check(self.ctx.lib.rve_macro_mech_set_traction(self.ctx.h, self.h, _ptr(m), _ptr(tv), int(bool(add))),
+               "rve_macro_mech_set_traction")
+
+    def mech_solve(self, C_gp, rtol=1e-12, max_iter=20000):
+        """C_gp: host array [nt, 4, 6, 6] (or [nt * 4, 6, 6]), or an integer device
+        address of that layout (e.g. the C output of Context.macro_update_dev)."""
+        st = MacroMechStats()
+        if isinstance(C_gp, int):
+            ptr, on_dev = C.c_void_p(C_gp), 1
+        else:
+            arr = np.ascontiguousarray(C_gp, np.float64).reshape(-1)
+            if arr.size != self.nt * 4 * 36:
+                raise ValueError("C_gp must have nt * 4 * 36 entries")
+            ptr, on_dev = _ptr(arr), 0
+        _check(self.ctx.lib.rve_macro_mech_solve(self.ctx.h, self.h, ptr, on_dev, float(rtol), int(max_iter),
+                                                 C.byref(st)), "rve_macro_mech_solve")
+        return st.as_dict()
+
+    def mech_get(self):
+        u = np.zeros((self.nv, 3))
+        sig = np.zeros((self.nt, 4, 6))
+        f = np.zeros((self.nv, 3))
+        _check(self.ctx.lib.rve_macro_mech_get(self.ctx.h, self.h, _ptr(u), _ptr(sig), _ptr(f)),
+               "rve_macro_mech_get")
+        return dict(u=u, stress=sig, load=f)

@@ -8,6 +8,11 @@
 //
 // Both fields are solved together as two columns of one matrix-free operator:
 // vectors v[node * 2 + field], field 0 temperature [C], field 1 moisture [wt%].
+//
+// The macro mechanical problem of the fully nested FE^2 step (Sec. 5) uses the
+// same mesh: linear elasticity with the homogenised stiffness C_bar of every
+// macro Gauss point, vectors u[node * 3 + component], solved by the same Jacobi
+// PCG with one field and a per-DOF held mask.
 // Everything here is FP64: the macro mesh is small next to the RVE batches.
 #include <cuda_runtime.h>
 
@@ -30,6 +35,11 @@ struct rve_macro_s {
     double rho_cp = 0;
     bool have_transport = false, have_face = false, have_state = false;
     double diag_dt = -1;                    // dt [s] the diagonal was formed for
+    // macro mechanics: held DOFs and their values, traction load, Jacobi
+    // diagonal, displacement, per-tet mean stiffness [nt][36], Gauss-point
+    // stiffness staged from the host [nt*4][36] and stresses [nt*4][6]
+    rve::DevBuf mfix, mval, mload, mdiag, mu, cm, cgp, msig;
+    bool have_mech_bc = false, have_mech_load = false, have_mech_u = false, have_mech_sig = false;
 };
 
 namespace rve {
@@ -107,31 +117,35 @@ __device__ __forceinline__ void block_add2(double a0, double a1, double* out) {
 
 // r = b - y on free rows (0 on held rows), z = r / diag, acc[0..1] += (r, z)
 // and acc[14..15] += (b, M^-1 b) over the free rows (the reference norm)
-__global__ void __launch_bounds__(256) k_macro_residual(int64_t n, const double* __restrict__ b,
+// (Vector kernels: nf interleaved fields per row group, field of row i is
+// i % nf; the held mask is indexed by i / mdiv: 2 for the per-node mask of the
+// transport pair, 1 for the per-DOF mask of the mechanics.)
+__global__ void __launch_bounds__(256) k_macro_residual(int64_t n, int nf, int mdiv, const double* __restrict__ b,
                                                         const double* __restrict__ y,
                                                         const uint8_t* __restrict__ mask,
                                                         const double* __restrict__ diag, double* __restrict__ r,
                                                         double* __restrict__ z, double* __restrict__ acc) {
     double a[2] = {0, 0}, bb[2] = {0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const bool held = mask[i / 2] != 0;
+        const int f = nf == 2 ? (int)(i & 1) : 0;
+        const bool held = mask[i / mdiv] != 0;
         const double ri = held ? 0.0 : b[i] - y[i];
         const double zi = ri / diag[i];
         r[i] = ri;
         z[i] = zi;
-        a[i & 1] += ri * zi;
-        if (!held) bb[i & 1] += b[i] * b[i] / diag[i];
+        a[f] += ri * zi;
+        if (!held) bb[f] += b[i] * b[i] / diag[i];
     }
     block_add2(a[0], a[1], acc);
     block_add2(bb[0], bb[1], acc + 14);
 }
 
 // acc[2..3] += (p, q) per field
-__global__ void __launch_bounds__(256) k_macro_dot(int64_t n, const double* __restrict__ p,
+__global__ void __launch_bounds__(256) k_macro_dot(int64_t n, int nf, const double* __restrict__ p,
                                                    const double* __restrict__ q, double* __restrict__ acc) {
     double a[2] = {0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        a[i & 1] += p[i] * q[i];
+        a[nf == 2 ? (int)(i & 1) : 0] += p[i] * q[i];
     block_add2(a[0], a[1], acc + 2);
 }
 
@@ -159,7 +173,7 @@ __global__ void k_macro_beta(double* acc, double tol2) {
 }
 
 // x += alpha p, r -= alpha q (held rows stay 0), z = r / diag, acc[0..1] += (r, z)
-__global__ void __launch_bounds__(256) k_macro_update(int64_t n, const uint8_t* __restrict__ mask,
+__global__ void __launch_bounds__(256) k_macro_update(int64_t n, int nf, int mdiv, const uint8_t* __restrict__ mask,
                                                      const double* __restrict__ diag, double* __restrict__ x,
                                                      double* __restrict__ r, double* __restrict__ z,
                                                      const double* __restrict__ p, const double* __restrict__ q,
@@ -167,11 +181,11 @@ __global__ void __launch_bounds__(256) k_macro_update(int64_t n, const uint8_t* 
     const double al[2] = {acc[8], acc[9]};
     double a[2] = {0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int f = (int)(i & 1);
+        const int f = nf == 2 ? (int)(i & 1) : 0;
         double ri = r[i];
         if (al[f] != 0.0) {
             x[i] += al[f] * p[i];
-            ri = mask[i / 2] ? 0.0 : ri - al[f] * q[i];
+            ri = mask[i / mdiv] ? 0.0 : ri - al[f] * q[i];
             r[i] = ri;
         }
         const double zi = ri / diag[i];
@@ -182,11 +196,11 @@ __global__ void __launch_bounds__(256) k_macro_update(int64_t n, const uint8_t* 
 }
 
 // p = z + beta p for active fields; q = 0
-__global__ void __launch_bounds__(256) k_macro_pupdate(int64_t n, const double* __restrict__ z,
+__global__ void __launch_bounds__(256) k_macro_pupdate(int64_t n, int nf, const double* __restrict__ z,
                                                       double* __restrict__ p, double* __restrict__ q,
                                                       const double* __restrict__ acc, int first) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int f = (int)(i & 1);
+        const int f = nf == 2 ? (int)(i & 1) : 0;
         if (first)
             p[i] = z[i];
         else if (acc[12 + f] != 0.0)
@@ -274,6 +288,174 @@ __global__ void k_macro_gauss(int64_t nt, const int32_t* __restrict__ tets, cons
     }
 }
 
+// ---------------------------------------------------------- macro mechanics
+// Voigt order [xx, yy, zz, xy, yz, zx] with engineering shear, as C_bar of the
+// RVE path.  On a linear tetrahedron the strain is constant, so the 4-point
+// Gauss rule of K = sum_g |T| / 4 B^T C_g B collapses to |T| B^T (mean_g C_g) B.
+
+// Voigt strain from the displacement gradient H_ij = du_i / dx_j
+__device__ __forceinline__ void mech_strain(const double* g, const double* ua, double eps[6]) {
+    double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) H[i][j] += ua[a * 3 + i] * g[a * 3 + j];
+    eps[0] = H[0][0];
+    eps[1] = H[1][1];
+    eps[2] = H[2][2];
+    eps[3] = H[0][1] + H[1][0];
+    eps[4] = H[1][2] + H[2][1];
+    eps[5] = H[2][0] + H[0][2];
+}
+
+// B^T sigma for node a with gradient (gx, gy, gz)
+__device__ __forceinline__ void mech_bt(double gx, double gy, double gz, const double* sg, double f[3]) {
+    f[0] = gx * sg[0] + gy * sg[3] + gz * sg[5];
+    f[1] = gy * sg[1] + gx * sg[3] + gz * sg[4];
+    f[2] = gz * sg[2] + gy * sg[4] + gx * sg[5];
+}
+
+// Per tetrahedron: cm = mean over its Gauss points of the symmetric part of C_g,
+// and the Jacobi diagonal |T| b^T cm b of each of its 12 DOFs (b the DOF's
+// column of B), added atomically into diag.
+__global__ void k_mech_material(int64_t nt, const int32_t* __restrict__ tets, const double* __restrict__ geo,
+                                const double* __restrict__ Cgp, double* __restrict__ cm,
+                                double* __restrict__ diag) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        double C[36];
+#pragma unroll
+        for (int k = 0; k < 36; ++k) C[k] = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const double* Cq = Cgp + (e * 4 + q) * 36;
+#pragma unroll
+            for (int J = 0; J < 6; ++J)
+#pragma unroll
+                for (int K = 0; K < 6; ++K) C[J * 6 + K] += 0.125 * (Cq[J * 6 + K] + Cq[K * 6 + J]);
+        }
+#pragma unroll
+        for (int k = 0; k < 36; ++k) cm[e * 36 + k] = C[k];
+        const double vol = geo[e * 13];
+        const double* g = geo + e * 13 + 1;
+        for (int a = 0; a < 4; ++a) {
+            const double gx = g[a * 3], gy = g[a * 3 + 1], gz = g[a * 3 + 2];
+            const int v = tets[e * 4 + a];
+            for (int i = 0; i < 3; ++i) {
+                double b[6] = {0, 0, 0, 0, 0, 0};
+                if (i == 0) { b[0] = gx; b[3] = gy; b[5] = gz; }
+                if (i == 1) { b[1] = gy; b[3] = gx; b[4] = gz; }
+                if (i == 2) { b[2] = gz; b[4] = gy; b[5] = gx; }
+                double d = 0.0;
+#pragma unroll
+                for (int J = 0; J < 6; ++J)
+#pragma unroll
+                    for (int K = 0; K < 6; ++K) d += b[J] * C[J * 6 + K] * b[K];
+                atomicAdd(diag + (int64_t)v * 3 + i, vol * d);
+            }
+        }
+    }
+}
+
+// y += K x: per tetrahedron eps = B x_T, sigma = cm eps, y_a += |T| B_a^T sigma
+__global__ void k_mech_apply(int64_t nt, const int32_t* __restrict__ tets, const double* __restrict__ geo,
+                             const double* __restrict__ cm, const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        int v[4];
+        double ua[12];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            v[a] = tets[e * 4 + a];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ua[a * 3 + i] = x[(int64_t)v[a] * 3 + i];
+        }
+        const double vol = geo[e * 13];
+        const double* g = geo + e * 13 + 1;
+        double eps[6], sg[6];
+        mech_strain(g, ua, eps);
+        const double* C = cm + e * 36;
+#pragma unroll
+        for (int J = 0; J < 6; ++J) {
+            double t = 0.0;
+#pragma unroll
+            for (int K = 0; K < 6; ++K) t += C[J * 6 + K] * eps[K];
+            sg[J] = vol * t;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            double f[3];
+            mech_bt(g[a * 3], g[a * 3 + 1], g[a * 3 + 2], sg, f);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) atomicAdd(y + (int64_t)v[a] * 3 + i, f[i]);
+        }
+    }
+}
+
+// Consistent nodal forces of a uniform traction t on every tetrahedron face
+// whose three vertices are all marked: t |F| / 3 on each, with the face area
+// |F_a| = 3 |T| |grad lambda_a| of the face opposite vertex a.
+__global__ void k_mech_traction(int64_t nt, const int32_t* __restrict__ tets, const double* __restrict__ geo,
+                                const uint8_t* __restrict__ face, double tx, double ty, double tz,
+                                double* __restrict__ f) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        int v[4];
+        bool on[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            v[a] = tets[e * 4 + a];
+            on[a] = face[v[a]] != 0;
+        }
+        const double vol = geo[e * 13];
+        const double* g = geo + e * 13 + 1;
+        for (int a = 0; a < 4; ++a) {
+            bool all = true;
+            for (int k = 0; k < 4; ++k)
+                if (k != a) all = all && on[k];
+            if (!all) continue;
+            const double gx = g[a * 3], gy = g[a * 3 + 1], gz = g[a * 3 + 2];
+            const double third = vol * sqrt(gx * gx + gy * gy + gz * gz);   // |F_a| / 3
+            for (int k = 0; k < 4; ++k)
+                if (k != a) {
+                    atomicAdd(f + (int64_t)v[k] * 3, tx * third);
+                    atomicAdd(f + (int64_t)v[k] * 3 + 1, ty * third);
+                    atomicAdd(f + (int64_t)v[k] * 3 + 2, tz * third);
+                }
+        }
+    }
+}
+
+// held DOFs take their prescribed values
+__global__ void k_mech_hold(int64_t n, const uint8_t* __restrict__ fix, const double* __restrict__ val,
+                            double* __restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (fix[i]) x[i] = val[i];
+}
+
+// sigma_g = sym(C_g) B u_T at every Gauss point [nt*4][6]
+__global__ void k_mech_stress(int64_t nt, const int32_t* __restrict__ tets, const double* __restrict__ geo,
+                              const double* __restrict__ Cgp, const double* __restrict__ u,
+                              double* __restrict__ sig) {
+    const int64_t n = nt * 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i / 4;
+        double ua[12];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) ua[a * 3 + k] = u[(int64_t)tets[e * 4 + a] * 3 + k];
+        double eps[6];
+        mech_strain(geo + e * 13 + 1, ua, eps);
+        const double* C = Cgp + i * 36;
+#pragma unroll
+        for (int J = 0; J < 6; ++J) {
+            double t = 0.0;
+#pragma unroll
+            for (int K = 0; K < 6; ++K) t += 0.5 * (C[J * 6 + K] + C[K * 6 + J]) * eps[K];
+            sig[i * 6 + J] = t;
+        }
+    }
+}
+
 unsigned grid_for(int64_t n) {
     int64_t b = (n + 255) / 256;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 4));
@@ -323,6 +505,69 @@ int build_diag(rve_macro m, double dt_s) {
     }
     RVE_TRY(upload(m->diag, d.data(), d.size(), m->ctx->stream));
     m->diag_dt = dt_s;
+    return RVE_OK;
+}
+
+// Jacobi PCG on the macro mesh over nf (1 or 2) interleaved fields of n rows in
+// all.  On entry x holds the start (held rows at their values) and b the
+// right-hand side; apply(in, out) adds the operator times in to out.  A field
+// has converged when (r, M^-1 r) <= rtol^2 max((b, M^-1 b), (r0, M^-1 r0)) over
+// the free rows.  Returns the iterations and final relative residuals per field.
+template <class Apply>
+int macro_pcg(rve_macro mm, int64_t n, int nf, int mdiv, const uint8_t* mask, const double* diag, double* x,
+              const double* b, Apply apply, double rtol, int max_iter, int its[2], double rel[2], bool& conv) {
+    cudaStream_t s = mm->ctx->stream;
+    double* r = mm->r.as<double>();
+    double* z = mm->z.as<double>();
+    double* p = mm->p.as<double>();
+    double* q = mm->q.as<double>();
+    double* acc = mm->acc.as<double>();
+    const unsigned gv = grid_for(n);
+    // r = b - A x, z = M^-1 r, (r, z)
+    RVE_CUDA(cudaMemsetAsync(q, 0, n * 8, s));
+    RVE_CUDA(cudaMemsetAsync(acc, 0, 16 * 8, s));
+    apply(x, q);
+    k_macro_residual<<<gv, 256, 0, s>>>(n, nf, mdiv, b, q, mask, diag, r, z, acc);
+    const double tol2 = rtol * rtol;
+    double h[16];
+    RVE_CUDA(cudaMemcpyAsync(h, acc, 16 * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    // convergence is relative to the larger of the right-hand side and the
+    // initial residual (which carries the held values): a field already at
+    // rest (rounding-level residual) needs no iteration
+    for (int f = 0; f < 2; ++f) {
+        h[4 + f] = h[f];                                  // current (r, z)
+        h[6 + f] = std::max(h[14 + f], h[f]);             // reference
+        h[12 + f] = h[f] > tol2 * h[6 + f] ? 1.0 : 0.0;   // active
+    }
+    h[0] = h[1] = h[2] = h[3] = 0.0;
+    RVE_CUDA(cudaMemcpyAsync(acc, h, 16 * 8, cudaMemcpyHostToDevice, s));
+    k_macro_pupdate<<<gv, 256, 0, s>>>(n, nf, z, p, q, acc, 1);
+    int it = 0;
+    its[0] = its[1] = 0;
+    bool active[2] = {h[12] != 0.0, h[13] != 0.0};
+    while ((active[0] || active[1]) && it < max_iter) {
+        const int chunk = std::min(8, max_iter - it);
+        for (int k = 0; k < chunk; ++k) {
+            apply(p, q);
+            k_macro_dot<<<gv, 256, 0, s>>>(n, nf, p, q, acc);
+            k_macro_alpha<<<1, 1, 0, s>>>(acc);
+            k_macro_update<<<gv, 256, 0, s>>>(n, nf, mdiv, mask, diag, x, r, z, p, q, acc);
+            k_macro_beta<<<1, 1, 0, s>>>(acc, tol2);
+            k_macro_pupdate<<<gv, 256, 0, s>>>(n, nf, z, p, q, acc, 0);
+        }
+        RVE_CUDA(cudaGetLastError());
+        it += chunk;
+        RVE_CUDA(cudaMemcpyAsync(h, acc, 16 * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaStreamSynchronize(s));
+        for (int f = 0; f < 2; ++f) {
+            if (active[f]) its[f] = it;
+            active[f] = h[12 + f] != 0.0;
+        }
+    }
+    conv = !(active[0] || active[1]);
+    rel[0] = h[6] > 0 ? std::sqrt(std::max(h[4], 0.0) / h[6]) : 0.0;
+    rel[1] = h[7] > 0 ? std::sqrt(std::max(h[5], 0.0) / h[7]) : 0.0;
     return RVE_OK;
 }
 
@@ -494,14 +739,8 @@ static int transport_solve(rve_macro mm, double dt_s, double rtol, int max_iter,
     const int64_t n = mm->nv * 2;
     double* x = mm->x.as<double>();
     double* b = mm->b.as<double>();
-    double* r = mm->r.as<double>();
-    double* z = mm->z.as<double>();
-    double* p = mm->p.as<double>();
-    double* q = mm->q.as<double>();
-    double* acc = mm->acc.as<double>();
     const uint8_t* mask = mm->mask.as<uint8_t>();
-    const double* diag = mm->diag.as<double>();
-    const unsigned ge = grid_for(mm->nt), gv = grid_for(n);
+    const unsigned ge = grid_for(mm->nt);
     MacroParams prm;
     std::memcpy(prm.KT, mm->KT, sizeof(prm.KT));
     std::memcpy(prm.Dc, mm->Dc, sizeof(prm.Dc));
@@ -514,52 +753,10 @@ static int transport_solve(rve_macro mm, double dt_s, double rtol, int max_iter,
     RVE_CUDA(cudaMemsetAsync(b, 0, n * 8, s));
     k_macro_apply<<<ge, 256, 0, s>>>(mm->nt, mm->tets.as<int32_t>(), mm->geo.as<double>(), x, b, mass);
     k_macro_hold<<<grid_for(mm->nv), 256, 0, s>>>(mm->nv, mask, mm->hold.as<double>(), x);
-    // r = b - A x, z = M^-1 r, (r, z)
-    RVE_CUDA(cudaMemsetAsync(q, 0, n * 8, s));
-    RVE_CUDA(cudaMemsetAsync(acc, 0, 16 * 8, s));
-    k_macro_apply<<<ge, 256, 0, s>>>(mm->nt, mm->tets.as<int32_t>(), mm->geo.as<double>(), x, q, prm);
-    k_macro_residual<<<gv, 256, 0, s>>>(n, b, q, mask, diag, r, z, acc);
-    const double tol2 = rtol * rtol;
-    double h[16];
-    RVE_CUDA(cudaMemcpyAsync(h, acc, 16 * 8, cudaMemcpyDeviceToHost, s));
-    RVE_CUDA(cudaStreamSynchronize(s));
-    // convergence is relative to the larger of the right-hand side and the
-    // initial residual (which carries the held face values): a field already at
-    // rest (rounding-level residual) needs no iteration
-    for (int f = 0; f < 2; ++f) {
-        h[4 + f] = h[f];                                  // current (r, z)
-        h[6 + f] = std::max(h[14 + f], h[f]);             // reference
-        h[12 + f] = h[f] > tol2 * h[6 + f] ? 1.0 : 0.0;   // active
-    }
-    h[0] = h[1] = h[2] = h[3] = 0.0;
-    RVE_CUDA(cudaMemcpyAsync(acc, h, 16 * 8, cudaMemcpyHostToDevice, s));
-    k_macro_pupdate<<<gv, 256, 0, s>>>(n, z, p, q, acc, 1);
-    int it = 0;
-    its[0] = its[1] = 0;
-    bool active[2] = {h[12] != 0.0, h[13] != 0.0};
-    while ((active[0] || active[1]) && it < max_iter) {
-        const int chunk = std::min(8, max_iter - it);
-        for (int k = 0; k < chunk; ++k) {
-            k_macro_apply<<<ge, 256, 0, s>>>(mm->nt, mm->tets.as<int32_t>(), mm->geo.as<double>(), p, q, prm);
-            k_macro_dot<<<gv, 256, 0, s>>>(n, p, q, acc);
-            k_macro_alpha<<<1, 1, 0, s>>>(acc);
-            k_macro_update<<<gv, 256, 0, s>>>(n, mask, diag, x, r, z, p, q, acc);
-            k_macro_beta<<<1, 1, 0, s>>>(acc, tol2);
-            k_macro_pupdate<<<gv, 256, 0, s>>>(n, z, p, q, acc, 0);
-        }
-        RVE_CUDA(cudaGetLastError());
-        it += chunk;
-        RVE_CUDA(cudaMemcpyAsync(h, acc, 16 * 8, cudaMemcpyDeviceToHost, s));
-        RVE_CUDA(cudaStreamSynchronize(s));
-        for (int f = 0; f < 2; ++f) {
-            if (active[f]) its[f] = it;
-            active[f] = h[12 + f] != 0.0;
-        }
-    }
-    conv = !(active[0] || active[1]);
-    rel[0] = h[6] > 0 ? std::sqrt(std::max(h[4], 0.0) / h[6]) : 0.0;
-    rel[1] = h[7] > 0 ? std::sqrt(std::max(h[5], 0.0) / h[7]) : 0.0;
-    return RVE_OK;
+    auto apply = [&](const double* in, double* out) {
+        k_macro_apply<<<ge, 256, 0, s>>>(mm->nt, mm->tets.as<int32_t>(), mm->geo.as<double>(), in, out, prm);
+    };
+    return macro_pcg(mm, n, 2, 2, mask, mm->diag.as<double>(), x, b, apply, rtol, max_iter, its, rel, conv);
 }
 
 int rve_macro_step(rve_ctx c, rve_macro m, double dt_h, const rve_degradation* deg, double rtol, int max_iter,
@@ -770,6 +967,160 @@ int rve_macro_get(rve_ctx c, rve_macro m, double* T_nodal, double* c_nodal, doub
     double* outs[4] = {T_gp, c_gp, W_gp, t_eq_gp};
     for (int k = 0; k < 4; ++k)
         if (outs[k]) RVE_CUDA(cudaMemcpyAsync(outs[k], m->gp.as<double>() + k * n, n * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    return RVE_OK;
+}
+
+// ---------------------------------------------------------- macro mechanics
+
+int rve_macro_mech_set_bc(rve_ctx c, rve_macro m, const uint8_t* fixed, const double* values) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !fixed) {
+        set_error("rve_macro_mech_set_bc: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    const size_t n = (size_t)m->nv * 3;
+    std::vector<uint8_t> f(n);
+    std::vector<double> v(n, 0.0);
+    for (size_t i = 0; i < n; ++i) {
+        f[i] = fixed[i] ? 1 : 0;
+        if (f[i] && values) {
+            if (!std::isfinite(values[i])) {
+                set_error("rve_macro_mech_set_bc: non-finite prescribed value");
+                return RVE_ERR_INVALID_ARGUMENT;
+            }
+            v[i] = values[i];
+        }
+    }
+    cudaStream_t s = c->stream;
+    RVE_TRY(upload(m->mfix, f.data(), n, s));
+    RVE_TRY(upload(m->mval, v.data(), n, s));
+    if (!m->have_mech_u) {
+        RVE_TRY(m->mu.ensure(n * 8));
+        RVE_CUDA(cudaMemsetAsync(m->mu.p, 0, n * 8, s));
+    }
+    RVE_CUDA(cudaStreamSynchronize(s));
+    m->have_mech_u = true;
+    m->have_mech_bc = true;
+    return RVE_OK;
+}
+
+int rve_macro_mech_set_u(rve_ctx c, rve_macro m, const double* u) {
+    RVE_TRY(check_ctx(c));
+    if (!m) {
+        set_error("rve_macro_mech_set_u: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    const size_t n = (size_t)m->nv * 3;
+    cudaStream_t s = c->stream;
+    if (u) {
+        RVE_TRY(upload(m->mu, u, n, s));
+    } else {
+        RVE_TRY(m->mu.ensure(n * 8));
+        RVE_CUDA(cudaMemsetAsync(m->mu.p, 0, n * 8, s));
+    }
+    RVE_CUDA(cudaStreamSynchronize(s));
+    m->have_mech_u = true;
+    return RVE_OK;
+}
+
+int rve_macro_mech_set_traction(rve_ctx c, rve_macro m, const uint8_t* face_nodes, const double t[3], int add) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !face_nodes || !t || !std::isfinite(t[0]) || !std::isfinite(t[1]) || !std::isfinite(t[2])) {
+        set_error("rve_macro_mech_set_traction: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    const size_t n = (size_t)m->nv * 3;
+    std::vector<uint8_t> mk(face_nodes, face_nodes + m->nv);
+    for (auto& x : mk) x = x ? 1 : 0;
+    cudaStream_t s = c->stream;
+    DevBuf fm;
+    RVE_TRY(upload(fm, mk.data(), mk.size(), s));
+    if (!add || !m->have_mech_load) {
+        RVE_TRY(m->mload.ensure(n * 8));
+        RVE_CUDA(cudaMemsetAsync(m->mload.p, 0, n * 8, s));
+    }
+    k_mech_traction<<<grid_for(m->nt), 256, 0, s>>>(m->nt, m->tets.as<int32_t>(), m->geo.as<double>(),
+                                                    fm.as<uint8_t>(), t[0], t[1], t[2], m->mload.as<double>());
+    RVE_CUDA(cudaGetLastError());
+    RVE_CUDA(cudaStreamSynchronize(s));
+    m->have_mech_load = true;
+    return RVE_OK;
+}
+
+int rve_macro_mech_solve(rve_ctx c, rve_macro m, const double* C_gp, int C_on_device, double rtol, int max_iter,
+                         rve_macro_mech_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !C_gp || !(rtol > 0) || max_iter < 1) {
+        set_error("rve_macro_mech_solve: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (!m->have_mech_bc || !m->have_mech_load) {
+        set_error("rve_macro_mech_solve: set the held DOFs and the traction first");
+        return RVE_ERR_STATE;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = c->stream;
+    const int64_t n = m->nv * 3;
+    const double* Cg = C_gp;
+    if (!C_on_device) {
+        RVE_TRY(upload(m->cgp, C_gp, (size_t)m->nt * 4 * 36, s));
+        Cg = m->cgp.as<double>();
+    }
+    for (DevBuf* bfr : {&m->b, &m->r, &m->z, &m->p, &m->q, &m->mdiag}) RVE_TRY(bfr->ensure((size_t)n * 8));
+    RVE_TRY(m->cm.ensure((size_t)m->nt * 36 * 8));
+    RVE_TRY(m->msig.ensure((size_t)m->nt * 4 * 6 * 8));
+    RVE_CUDA(cudaMemsetAsync(m->mdiag.p, 0, n * 8, s));
+    const unsigned ge = grid_for(m->nt);
+    const int32_t* tets = m->tets.as<int32_t>();
+    const double* geo = m->geo.as<double>();
+    k_mech_material<<<ge, 256, 0, s>>>(m->nt, tets, geo, Cg, m->cm.as<double>(), m->mdiag.as<double>());
+    double* b = m->b.as<double>();
+    double* u = m->mu.as<double>();
+    RVE_CUDA(cudaMemcpyAsync(b, m->mload.p, n * 8, cudaMemcpyDeviceToDevice, s));
+    k_mech_hold<<<grid_for(n), 256, 0, s>>>(n, m->mfix.as<uint8_t>(), m->mval.as<double>(), u);
+    const double* cm = m->cm.as<double>();
+    auto apply = [&](const double* in, double* out) {
+        k_mech_apply<<<ge, 256, 0, s>>>(m->nt, tets, geo, cm, in, out);
+    };
+    int its[2] = {0, 0};
+    double rel[2] = {0, 0};
+    bool conv = false;
+    RVE_TRY(macro_pcg(m, n, 1, 1, m->mfix.as<uint8_t>(), m->mdiag.as<double>(), u, b, apply, rtol, max_iter, its,
+                      rel, conv));
+    k_mech_stress<<<grid_for(m->nt * 4), 256, 0, s>>>(m->nt, tets, geo, Cg, u, m->msig.as<double>());
+    RVE_CUDA(cudaGetLastError());
+    RVE_CUDA(cudaStreamSynchronize(s));
+    m->have_mech_sig = true;
+    if (st) {
+        st->iterations = its[0];
+        st->converged = conv ? 1 : 0;
+        st->rel_residual = rel[0];
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!conv) {
+        set_error("rve_macro_mech_solve: PCG did not reach rtol within max_iter");
+        return RVE_ERR_NOT_CONVERGED;
+    }
+    return RVE_OK;
+}
+
+int rve_macro_mech_get(rve_ctx c, rve_macro m, double* u, double* stress_gp, double* load) {
+    RVE_TRY(check_ctx(c));
+    if (!m) {
+        set_error("rve_macro_mech_get: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if ((u && !m->have_mech_u) || (stress_gp && !m->have_mech_sig) || (load && !m->have_mech_load)) {
+        set_error("rve_macro_mech_get: nothing of that kind has been set or solved yet");
+        return RVE_ERR_STATE;
+    }
+    cudaStream_t s = c->stream;
+    const size_t n = (size_t)m->nv * 3;
+    if (u) RVE_CUDA(cudaMemcpyAsync(u, m->mu.p, n * 8, cudaMemcpyDeviceToHost, s));
+    if (load) RVE_CUDA(cudaMemcpyAsync(load, m->mload.p, n * 8, cudaMemcpyDeviceToHost, s));
+    if (stress_gp)
+        RVE_CUDA(cudaMemcpyAsync(stress_gp, m->msig.p, (size_t)m->nt * 4 * 6 * 8, cudaMemcpyDeviceToHost, s));
     RVE_CUDA(cudaStreamSynchronize(s));
     return RVE_OK;
 }
