@@ -420,7 +420,7 @@ SURROGATE_TAU = 5e-3
 def surrogate_leg(ctx, rve, n_points, rank):
     """Surrogate + fallback against plain batched PCG on the surrogate's RVE class
     (24x24x8, p = 2, periodic): n_points Gauss points (seed 5 + rank) through
-    macro_update_gauss_points_surrogate; the error is judged on a sample solved
+    macro_update_gauss_points_surrogate; the error is measured on a sample solved
     by the plain PCG, and the plain PCG rate on that class is measured beside it."""
     if not os.path.exists(SURROGATE_FILE):
         return {"unavailable": "no trained surrogate weights in the package"}
@@ -604,10 +604,14 @@ def cpu_baseline(budget_s=20.0):
         el = time.perf_counter() - t0
         if el > budget_s or n >= 64:
             break
+    host = os.cpu_count() or 1
     return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} homogenisations (12 load cases each) of the 16x16x6 p=1 class, the cheapest "
                       f"class of the workload, single-threaded FP64 oracle; larger classes are slower, so "
-                      f"this overstates the CPU rate on the full mix"}
+                      f"this overstates the CPU rate on the full mix",
+            "ideal_parallel_bound": {"value": n / el * host, "unit": UNIT, "cores": host,
+                                     "note": "the single-thread rate times the host's cores: an upper "
+                                             "bound for independent points, not measured"}}
 
 
 def run_reference(args, world, rank):

@@ -221,7 +221,9 @@ int macro_update_gauss_points_dev(rve_ctx ctx, const rve_mesh* meshes, int n_mes
  * Solves the n sample states (host arrays, all on mesh m) once untimed, then
  * once per candidate batch size (candidates: n_cand sizes, or NULL / 0 for
  * {8, 16, 32, 64, 128, 256}), times each pass on the host clock, and keeps the
- * fastest: later calls with options.batch == 0 solve this mesh in batches of
+ * smallest candidate within 3 % of the fastest (a call runs several meshes at
+ * once, which fill the GPU between them; the margin also absorbs timing
+ * noise): later calls with options.batch == 0 solve this mesh in batches of
  * *best.  rates (optional, n_cand or 6 entries) receives each candidate's
  * homogenisations per second (0 for one that failed).  The sample should
  * follow the distribution of the states the mesh will see: the warm starts

@@ -359,8 +359,15 @@ template void launch_operator<double>(int, int, bool, const ElemView<double>&, c
 
 // list[0 .. n) = the columns with active != 0 in ascending order: each warp ballots
 // 32 flags, the warp counts are scanned in shared memory, lanes write in order.
+// With CTL it is also the loop control of the device-side PCG loop (the body of a
+// conditional WHILE graph node): it counts the iteration and keeps the loop going
+// while some column is active and fewer than max_iter iterations have run; one
+// thread sets the condition, whose value the node reads when the body ends.
+template <bool CTL>
 __global__ void __launch_bounds__(256) k_compact_active(const int32_t* __restrict__ active, int ncols,
-                                                        int32_t* __restrict__ list, int32_t* __restrict__ n_list) {
+                                                        int32_t* __restrict__ list, int32_t* __restrict__ n_list,
+                                                        cudaGraphConditionalHandle h, int32_t* __restrict__ counter,
+                                                        int max_iter) {
     __shared__ int counts[8];
     __shared__ int base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -380,11 +387,23 @@ __global__ void __launch_bounds__(256) k_compact_active(const int32_t* __restric
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) base += counts[w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *n_list = base;
+    if (threadIdx.x == 0) {
+        *n_list = base;
+        if constexpr (CTL) {
+            const int n = *counter + 1;
+            *counter = n;
+            cudaGraphSetConditional(h, (base > 0 && n < max_iter) ? 1u : 0u);
+        }
+    }
 }
 
 void launch_compact_active(const int32_t* active, int ncols, int32_t* list, int32_t* n_list, cudaStream_t s) {
-    k_compact_active<<<1, 256, 0, s>>>(active, ncols, list, n_list);
+    k_compact_active<false><<<1, 256, 0, s>>>(active, ncols, list, n_list, 0, nullptr, 0);
+}
+
+void launch_compact_continue(const int32_t* active, int ncols, int32_t* list, int32_t* n_list,
+                             cudaGraphConditionalHandle h, int32_t* counter, int max_iter, cudaStream_t s) {
+    k_compact_active<true><<<1, 256, 0, s>>>(active, ncols, list, n_list, h, counter, max_iter);
 }
 
 // ------------------------------------- double-float residual (mixed precision)
@@ -1181,28 +1200,6 @@ void launch_constraint_dot(const RowView<T>& rv, const T* r, double* c_partial, 
 template void launch_constraint_dot<float>(const RowView<float>&, const float*, double*, const Launch&);
 template void launch_constraint_dot<double>(const RowView<double>&, const double*, double*,
                                             const Launch&);
-
-// Loop control of the device-side PCG loop (the body of a conditional WHILE graph
-// node): counts the iteration and keeps the loop going while some column is active
-// and fewer than max_iter iterations have run.  One block; exactly one thread sets
-// the condition.
-__global__ void __launch_bounds__(256) k_pcg_continue(cudaGraphConditionalHandle h,
-                                                      const int32_t* __restrict__ active, int ncols,
-                                                      int32_t* __restrict__ counter, int max_iter) {
-    int any = 0;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) any |= active[c] != 0;
-    any = __syncthreads_or(any);
-    if (threadIdx.x == 0) {
-        const int n = *counter + 1;
-        *counter = n;
-        cudaGraphSetConditional(h, (any && n < max_iter) ? 1u : 0u);
-    }
-}
-
-void launch_pcg_continue(cudaGraphConditionalHandle h, const int32_t* active, int ncols, int32_t* counter,
-                         int max_iter, cudaStream_t s) {
-    k_pcg_continue<<<1, 256, 0, s>>>(h, active, ncols, counter, max_iter);
-}
 
 // mu = S^-1 w, rz = (r, M^-1 r) - w . mu, beta, convergence.
 // first: 0 = iteration, 1 = initial residual, 2 = multipliers only (no state change).

@@ -150,9 +150,10 @@ void launch_residual_df(int p, int nc, const ElemView<float>& ev, const float* x
 // x = x_h + x_l (two FP32 words per FP64 entry)
 void launch_split_d2ff(int64_t n, const double* x, float* xh, float* xl, cudaStream_t s);
 
-// device-side PCG loop control: counter += 1; condition = any active && counter < max_iter
-void launch_pcg_continue(cudaGraphConditionalHandle h, const int32_t* active, int ncols, int32_t* counter,
-                         int max_iter, cudaStream_t s);
+// the compaction above, plus the device-side PCG loop control: counter += 1;
+// condition = any active && counter < max_iter
+void launch_compact_continue(const int32_t* active, int ncols, int32_t* list, int32_t* n_list,
+                             cudaGraphConditionalHandle h, int32_t* counter, int max_iter, cudaStream_t s);
 
 // right-hand sides of a batch from the per-phase macro loads y = [2][n_rows][6]
 void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,

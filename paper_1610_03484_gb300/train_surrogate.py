@@ -3,7 +3,7 @@
 Training data: macro Gauss points drawn like the batched workload (T ~ U(20,60)
 C, moisture ~ U(0,1.5) wt%, t = 10^U(0,4) h), each solved by the batched
 mixed-precision PCG (`macro_update_gauss_points`); held-out points from a
-second seed judge the error.  Everything (solves, training, inference) runs
+second seed measure the error.  Everything (solves, training, inference) runs
 on the GPU through librve.
 
     python -m paper_1610_03484_gb300.train_surrogate --n-train 20000 --n-test 2000 \
