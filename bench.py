@@ -536,13 +536,13 @@ def macro_leg(ctx, rve, rank):
                           "s_per_step_all_points": n_gp / (ns / pcg_s)},
             "max_rel_err_C_vs_pcg": err}
         s.free()
-        out["mechanics"] = macro_mech(m, rve, xyz, g["W"].reshape(-1), g["W"].reshape(-1)[pick], Cs, hom.C)
+        out["mechanics"] = macro_mech(m, xyz, g["W"].reshape(-1), g["W"].reshape(-1)[pick], Cs, hom.C)
     m.free()
     mesh.free()
     return out
 
 
-def macro_mech(m, rve, xyz, W_all, W_sample, C_sample, C_nominal):
+def macro_mech(m, xyz, W_all, W_sample, C_sample, C_nominal):
     import time as _t
     import torch
     order = np.argsort(W_sample)

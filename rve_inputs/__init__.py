@@ -226,6 +226,17 @@ def gauss_point_states(G: int, seed: int):
     return T, c, t, size, p
 
 
+def aged_states(G: int, seed: int):
+    """Per Gauss point, the long-exposure part of the state space that a macro
+    structure held hot reaches while moisture diffuses in: T [deg C] ~ U(40,60),
+    moisture [wt%] ~ U(0,1.5), exposure time [h] = 10^U(2,4), seeded."""
+    rng = np.random.default_rng(seed)
+    T = rng.uniform(40.0, 60.0, G)
+    c = rng.uniform(0.0, 1.5, G)
+    t = 10.0 ** rng.uniform(2.0, 4.0, G)
+    return T, c, t
+
+
 def weave_rve(nx: int, ny: int, nz: int):
     """Convenience: Kuhn grid plus plain-weave phases and tangents."""
     xyz, tets = kuhn_grid(nx, ny, nz)
@@ -243,7 +254,7 @@ __all__ = [
     "PHASE_MATRIX", "PHASE_YARN", "kuhn_grid", "mesh_counts", "centroids", "plain_weave",
     "layered", "WeaveGeometry", "MatrixProps", "YarnProps", "DegradationParams",
     "NOMINAL_MATRIX", "NOMINAL_YARN", "NOMINAL_DEGRADATION", "jitter_props", "SIZE_CLASSES",
-    "P_CLASSES", "gauss_point_states", "weave_rve", "random_unit_vectors",
+    "P_CLASSES", "gauss_point_states", "aged_states", "weave_rve", "random_unit_vectors",
 ]
 
 
