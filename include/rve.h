@@ -219,8 +219,9 @@ int macro_update_gauss_points_dev(rve_ctx ctx, const rve_mesh* meshes, int n_mes
 
 /* Batch-size autotuner for one mesh (scheduling; no counterpart in the paper).
  * Solves the n sample states (host arrays, all on mesh m) once untimed, then
- * once per candidate batch size (candidates: n_cand sizes, or NULL / 0 for
- * {8, 16, 32, 64, 128, 256}), times each pass on the host clock, and keeps the
+ * twice per candidate batch size (candidates: n_cand sizes, or NULL / 0 for
+ * {8, 16, 32, 64, 128, 256}), times each pass on the host clock (the faster of
+ * a candidate's two passes counts), and keeps the
  * smallest candidate within 3 % of the fastest (a call runs several meshes at
  * once, which fill the GPU between them; the margin also absorbs timing
  * noise): later calls with options.batch == 0 solve this mesh in batches of
