@@ -375,6 +375,16 @@ int rve_fibre_directions(rve_ctx ctx, const double* xyz, int64_t nv, const int32
                          const int32_t* yarn_of_tet, int n_yarn, const int32_t* yarn_axis, double rtol,
                          double* dir);
 
+/* Checkpoint / resume of the macro time loop: restores a state saved with
+ * rve_macro_get (nodal T and c [nv], Gauss-point 1 - omega [nt * 4], host
+ * arrays) in place of rve_macro_reset, and recomputes the Gauss-point T, c
+ * and t_eq from it (deg NULL = paper constants; 1 - omega is not advanced).
+ * Continuing with rve_macro_step then follows the run that saved the state.
+ * RVE_ERR_INVALID_ARGUMENT for a 1 - omega outside (0, 1] or a non-finite
+ * nodal value. */
+int rve_macro_set_state(rve_ctx ctx, rve_macro m, const double* T_nodal, const double* c_nodal, const double* W_gp,
+                        const rve_degradation* deg);
+
 /* Device pointers to the Gauss-point arrays [nt * 4] (tet-major): temperature,
  * moisture, 1 - omega and t_eq.  Valid until the next step or free; any output
  * may be NULL.  They can be passed straight to macro_update_gauss_points_dev. */

@@ -131,6 +131,7 @@ _SIGS = {
     "rve_macro_set_held": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_macro_solve_steady": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(MacroStats)]),
     "rve_macro_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "rve_macro_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_macro_mech_set_bc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_macro_mech_set_u": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_macro_mech_set_traction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -576,6 +577,18 @@ class Macro:
         _check(self.ctx.lib.rve_macro_step(self.ctx.h, self.h, float(dt_h), C.byref(dg), float(rtol),
                                            int(max_iter), C.byref(st)), "rve_macro_step")
         return st.as_dict()
+
+    def set_state(self, T, c, W, beta=-0.001682, Tg_C=126.0, c_sat_wt=1.5):
+        """Resume from a saved state: nodal T and c [nv], Gauss-point 1 - omega [nt, 4]
+        (as returned by get())."""
+        Tn = np.ascontiguousarray(T, np.float64).reshape(-1)
+        cn = np.ascontiguousarray(c, np.float64).reshape(-1)
+        Wg = np.ascontiguousarray(W, np.float64).reshape(-1)
+        if Tn.size != self.nv or cn.size != self.nv or Wg.size != self.nt * 4:
+            raise ValueError("T and c need nv entries, W nt * 4")
+        dg = Degradation(beta, Tg_C, c_sat_wt, 0)
+        _check(self.ctx.lib.rve_macro_set_state(self.ctx.h, self.h, _ptr(Tn), _ptr(cn), _ptr(Wg), C.byref(dg)),
+               "rve_macro_set_state")
 
     def gauss_dev(self):
         """Device addresses of the Gauss-point T, c, 1 - omega and t_eq arrays [nt * 4]."""

@@ -809,6 +809,45 @@ int rve_macro_step(rve_ctx c, rve_macro m, double dt_h, const rve_degradation* d
     return RVE_OK;
 }
 
+int rve_macro_set_state(rve_ctx c, rve_macro m, const double* T_nodal, const double* c_nodal, const double* W_gp,
+                        const rve_degradation* deg) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !T_nodal || !c_nodal || !W_gp) {
+        set_error("rve_macro_set_state: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    const int64_t n = m->nt * 4;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(W_gp[i] > 0.0 && W_gp[i] <= 1.0)) {
+            set_error("rve_macro_set_state: 1 - omega outside (0, 1]");
+            return RVE_ERR_INVALID_ARGUMENT;
+        }
+    std::vector<double> x((size_t)m->nv * 2);
+    for (int64_t i = 0; i < m->nv; ++i) {
+        if (!std::isfinite(T_nodal[i]) || !std::isfinite(c_nodal[i])) {
+            set_error("rve_macro_set_state: non-finite nodal value");
+            return RVE_ERR_INVALID_ARGUMENT;
+        }
+        x[(size_t)i * 2] = T_nodal[i];
+        x[(size_t)i * 2 + 1] = c_nodal[i];
+    }
+    rve_degradation dg{-0.001682, 126.0, 1.5, 0};
+    if (deg) dg = *deg;
+    cudaStream_t s = c->stream;
+    RVE_TRY(upload(m->x, x.data(), x.size(), s));
+    RVE_TRY(upload(m->W, W_gp, (size_t)n, s));
+    // the Gauss-point T, c and t_eq of the restored state; 1 - omega is not advanced
+    RVE_CUDA(cudaMemsetAsync(m->flags.p, 0, 16, s));
+    k_macro_gauss<<<grid_for(n), 256, 0, s>>>(m->nt, m->tets.as<int32_t>(), m->x.as<double>(), m->W.as<double>(),
+                                              m->gp.as<double>(), 0.0, dg.beta, dg.Tg_C, dg.c_sat_wt, 0,
+                                              m->flags.as<int>(),
+                                              reinterpret_cast<unsigned long long*>(m->flags.as<char>() + 8));
+    RVE_CUDA(cudaGetLastError());
+    RVE_CUDA(cudaStreamSynchronize(s));
+    m->have_state = true;
+    return RVE_OK;
+}
+
 int rve_macro_gauss_dev(rve_ctx c, rve_macro m, const double** T_gp, const double** c_gp, const double** W_gp,
                         const double** t_eq_gp) {
     RVE_TRY(check_ctx(c));
