@@ -222,9 +222,9 @@ int macro_update_gauss_points_dev(rve_ctx ctx, const rve_mesh* meshes, int n_mes
  * twice per candidate batch size (candidates: n_cand sizes, or NULL / 0 for
  * {8, 16, 32, 64, 128, 256}), times each pass on the host clock (the faster of
  * a candidate's two passes counts), and keeps the
- * smallest candidate within 3 % of the fastest (a call runs several meshes at
- * once, which fill the GPU between them; the margin also absorbs timing
- * noise): later calls with options.batch == 0 solve this mesh in batches of
+ * smallest candidate within 6 % of the fastest (a call runs several meshes at
+ * once, which fill the GPU between them, so a larger batch gains less there
+ * than alone): later calls with options.batch == 0 solve this mesh in batches of
  * *best.  rates (optional, n_cand or 6 entries) receives each candidate's
  * homogenisations per second (0 for one that failed).  The sample should
  * follow the distribution of the states the mesh will see: the warm starts

@@ -41,9 +41,9 @@ def test_autotune_batch_picks_a_candidate_and_is_used(rve):
         best, rates = mesh.autotune_batch(Ts, cs, ts, [4, 8])
         assert best in (4, 8)
         assert all(r > 0 for r in rates.values())
-        # the smallest candidate within 3 % of the fastest
-        assert rates[best] >= 0.97 * max(rates.values())
-        assert all(b >= best for b, r in rates.items() if r >= 0.97 * max(rates.values()))
+        # the smallest candidate within 6 % of the fastest
+        assert rates[best] >= 0.94 * max(rates.values())
+        assert all(b >= best for b, r in rates.items() if r >= 0.94 * max(rates.values()))
         Ct, Kt, Dt, st, stats, rc = ctx.macro_update([mesh], T, c, t, np.zeros(20, np.int32))
         assert (st == 0).all()
         mesh.free()
