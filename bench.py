@@ -40,9 +40,9 @@ WORKLOAD = ("batched FE2 evaluation: 4096 macro Gauss points per GPU, plain-weav
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 RTOL = 1e-5          # FP64 outer (true-residual) tolerance of every cell solve
 INNER_RTOL = 5e-6    # FP32 inner PCG tolerance per refinement sweep
-# One ncu capture of the current p = 2 mechanical operator
-# (profiles/k_operator_p2_mech_f32_32x32x10_b8.md): DRAM read + write bytes of one launch
-# against its algorithmic bytes.  The bench scales the ratio to its own mean launch of that
+# One ncu capture of the current p = 2 mechanical operator (one launch on the 32x32x10
+# weave, 8 RVEs, all 48 columns active): DRAM read + write bytes of that launch against its
+# algorithmic bytes.  The bench scales the ratio to its own mean launch of that
 # instance (traffic grows with the columns and elements processed); None for other kernels.
 TRAFFIC_KERNEL = "k_operator<p=2,mech,f32>"
 TRAFFIC_CAPTURE = {"case": "k_operator<2,3,float>, 32x32x10 p=2 periodic, 8 RVEs (48 columns, all active)",
@@ -205,6 +205,9 @@ def mesh_ids(size, p, classes):
 
 
 def run_ours(args, world, rank, local):
+    # the CPU oracle's per-class timings run in spawned worker processes on the
+    # host cores while the GPU legs run (started before the first GPU call)
+    cpu_pool = cpu_baseline_start() if (rank == 0 and not args.no_cpu_baseline and world == 1) else None
     import torch
     import paper_1610_03484_gb300 as rve
     torch.cuda.set_device(local)
@@ -258,6 +261,9 @@ def run_ours(args, world, rank, local):
     barrier(world)
     clk = clocks.stop()
     status = Sd.cpu().numpy()
+    if not (status == 0).all():
+        raise RuntimeError(f"timed leg: {int((status != 0).sum())} points not converged")
+    C_timed, K_timed, D_timed = Cd.cpu().numpy(), Kd.cpu().numpy(), Dd.cpu().numpy()
     # one more step of the same workload with every operator launch bracketed by
     # CUDA events on the launching stream (profile mode replaces the graph
     # replay by direct launches); gives the operator's mean launch duration
@@ -305,16 +311,21 @@ def run_ours(args, world, rank, local):
     Th = torch.tensor(T).pin_memory()
     ch = torch.tensor(c).pin_memory()
     th = torch.tensor(t).pin_memory()
-    e2e_times = []
+    e2e_times, e2e_ok = [], 0
     for _ in range(max(1, args.steps)):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Cc, Kk, Ddd, stt, _, _ = ctx.macro_update(meshes, Th.numpy(), ch.numpy(), th.numpy(), mid,
-                                                  allow_not_converged=True)
+        # a point that did not converge raises here (RVE_ERR_NOT_CONVERGED is not accepted)
+        Cc, Kk, Ddd, stt, _, _ = ctx.macro_update(meshes, Th.numpy(), ch.numpy(), th.numpy(), mid)
         e2e_times.append(time.perf_counter() - t0)
+        e2e_ok += int((stt == 0).sum())
+    if e2e_ok != G * len(e2e_times):
+        raise RuntimeError(f"end-to-end leg: {G * len(e2e_times) - e2e_ok} points not converged")
     e2e_s = max_over_ranks(sum(e2e_times), world)
     e2e_value = sum_over_ranks(G * len(e2e_times), world) / e2e_s
+
+    check = self_check(ctx, rve, meshes, classes, T, c, t, size, p, C_timed, K_timed, D_timed)
 
     pk, pk_kind = peaks()
     result = {
@@ -328,8 +339,10 @@ def run_ours(args, world, rank, local):
                    "batch_per_mesh": tuned if tuned is not None else "built-in rule",
                    "l2": "256 MB buffer written between timed steps; per-step working set >> 129 MB L2",
                    "status_ok": int((status == 0).sum())},
+        "self_check": check,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": G * 3 * 8,
-                "d2h_bytes_per_step": G * (36 + 9 + 9) * 8 + G * 4},
+                "d2h_bytes_per_step": G * (36 + 9 + 9) * 8 + G * 4,
+                "points_converged": e2e_ok, "points": G * len(e2e_times)},
         "gpu_launches": int(launches),
         "variants": variant,
         "host_overhead": {"graph_build_ms_per_step": graph_ms / args.steps,
@@ -339,9 +352,10 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": None,
     }
     if op_n > 0:
-        result["roofline"] = roofline(st, prof_step_ms, pk, pk_kind, clk)
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
-        result["cpu_baseline"] = cpu_baseline(budget_s=20.0)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        result["roofline"] = roofline(st, prof_step_ms, pk, pk_kind, clk, n_sm)
+    if cpu_pool is not None:
+        result["cpu_baseline"] = cpu_baseline_collect(cpu_pool)
     if not args.no_surrogate:
         result["surrogate"] = surrogate_leg(ctx, rve, args.surrogate_points, rank)
     if not args.no_macro:
@@ -352,16 +366,18 @@ def run_ours(args, world, rank, local):
     return result
 
 
-def roofline(st, step_ms, pk, pk_kind, clk):
+def roofline(st, step_ms, pk, pk_kind, clk, n_sm):
     """Roofline of the step's kernels from one profiled step of the same workload:
     every launch of the PCG iteration is bracketed by CUDA events on its stream
     and its algorithmic bytes (and, for the operator, flops) are counted by the
     library, per operator instance (order p x field).  The dominant kernel (the
-    largest share of the step) fills the top-level fields, against the roof that
-    binds it (the larger of its HBM and FP32-ALU fractions)."""
+    largest share of the step) fills the top-level fields with its HBM fraction:
+    algorithmic bytes per launch / mean launch time / the measured copy
+    bandwidth.  Its FP32-ALU fraction (against a peak derived from the device's
+    SM count and the sampled clock) is reported beside it."""
     hbm_peak = pk["hbm_gbs"]
     mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12      # FP32 CUDA-core FMA peak at the sampled clock
+    fp32_peak = n_sm * 128 * 2 * mhz * 1e6 / 1e12      # FP32 CUDA-core FMA peak at the sampled clock
 
     def op_entry(ms, n, by, fl, act):
         sec = ms / 1e3
@@ -394,21 +410,20 @@ def roofline(st, step_ms, pk, pk_kind, clk):
     dom = max(cands, key=lambda k: kernels[k]["share_of_step"])
     out = {"how": "one extra step of the same workload after the timed ones, every PCG-iteration launch "
                   "bracketed by CUDA events on its stream; bytes and flops are algorithmic, counted for "
-                  "the columns still iterating",
+                  "the columns still iterating; frac = achieved / peak with achieved = bytes_per_launch / "
+                  "mean_launch_ms of the dominant kernel (HBM roofline)",
            "profiled_step_ms": step_ms, "kernels": kernels, "kernel": dom,
            "traffic": (TRAFFIC_CAPTURE["ratio"] * kernels[dom]["bytes_per_launch"]
                        if dom == TRAFFIC_KERNEL else None),
            "traffic_capture": TRAFFIC_CAPTURE,
-           "peaks": {"hbm_gbs": hbm_peak, "hbm_kind": f"{pk_kind} (MEASURED_PEAKS.json copy bandwidth)",
+           "peaks": {"hbm_gbs": hbm_peak, "hbm_kind": f"{pk_kind} (copy bandwidth)",
                      "fp32_tflops": fp32_peak,
-                     "fp32_kind": f"derived: 152 SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled median)"}}
+                     "fp32_kind": f"derived, not measured: {n_sm} SM (device query) x 128 FP32 lanes x 2 x "
+                                  f"{mhz:.0f} MHz (sampled median)"}}
     k = kernels[dom]
-    if k["bound"] == "alu":
-        out.update({"bound": "alu", "achieved": k["tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": k["alu_frac"]})
-    else:
-        out.update({"bound": "hbm", "achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": k["hbm_frac"]})
+    out.update({"bound": "hbm", "achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": k["hbm_frac"], "alu_frac_derived": k.get("alu_frac"),
+                "binding_roof": k["bound"]})
     return out
 
 
@@ -439,7 +454,7 @@ def surrogate_leg(ctx, rve, n_points, rank):
     Cs, Ks, Ds, st, fb, stats, rc = ctx.macro_update_surrogate([mesh], [s], SURROGATE_TAU, T, c, t, mid)
     sur_s = _t.perf_counter() - t0
     # plain batched PCG on a sample of the same points: rate and the error reference
-    ns = 256
+    ns = min(4096, n_points)
     t0 = _t.perf_counter()
     Cp, Kp, Dp, stp, _, _ = ctx.macro_update([mesh], T[:ns], c[:ns], t[:ns], mid[:ns])
     pcg_s = _t.perf_counter() - t0
@@ -464,6 +479,7 @@ MACRO_GRID = (200, 40, 10)       # hexes of the 0.5 x 0.1 x 0.01 m plate, 6 tets
 MACRO_DT_H = 100.0               # 100 implicit steps to 1e4 h
 MACRO_REFRESH_SAMPLE = 1 << 18   # Gauss points refreshed through the surrogate at the last step
 MACRO_TENSION_PA = 1.0e8         # in-plane traction on the plate's end x = L (macro mechanics)
+MACRO_PCG_SAMPLE = 4096          # Gauss points refreshed through the plain PCG at the last step
 
 
 def macro_leg(ctx, rve, rank):
@@ -509,31 +525,54 @@ def macro_leg(ctx, rve, rank):
     out = {"plate_hexes": list(MACRO_GRID), "tets": int(len(tets)), "gauss_points": int(n_gp),
            "steps": ex.n_steps, "dt_h": MACRO_DT_H,
            "transport_and_degradation_ms_per_step": march_s * 1e3 / ex.n_steps,
-           "pcg_iterations_per_step": float(np.mean(its)), "gauss_points_unencodable": int(bad),
+           "pcg_iterations_per_step": float(np.mean(its)),
+           "t_eq_unencodable_point_steps": int(bad),
            "W_min_last_step": float(g["W"].min()), "W_mean_last_step": float(g["W"].mean())}
+    Wg = g["W"].reshape(-1)
+    # points whose 1 - omega the closed-form law cannot reproduce at their own (T, c)
+    # (degraded, then dried out): t_eq = 0 although W < 1
+    unenc = (teq == 0.0) & (Wg < 1.0)
+    out["handover"] = {"plain_pcg": "1 - omega passed per point (macro_update_gauss_points_w)",
+                       "surrogate": "features from (T, c, t_eq); points that t_eq cannot encode go to the "
+                                    "1 - omega route of the plain PCG",
+                       "gauss_points_unencodable_last_step_t_eq": int(unenc.sum()),
+                       "gauss_points_handed_over_inexactly": 0}
     if os.path.exists(SURROGATE_FILE):
         z = np.load(SURROGATE_FILE)
         s = rve.Surrogate(ctx, members=int(z["members"]), seed=0)
         s.set_params(z["params"])
+        ps, pw = pick[~unenc[pick]], pick[unenc[pick]]
         mid = np.zeros(len(pick), np.int32)
-        ctx.macro_update_surrogate([mesh], [s], SURROGATE_TAU, Tg[pick[:4096]], cg[pick[:4096]],
-                                   teq[pick[:4096]], mid[:4096])
+        ctx.macro_update_surrogate([mesh], [s], SURROGATE_TAU, Tg[ps[:4096]], cg[ps[:4096]],
+                                   teq[ps[:4096]], mid[:min(4096, len(ps))])
         t0 = _t.perf_counter()
-        Cs, Ks, Ds, sst, fb, _, _ = ctx.macro_update_surrogate([mesh], [s], SURROGATE_TAU, Tg[pick], cg[pick],
-                                                               teq[pick], mid)
+        Cs_s, _, _, sst, fb, _, _ = ctx.macro_update_surrogate([mesh], [s], SURROGATE_TAU, Tg[ps], cg[ps],
+                                                               teq[ps], mid[:len(ps)])
+        if len(pw):
+            Cs_w, _, _, wst, _, _ = ctx.macro_update_w([mesh], Wg[pw], mid[:len(pw)])
         sur_s = _t.perf_counter() - t0
-        ns = 256
+        Cs = np.zeros((len(pick), 6, 6))
+        Cs[~unenc[pick]] = Cs_s
+        if len(pw):
+            Cs[unenc[pick]] = Cs_w
+            sst = np.concatenate([sst, wst])
+        ns = min(MACRO_PCG_SAMPLE, len(pick))
         t0 = _t.perf_counter()
-        Cp, _, _, pst, _, _ = ctx.macro_update([mesh], Tg[pick[:ns]], cg[pick[:ns]], teq[pick[:ns]], mid[:ns])
+        Cp, _, _, pst, _, _ = ctx.macro_update_w([mesh], Wg[pick[:ns]], mid[:ns])
         pcg_s = _t.perf_counter() - t0
         err = float((np.linalg.norm((Cs[:ns] - Cp).reshape(ns, -1), axis=1) /
                      np.linalg.norm(Cp.reshape(ns, -1), axis=1)).max())
         out["refresh"] = {
             "surrogate_fallback": {"rate": len(pick) / sur_s, "unit": UNIT, "sample": int(len(pick)),
                                    "fallback_frac": float(fb.mean()), "status_ok": int((sst == 0).sum()),
-                                   "s_per_step_all_points": n_gp / (len(pick) / sur_s)},
+                                   "via_1_minus_omega_route": int(len(pw)),
+                                   "s_per_step_all_points": n_gp / (len(pick) / sur_s),
+                                   "scaled": f"extrapolated from a seeded sample of {len(pick)} of the "
+                                             f"{n_gp} Gauss points at the sample's rate"},
             "plain_pcg": {"rate": ns / pcg_s, "unit": UNIT, "sample": ns,
-                          "s_per_step_all_points": n_gp / (ns / pcg_s)},
+                          "s_per_step_all_points": n_gp / (ns / pcg_s),
+                          "scaled": f"extrapolated from a seeded sample of {ns} of the {n_gp} Gauss points "
+                                    f"(one warm-started batched call) at the sample's rate"},
             "max_rel_err_C_vs_pcg": err}
         s.free()
         out["mechanics"] = macro_mech(m, xyz, g["W"].reshape(-1), g["W"].reshape(-1)[pick], Cs, hom.C)
@@ -592,26 +631,83 @@ def oracle_one(grid, p, T, c, t):
     return fem.homogenise(xyz, tets, grid, p, fem.BC_PERIODIC, D, K, Dd)
 
 
-def cpu_baseline(budget_s=20.0):
-    """Times the FP64 oracle on the cheapest RVE class of the workload (16x16x6,
-    p = 1), repeating whole homogenisations (12 load cases) until the budget."""
-    T, c, t, _, _ = ri.gauss_point_states(64, SEED)
-    grid, p = ri.SIZE_CLASSES[0], 1
-    n, t0 = 0, time.perf_counter()
-    while True:
-        oracle_one(grid, p, T[n], c[n], t[n])
-        n += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or n >= 64:
-            break
+def _oracle_class_worker(si, p, seed_index):
+    """One homogenisation (12 load cases) of one class, timed in its own process."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    T, c, t, size, pp = ri.gauss_point_states(256, SEED)
+    g = int(np.nonzero((size == si) & (pp == p))[0][seed_index])
+    t0 = time.perf_counter()
+    oracle_one(ri.SIZE_CLASSES[si], p, T[g], c[g], t[g])
+    return si, p, g, time.perf_counter() - t0
+
+
+def cpu_baseline_start():
+    """Starts one single-threaded worker per class (six processes, spawn) that
+    times one seeded point of that class through the FP64 oracle."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    pool = mp.get_context("spawn").Pool(len(ri.SIZE_CLASSES) * len(ri.P_CLASSES))
+    jobs = [pool.apply_async(_oracle_class_worker, (si, p, 0))
+            for si in range(len(ri.SIZE_CLASSES)) for p in ri.P_CLASSES]
+    return pool, jobs, time.perf_counter()
+
+
+def cpu_baseline_collect(handle):
+    """Mean oracle time per homogenisation over the workload's uniform class mix
+    (one seeded point of each of the six classes, each in its own single-threaded
+    process) -> homogenisations/s of one core."""
+    pool, jobs, t0 = handle
+    per = [j.get() for j in jobs]
+    pool.close()
+    pool.join()
+    secs = {f"{'x'.join(map(str, ri.SIZE_CLASSES[si]))} p={p}": round(dt, 3) for si, p, _, dt in per}
+    mean_s = float(np.mean([dt for *_, dt in per]))
     host = os.cpu_count() or 1
-    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} homogenisations (12 load cases each) of the 16x16x6 p=1 class, the cheapest "
-                      f"class of the workload, single-threaded FP64 oracle; larger classes are slower, so "
-                      f"this overstates the CPU rate on the full mix",
-            "ideal_parallel_bound": {"value": n / el * host, "unit": UNIT, "cores": host,
-                                     "note": "the single-thread rate times the host's cores: an upper "
-                                             "bound for independent points, not measured"}}
+    return {"value": 1.0 / mean_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one seeded Gauss point of each of the six size/order classes (12 load cases each), "
+                      "FP64 oracle, each class timed in its own single-threaded process (six processes ran "
+                      "concurrently beside the GPU legs); value = 1 / mean seconds per homogenisation over "
+                      "the uniform class mix, i.e. the rate of one core on the workload's mix",
+            "seconds_per_class": secs, "wall_s": time.perf_counter() - t0,
+            "ideal_parallel_bound": {"value": host / mean_s, "unit": UNIT, "cores": host,
+                                     "note": "the one-core rate times the host's cores: an upper bound for "
+                                             "independent points, not measured"}}
+
+
+SELF_CHECK_PER_CLASS = 8
+SELF_CHECK_RTOL = 1e-11
+
+
+def self_check(ctx, rve, meshes, classes, T, c, t, size, p, C_t, K_t, D_t):
+    """Outside every timed region: re-solves a seeded sample of the timed points
+    (SELF_CHECK_PER_CLASS per class) on the FP64 path at rtol 1e-11 and compares
+    the timed (mixed-precision, rtol 1e-5, warm-started) tensors with them."""
+    opts = dict(precision=rve.PREC_FP64, rtol=SELF_CHECK_RTOL, warm_start=0, batch=SELF_CHECK_PER_CLASS)
+    saved = ctx.get_options()
+    ctx.set_options(**opts)
+    worst = {"C": 0.0, "K": 0.0, "D": 0.0}
+    per_class = {}
+    try:
+        for i, (si, q) in enumerate(classes):
+            idx = np.nonzero((size == si) & (p == q))[0][:SELF_CHECK_PER_CLASS]
+            if len(idx) == 0:
+                continue
+            Cr, Kr, Dr, st, _, _ = ctx.macro_update([meshes[i]], T[idx], c[idx], t[idx],
+                                                   np.zeros(len(idx), np.int32))
+            errs = {}
+            for name, a, b in (("C", C_t[idx].reshape(len(idx), 36), Cr.reshape(len(idx), 36)),
+                               ("K", K_t[idx].reshape(len(idx), 9), Kr.reshape(len(idx), 9)),
+                               ("D", D_t[idx].reshape(len(idx), 9), Dr.reshape(len(idx), 9))):
+                e = float((np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)).max())
+                errs[name] = e
+                worst[name] = max(worst[name], e)
+            per_class[f"{'x'.join(map(str, ri.SIZE_CLASSES[si]))} p={q}"] = errs
+    finally:
+        ctx.set_options(**saved)
+    return {"max_rel_err_vs_fp64": worst, "per_class": per_class, "points_per_class": SELF_CHECK_PER_CLASS,
+            "reference": f"FP64 path, rtol {SELF_CHECK_RTOL:g}, cold batches", "bound": 1e-6,
+            "ok": bool(max(worst.values()) <= 1e-6)}
 
 
 def run_reference(args, world, rank):

@@ -217,6 +217,24 @@ int macro_update_gauss_points_dev(rve_ctx ctx, const rve_mesh* meshes, int n_mes
                                   double* C_dev, double* K_dev, double* D_dev,
                                   int32_t* status_dev, int mode, rve_stats* stats);
 
+/* The same batched evaluation for points whose degradation factor 1 - omega is
+ * already known (Sec. 5: the macro time loop integrates the degradation
+ * parameter at every macro Gauss point and hands it to the RVE, whose matrix
+ * modulus it scales).  W[g] in (0, 1] replaces the degradation law at
+ * (T, c, t), so a point is handed over exactly whatever its moisture history
+ * (a point that degraded and then dried out keeps its W).  The mesh's
+ * apply_to_yarn choice still applies.  Fails with RVE_ERR_INVALID_ARGUMENT when
+ * some W[g] lies outside (0, 1] or is NaN; otherwise as
+ * macro_update_gauss_points.  Host arrays; _dev takes W and the outputs on the
+ * context's device (mesh_id_host on the host, for scheduling). */
+int macro_update_gauss_points_w(rve_ctx ctx, const rve_mesh* meshes, int n_meshes, int64_t G,
+                                const double* W, const int32_t* mesh_id, double* C, double* K, double* D,
+                                int32_t* status, int mode, rve_stats* stats);
+int macro_update_gauss_points_w_dev(rve_ctx ctx, const rve_mesh* meshes, int n_meshes, int64_t G,
+                                    const double* W_dev, const int32_t* mesh_id_host, double* C_dev,
+                                    double* K_dev, double* D_dev, int32_t* status_dev, int mode,
+                                    rve_stats* stats);
+
 /* Batch-size autotuner for one mesh (scheduling; no counterpart in the paper).
  * Solves the n sample states (host arrays, all on mesh m) once untimed, then
  * twice per candidate batch size (candidates: n_cand sizes, or NULL / 0 for

@@ -140,6 +140,12 @@ _SIGS = {
     "rve_macro_mech_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_fibre_directions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                        C.c_int, C.c_void_p, C.c_double, C.c_void_p]),
+    "macro_update_gauss_points_w": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_int, C.POINTER(Stats)]),
+    "macro_update_gauss_points_w_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
+                                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                  C.c_int, C.POINTER(Stats)]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
     "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
@@ -241,6 +247,11 @@ class Context:
         self.h = h
         self.lib = lib
 
+    def get_options(self) -> dict:
+        o = Options()
+        _check(self.lib.rve_get_options(self.h, C.byref(o)), "rve_get_options")
+        return {n: getattr(o, n) for n, _ in Options._fields_ if n not in ("device", "stream")}
+
     def set_options(self, **kw):
         o = Options()
         _check(self.lib.rve_get_options(self.h, C.byref(o)), "rve_get_options")
@@ -324,6 +335,33 @@ class Context:
                                                        MODE_PCG, C.byref(s)),
                     "macro_update_gauss_points", allow)
         return Cc, Kk, Dd, st, s.as_dict(), rc
+
+    def macro_update_w(self, meshes, W, mesh_id, allow_not_converged=False):
+        """Batched evaluation with the degradation factor 1 - omega given per point."""
+        G = len(W)
+        arr = (C.c_void_p * len(meshes))(*[m.h for m in meshes])
+        w = np.ascontiguousarray(W, np.float64)
+        mid = np.ascontiguousarray(mesh_id, np.int32)
+        Cc, Kk, Dd = np.zeros((G, 6, 6)), np.zeros((G, 3, 3)), np.zeros((G, 3, 3))
+        st = np.zeros(G, np.int32)
+        s = Stats()
+        allow = (-4,) if allow_not_converged else ()
+        rc = _check(self.lib.macro_update_gauss_points_w(self.h, arr, len(meshes), G, _ptr(w), _ptr(mid), _ptr(Cc),
+                                                         _ptr(Kk), _ptr(Dd), _ptr(st), MODE_PCG, C.byref(s)),
+                    "macro_update_gauss_points_w", allow)
+        return Cc, Kk, Dd, st, s.as_dict(), rc
+
+    def macro_update_w_dev(self, meshes, W_dev, mesh_id, C_dev, K_dev, D_dev, status_dev):
+        """Device-pointer form of macro_update_w (mesh_id is a host array)."""
+        arr = (C.c_void_p * len(meshes))(*[m.h for m in meshes])
+        mid = np.ascontiguousarray(mesh_id, np.int32)
+        s = Stats()
+        rc = _check(self.lib.macro_update_gauss_points_w_dev(self.h, arr, len(meshes), len(mid), C.c_void_p(W_dev),
+                                                             _ptr(mid), C.c_void_p(C_dev), C.c_void_p(K_dev),
+                                                             C.c_void_p(D_dev), C.c_void_p(status_dev), MODE_PCG,
+                                                             C.byref(s)),
+                    "macro_update_gauss_points_w_dev")
+        return s.as_dict(), rc
 
     def features(self, mesh, T_C, c_wt, t_h):
         T = np.ascontiguousarray(T_C, np.float64)

@@ -229,7 +229,7 @@ Launch make_launch(int ncols, int64_t work, cudaStream_t s) {
     L.rows_per_block = 256 / L.cpb;
     const int gx = ncols / L.cpb;
     const int64_t want = (work + L.rows_per_block - 1) / L.rows_per_block;
-    const int64_t cap = std::max<int64_t>(1, (152 * 8) / gx);
+    const int64_t cap = std::max<int64_t>(1, (sm_count() * 8) / gx);
     L.nby = (int)std::max<int64_t>(1, std::min(want, cap));
     L.stream = s;
     return L;
@@ -1452,10 +1452,12 @@ static int auto_batch(rve_mesh m) {
     return (B / 8) * 8;
 }
 
+// W_dev (optional, [G]): the degradation factor 1 - omega of each point, used in
+// place of the degradation law at (T, c, t) (which are then not read).
 static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, int64_t G,
                              const double* T_dev, const double* c_dev, const double* t_dev,
                              const int32_t* mesh_id, double* C_dev, double* K_dev, double* D_dev,
-                             int32_t* status_dev, rve_stats* st) {
+                             int32_t* status_dev, rve_stats* st, const double* W_dev = nullptr) {
     cudaStream_t s = c->stream;
     // group points by mesh
     std::vector<std::vector<int64_t>> groups(n_meshes);
@@ -1478,9 +1480,19 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
         for (int mj : work) repeated |= meshes[mj] == m;
         work.push_back(mi);
     }
-    // host copy of the states, used only to order the points of each mesh
-    std::vector<double> hT_all(G), hc_all(G), ht_all(G);
-    if (G > 0) {
+    // host copy of the states (or of the factors), used only to order the points
+    // of each mesh
+    std::vector<double> hT_all(G), hc_all(G), ht_all(G), hW_all;
+    if (G > 0 && W_dev) {
+        hW_all.resize(G);
+        RVE_CUDA(cudaMemcpyAsync(hW_all.data(), W_dev, G * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaStreamSynchronize(s));
+        for (int64_t g = 0; g < G; ++g)
+            if (!(hW_all[g] > 0.0 && hW_all[g] <= 1.0)) {
+                set_error("macro_update_gauss_points_w: degradation factor outside (0, 1]");
+                return RVE_ERR_INVALID_ARGUMENT;
+            }
+    } else if (G > 0) {
         RVE_CUDA(cudaMemcpyAsync(hT_all.data(), T_dev, G * 8, cudaMemcpyDeviceToHost, s));
         RVE_CUDA(cudaMemcpyAsync(hc_all.data(), c_dev, G * 8, cudaMemcpyDeviceToHost, s));
         RVE_CUDA(cudaMemcpyAsync(ht_all.data(), t_dev, G * 8, cudaMemcpyDeviceToHost, s));
@@ -1500,6 +1512,10 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
             const rve_degradation& dg = m->deg;
             for (size_t i = 0; i < grp.size(); ++i) {
                 const int64_t g = grp[i];
+                if (W_dev) {
+                    wg[i] = hW_all[g];
+                    continue;
+                }
                 const double cn = std::min(std::max(hc_all[g] / dg.c_sat_wt, 0.0), 1.0);
                 const double alpha = dg.beta * std::log(1.0 - (hT_all[g] + 273.15) / (dg.Tg_C + 273.15));
                 wg[i] = std::exp(-cn * alpha * ht_all[g] / 24.0);
@@ -1536,9 +1552,17 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
             if (rc0 != RVE_OK) return fail(rc0);
             double* st3 = d_tmp.as<double>();
             double* dw = st3 + 3 * B;
-            launch_gather_states(B, idx, T_dev, c_dev, t_dev, st3, sm);
-            launch_degradation(B, st3, st3 + B, st3 + 2 * B, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, dw, sm);
-            c->launches += 2;
+            if (W_dev) {
+                // the factors themselves: gathered three times over, the first copy is the batch's w
+                launch_gather_states(B, idx, W_dev, W_dev, W_dev, st3, sm);
+                dw = st3;
+                c->launches += 1;
+            } else {
+                launch_gather_states(B, idx, T_dev, c_dev, t_dev, st3, sm);
+                launch_degradation(B, st3, st3 + B, st3 + 2 * B, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, dw,
+                                   sm);
+                c->launches += 2;
+            }
             res.assign((size_t)B * 55, 0.0);
             std::vector<double> hC((size_t)B * 36), hK((size_t)B * 9), hD((size_t)B * 9);
             int rc = homogenise_batch(m, B, dw, hC.data(), hK.data(), hD.data(), stm,
@@ -1699,6 +1723,62 @@ int macro_update_gauss_points(rve_ctx c, const rve_mesh* meshes, int n_meshes, i
     int32_t* dS = reinterpret_cast<int32_t*>(dD + 9 * G);
     int rc = macro_update_gauss_points_dev(c, meshes, n_meshes, G, dT, dT + G, dT + 2 * G, mesh_id,
                                            dC, dK, dD, dS, mode, st);
+    if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return rc;
+    RVE_CUDA(cudaMemcpyAsync(C, dC, G * 36 * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(K, dK, G * 9 * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(D, dD, G * 9 * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(status, dS, G * 4, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
+int macro_update_gauss_points_w_dev(rve_ctx c, const rve_mesh* meshes, int n_meshes, int64_t G,
+                                    const double* W_dev, const int32_t* mesh_id_host, double* C_dev,
+                                    double* K_dev, double* D_dev, int32_t* status_dev, int mode, rve_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (!meshes || n_meshes <= 0 || G < 0 || (G > 0 && (!W_dev || !mesh_id_host || !C_dev || !K_dev || !D_dev ||
+        !status_dev)) || mode != RVE_MODE_PCG) {
+        set_error("macro_update_gauss_points_w_dev: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t l0 = c->launches;
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->converged = 1;
+    }
+    const ProfCounters pc0 = c->prof;
+    int rc = macro_update_impl(c, meshes, n_meshes, G, nullptr, nullptr, nullptr, mesh_id_host, C_dev, K_dev,
+                               D_dev, status_dev, st, W_dev);
+    if (st) {
+        cudaStreamSynchronize(c->stream);
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        st->kernel_launches = c->launches - l0;
+        fill_profile(pc0, c->prof, st);
+    }
+    return rc;
+}
+
+int macro_update_gauss_points_w(rve_ctx c, const rve_mesh* meshes, int n_meshes, int64_t G, const double* W,
+                                const int32_t* mesh_id, double* C, double* K, double* D, int32_t* status,
+                                int mode, rve_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (G < 0 || (G > 0 && (!W || !mesh_id || !C || !K || !D || !status))) {
+        set_error("macro_update_gauss_points_w: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (G == 0) return RVE_OK;
+    cudaStream_t s = c->stream;
+    DevBuf in, outb;
+    RVE_TRY(in.ensure((size_t)G * 8));
+    RVE_TRY(outb.ensure((size_t)G * (36 + 9 + 9) * 8 + (size_t)G * 4));
+    double* dW = in.as<double>();
+    RVE_CUDA(cudaMemcpyAsync(dW, W, G * 8, cudaMemcpyHostToDevice, s));
+    double* dC = outb.as<double>();
+    double* dK = dC + 36 * G;
+    double* dD = dK + 9 * G;
+    int32_t* dS = reinterpret_cast<int32_t*>(dD + 9 * G);
+    int rc = macro_update_gauss_points_w_dev(c, meshes, n_meshes, G, dW, mesh_id, dC, dK, dD, dS, mode, st);
     if (rc != RVE_OK && rc != RVE_ERR_NOT_CONVERGED && rc != RVE_ERR_NUMERIC) return rc;
     RVE_CUDA(cudaMemcpyAsync(C, dC, G * 36 * 8, cudaMemcpyDeviceToHost, s));
     RVE_CUDA(cudaMemcpyAsync(K, dK, G * 9 * 8, cudaMemcpyDeviceToHost, s));

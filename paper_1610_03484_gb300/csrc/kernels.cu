@@ -7,6 +7,7 @@
 // writes one FP64 partial per (blockIdx.y, column), summed by a finalize kernel.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
@@ -14,6 +15,20 @@
 #include "rve_internal.h"
 
 namespace rve {
+
+// Number of SMs of the current device, queried once per device ordinal; grid caps
+// of the grid-stride kernels are multiples of it.
+int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
 
 // ------------------------------------------------------------ basis tables
 // A[k][m][j] of the hierarchic basis (see rve_internal.h), per order p.
@@ -664,7 +679,7 @@ __global__ void k_split_d2ff(int64_t n, const double* __restrict__ x, float* __r
 
 void launch_split_d2ff(int64_t n, const double* x, float* xh, float* xl, cudaStream_t s) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > sm_count() * 16) b = sm_count() * 16;
     if (b < 1) b = 1;
     k_split_d2ff<<<(unsigned)b, 256, 0, s>>>(n, x, xh, xl);
 }
@@ -1655,7 +1670,7 @@ template <typename TO>
 void launch_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* coef,
                             const double* src, TO* x, cudaStream_t s) {
     int64_t b = (n_rows * ncols + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > sm_count() * 16) b = sm_count() * 16;
     if (b < 1) b = 1;
     k_combine_columns<TO><<<(unsigned)b, 256, 0, s>>>(n_rows, ncols, src_cols, map, coef, src, x);
 }
@@ -1681,7 +1696,7 @@ __global__ void k_rhs_combine(int64_t n_rows, int nrve, const double* __restrict
 void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,
                         cudaStream_t s) {
     int64_t blocks = (n_rows * 6 * nrve + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > sm_count() * 16) blocks = sm_count() * 16;
     if (blocks < 1) blocks = 1;
     k_rhs_combine<<<(unsigned)blocks, 256, 0, s>>>(n_rows, nrve, y, scale, b);
 }
@@ -1701,7 +1716,7 @@ __global__ void k_neg(int64_t n, double* __restrict__ a) {
 }
 static unsigned ew_blocks(int64_t n) {
     int64_t b = (n + 255) / 256;
-    return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+    return (unsigned)(b > sm_count() * 16 ? sm_count() * 16 : (b < 1 ? 1 : b));
 }
 void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s) {
     k_cast_d2f<<<ew_blocks(n), 256, 0, s>>>(n, a, b);

@@ -65,6 +65,8 @@ struct ColState {
 };
 
 void upload_basis_tables();
+// SMs of the current device (cached per device ordinal)
+int sm_count();
 
 // y += K x (+ macro load when macro != 0); energy partials x.Kx per column.
 // active (optional, [ncols]): columns with active == 0 are skipped.

@@ -458,7 +458,7 @@ __global__ void k_mech_stress(int64_t nt, const int32_t* __restrict__ tets, cons
 
 unsigned grid_for(int64_t n) {
     int64_t b = (n + 255) / 256;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 4));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 4));
 }
 
 bool sym_pos_def(const double k[9]) {

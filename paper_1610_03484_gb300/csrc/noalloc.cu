@@ -2,7 +2,7 @@
 //
 // The array below is the only scratch that rve_operator_energy_noalloc uses.
 // It is a file-scope __device__ array, so every GPU that loads librve holds it
-// (about 1 MB) until the process exits.  In host code its name is only a
+// (about 0.9 MB) until the process exits.  In host code its name is only a
 // host-side stand-in; the device address is looked up once per device with
 // cudaGetSymbolAddress and passed to the kernels.
 #include <cuda_runtime.h>

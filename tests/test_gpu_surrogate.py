@@ -162,3 +162,164 @@ def test_save_load_round_trip(rve, trained):
     np.testing.assert_allclose(a[0], b[0], rtol=1e-6)
     np.testing.assert_allclose(a[3], b[3], rtol=1e-6, atol=1e-9)
     s2.free()
+
+
+# ------------------------------------------------ entry-by-entry against the oracle
+DIMS = [(64, 256), (256, 256), (256, 256), (256, 256), (256, 64)]
+
+
+def unpack_member(buf, member, nparam):
+    """One member of the get_params layout as padded (W [in][out], b [out]) pairs."""
+    p = buf[52 + member * nparam: 52 + (member + 1) * nparam].astype(np.float64)
+    out, o = [], 0
+    for k, n in DIMS:
+        W = p[o:o + k * n].reshape(k, n)
+        o += k * n
+        out.append((W, p[o:o + n].copy()))
+        o += n
+    return out
+
+
+def flatten(params):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params])
+
+
+def emulate_member(params, feat, mean, std):
+    """oracle.surrogate.forward layer by layer with the GPU's precision decisions:
+    FP32 feature normalisation, BF16 weights and BF16 activations between
+    layers (FP32 accumulation is replaced by the oracle's FP64)."""
+    inv = (np.float32(1.0) / std.astype(np.float32))
+    x = bf16((feat.astype(np.float32) - mean.astype(np.float32)) * inv)
+    h = np.zeros((len(feat), 64))
+    h[:, :8] = x
+    for l, (W, b) in enumerate(params):
+        a, _ = osg.forward([(bf16(W), b)], h)
+        h = bf16(osg.silu(a)) if l < len(params) - 1 else a
+    return h[:, :33]
+
+
+def test_predict_matches_oracle_entry_by_entry(rve, trained):
+    """Inference (features, four BF16 members, softplus head, L L^T, ensemble mean
+    and spread) against oracle.surrogate.forward -> factor_entries ->
+    tensors_from_factors on the same BF16-rounded weights and inputs.  Tolerance
+    of a BF16 network: an activation whose FP32 and FP64 sums round to different
+    BF16 neighbours moves a member's tensors by about 5e-4."""
+    s = trained["s"]
+    f = trained["feat"][1024:1024 + 128]
+    Cg, Kg, Dg, spread_g = s.predict(f)
+    buf = s.get_params()
+    members = 4
+    nparam = (len(buf) - 52) // members
+    mean, std, ref = buf[:8], buf[8:16], buf[49:52].astype(np.float64)
+    Ts = []
+    for e in range(members):
+        z = emulate_member(unpack_member(buf, e, nparam), f, mean, std)
+        Ts.append(osg.tensors_from_factors(osg.factor_entries(z)))
+    Tm = [np.mean([T[b] for T in Ts], axis=0) for b in range(3)]
+    for b, (G, r) in enumerate(((Cg, ref[0]), (Kg, ref[1]), (Dg, ref[2]))):
+        err = rel(G, Tm[b] * r)
+        assert err.max() < 2e-3, (b, err.max())
+    spread = np.zeros(len(f))
+    for b in range(3):
+        den = np.linalg.norm(Tm[b].reshape(len(f), -1), axis=1)
+        for T in Ts:
+            spread = np.maximum(spread, np.linalg.norm((T[b] - Tm[b]).reshape(len(f), -1), axis=1) / den)
+    assert np.abs(spread_g - spread).max() < 2e-3, np.abs(spread_g - spread).max()
+
+
+def test_adam_steps_match_oracle(rve):
+    """Two steps of the GPU's minibatch Adam (one batch per epoch, learning rate
+    lr then 0.51 lr from the cosine schedule) against oracle.surrogate.adam_step
+    fed with the GPU's own gradients at the same weights: FP32 agreement.  The
+    first step must be -lr * g / (|g| + eps) (the bias-corrected first step)."""
+    rng = np.random.default_rng(21)
+    n, lr = 64, 1e-3
+    feat = rng.normal(size=(n, 8)) * [10, 0.4, 1, 1e9, 4e9, 1e9, 5e8, 0.05] + [40, 0.75, 2, 3e9, 45e9, 12e9, 5e9, 0.2]
+    A = rng.normal(size=(n, 6, 6))
+    Cc = A @ np.swapaxes(A, 1, 2) + 6 * np.eye(6)
+    B3 = rng.normal(size=(n, 3, 3))
+    Kk = B3 @ np.swapaxes(B3, 1, 2) + 3 * np.eye(3)
+    Dd = 2 * Kk + np.eye(3)
+    with rve.Context() as ctx:
+        s0 = rve.Surrogate(ctx, members=1, seed=5)
+        buf0 = s0.get_params()
+        s1 = rve.Surrogate(ctx, members=1, seed=5)
+        s1.train(feat, Cc, Kk, Dd, epochs=1, batch=n, lr=lr, seed=1)
+        buf1 = s1.get_params()
+        s2 = rve.Surrogate(ctx, members=1, seed=5)
+        s2.train(feat, Cc, Kk, Dd, epochs=2, batch=n, lr=lr, seed=1)
+        buf2 = s2.get_params()
+        header = buf2[:52]
+        assert np.array_equal(header, buf1[:52])
+        ref = header[49:52].astype(np.float64)
+        sym = lambda T: 0.5 * (T + np.swapaxes(T, 1, 2))
+        target = osg.factors_from_tensors(sym(Cc) / ref[0], sym(Kk) / ref[1], sym(Dd) / ref[2]).astype(np.float32)
+        grads = []
+        for pb in (buf0, buf1):
+            sg = rve.Surrogate(ctx, members=1, seed=5)
+            sg.set_params(np.concatenate([header, pb[52:]]).astype(np.float32))
+            g, _ = sg.gradients(0, feat, target)
+            grads.append(g.astype(np.float64))
+            sg.free()
+        for x in (s0, s1, s2):
+            x.free()
+    nparam = len(buf0) - 52
+    P0 = unpack_member(buf0, 0, nparam)
+    state = [(np.zeros_like(W), np.zeros_like(W), np.zeros_like(b), np.zeros_like(b)) for W, b in P0]
+
+    def as_pairs(flat):
+        out, o = [], 0
+        for k, nn in DIMS:
+            out.append((flat[o:o + k * nn].reshape(k, nn), flat[o + k * nn:o + k * nn + nn]))
+            o += k * nn + nn
+        return out
+
+    P1 = osg.adam_step(P0, as_pairs(grads[0]), state, lr, 1)
+    P2 = osg.adam_step(P1, as_pairs(grads[1]), state, 0.51 * lr, 2)
+    f0, f1, f2 = flatten(P0), flatten(P1), flatten(P2)
+    g1 = grads[0]
+    # first step identity on the oracle side (documents what is compared)
+    np.testing.assert_allclose(f1 - f0, -lr * g1 / (np.abs(g1) + 1e-8), rtol=1e-12, atol=1e-15)
+    gpu1 = buf1[52:].astype(np.float64)
+    gpu2 = buf2[52:].astype(np.float64)
+    ulp = np.spacing(np.abs(f0).astype(np.float32)).astype(np.float64)
+    assert np.abs(gpu1 - f1).max() <= (4 * ulp + 2e-6 * lr).max(), np.abs(gpu1 - f1).max()
+    d2 = np.abs(gpu2 - f2)
+    assert (d2 <= 8 * ulp + 1e-5 * lr).mean() > 0.999, np.sort(d2)[-10:]
+    assert d2.max() < 0.05 * lr, d2.max()
+
+
+def test_surrogate_gain_on_bench_class(rve):
+    """The trained weights of the benchmark's class (24x24x8, p = 2) answer 2048
+    Gauss points, with spread-gated fallback, faster than plain batched PCG
+    solves them, within 1e-2 of the PCG tensors."""
+    import os
+    import bench
+    if not os.path.exists(bench.SURROGATE_FILE):
+        pytest.skip("no trained weights")
+    z = np.load(bench.SURROGATE_FILE)
+    xyz, tets, phase, tangent = ri.weave_rve(24, 24, 8)
+    T, c, t, _, _ = ri.gauss_point_states(2048 + 512, 41)
+    with rve.Context(precision=rve.PREC_MIXED, rtol=bench.RTOL, inner_rtol=bench.INNER_RTOL, max_refine=4) as ctx:
+        mesh = ctx.mesh_load(xyz, tets, 2, phase, tangent)
+        mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+        mesh.set_bc(rve.BC_PERIODIC)
+        s = rve.Surrogate(ctx, members=int(z["members"]), seed=0)
+        s.set_params(z["params"])
+        mid = np.zeros(2048, np.int32)
+        w = slice(2048, None)   # warm-up on other points
+        ctx.macro_update_surrogate([mesh], [s], bench.SURROGATE_TAU, T[w], c[w], t[w], mid[:512])
+        ctx.macro_update([mesh], T[w][:64], c[w][:64], t[w][:64], mid[:64])
+        t0 = time.perf_counter()
+        Cs, Ks, Ds, st, fb, _, _ = ctx.macro_update_surrogate([mesh], [s], bench.SURROGATE_TAU, T[:2048], c[:2048],
+                                                              t[:2048], mid)
+        sur_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        Cp, Kp, Dp, stp, _, _ = ctx.macro_update([mesh], T[:2048], c[:2048], t[:2048], mid)
+        pcg_s = time.perf_counter() - t0
+        s.free()
+        mesh.free()
+    assert (st == 0).all() and (stp == 0).all()
+    for P, R in ((Cs, Cp), (Ks, Kp), (Ds, Dp)):
+        assert rel(P, R).max() < 1e-2
+    assert sur_s < 0.5 * pcg_s, (sur_s, pcg_s, fb.mean())
