@@ -85,6 +85,11 @@ typedef struct rve_options {
                                 those K and D (transport is not degraded, Sec. 5, so they are the
                                 same problems); 0 (default) solves all twelve load cases for
                                 every point */
+    int     operator_kernel; /* MIXED inner solve, mechanics at p = 2 and 3: 0 (default) applies
+                                the operator on the tensor cores (element matrices stored once
+                                per mesh and materials, 3 x TF32 products with FP32 accumulation);
+                                1 uses the matrix-free CUDA-core kernel.  Other cases always use
+                                the matrix-free kernel. */
 } rve_options;
 
 /* Isotropic matrix phase (Sec. 1, Sec. 7). */
@@ -197,6 +202,21 @@ int rve_set_bc(rve_ctx ctx, rve_mesh mesh, int bc);
  * Any output pointer may be NULL; stats may be NULL.  Returns
  * RVE_ERR_NOT_CONVERGED (outputs still written) if rtol was not reached. */
 int rve_homogenise(rve_ctx ctx, rve_mesh mesh, double* C, double* K, double* D, rve_stats* stats);
+
+/* The paper's own route to the homogenised tensors (Sec. 2): after the cell
+ * problems are solved (as rve_homogenise, whose energy-form tensors are written
+ * to C_energy, K_energy, D_energy), the constraint rows C of the boundary
+ * condition are written out (Eqs. eq_RVE_disc_Eqs, eq_mat_C_and_D: one row per
+ * boundary DOF for linear Dirichlet; u_image - u_master per image DOF of the
+ * unfolded mesh for periodic; the uniform-traction rows plus the rigid-mode rows
+ * for Neumann), D = C X with X the nodal interpolant of the unit macro fields,
+ * the Lagrange multipliers lambda recovered from the equilibrium of the total
+ * field, K u + C^T lambda = 0, and sigma_bar = -D^T lambda / V
+ * (Eq. eq_homo_stress) returned as C (6x6, column j = load case j), K and D
+ * (3x3).  They equal the energy-form tensors up to the solver tolerance and
+ * are not symmetrised.  Any output may be NULL.  Errors as rve_homogenise. */
+int rve_homogenise_weak(rve_ctx ctx, rve_mesh mesh, double* C, double* K, double* D, double* C_energy,
+                        double* K_energy, double* D_energy, rve_stats* stats);
 
 /* Batched FE^2 evaluation (Sec. 5): for G macro Gauss points with states
  * (T_C[g], c_wt[g], t_h[g]) and RVE meshes[mesh_id[g]] (each with materials and
@@ -482,6 +502,20 @@ int rve_mesh_get_tensors(rve_ctx ctx, rve_mesh mesh, double* stiffness, double* 
  * ([n_scalar_dofs][ncols]); units of the current materials; FP64. */
 int rve_apply_operator(rve_ctx ctx, rve_mesh mesh, int field, int ncols, const double* x,
                        double* y);
+
+/* The FP32 operator of the mixed-precision inner solve of the mechanics
+ * (Eq. RVE_Eq_var_final, as the PCG applies it): y = sum_e s(col, phase_e) K_e x_e
+ * for the active columns, with s = scale[col][phase] (phase 0 matrix, 1 yarn;
+ * NULL: all ones) and energy[col] = x_col . y_col accumulated element by
+ * element (NULL: not returned).  kernel 0: the tensor-core kernel (p = 2 or 3
+ * only); 1: the matrix-free CUDA-core kernel.  x, y: host [n_scalar_dofs][3]
+ * [ncols] in SI units (x rounded to FP32 on the way in), ncols a positive
+ * multiple of 6; active (NULL: all) [ncols] nonzero for the columns to apply,
+ * the others come back as zero.  Diagnostic entry point: it allocates and
+ * frees its own device buffers.  RVE_ERR_TIMEOUT if a bounded device wait
+ * gave up. */
+int rve_apply_operator_mixed(rve_ctx ctx, rve_mesh mesh, int kernel, int ncols, const double* x,
+                             const double* scale, const int32_t* active, double* y, double* energy);
 
 /* Allocation-free variant of the operator apply, for callers that cannot
  * allocate device memory while they run: for example a host application that

@@ -36,7 +36,7 @@ class Options(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_iter", C.c_int), ("inner_rtol", C.c_double), ("max_refine", C.c_int),
                 ("check_every", C.c_int), ("batch", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("warm_start", C.c_int), ("transport_once", C.c_int)]
+                ("warm_start", C.c_int), ("transport_once", C.c_int), ("operator_kernel", C.c_int)]
 
 
 class MatrixProps(C.Structure):
@@ -146,6 +146,10 @@ _SIGS = {
     "macro_update_gauss_points_w_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
                                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                                   C.c_int, C.POINTER(Stats)]),
+    "rve_apply_operator_mixed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_homogenise_weak": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(Stats)]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
     "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
@@ -522,6 +526,15 @@ class Mesh:
                "rve_autotune_batch")
         return int(best.value), {int(b): float(r) for b, r in zip(cand, rates)}
 
+    def homogenise_weak(self):
+        """(sigma-route tensors C, K, D via the multipliers, energy-form C, K, D)."""
+        out = [np.zeros((6, 6)), np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((6, 6)), np.zeros((3, 3)),
+               np.zeros((3, 3))]
+        s = Stats()
+        _check(self.ctx.lib.rve_homogenise_weak(self.ctx.h, self.h, *[_ptr(a) for a in out], C.byref(s)),
+               "rve_homogenise_weak")
+        return out
+
     def homogenise(self, allow_not_converged=False) -> Result:
         Cc = np.zeros((6, 6))
         Kk = np.zeros((3, 3))
@@ -547,6 +560,19 @@ class Mesh:
         _check(self.ctx.lib.rve_apply_operator(self.ctx.h, self.h, int(field), int(ncols), _ptr(x), _ptr(y)),
                "rve_apply_operator")
         return y
+
+    def apply_operator_mixed(self, x: np.ndarray, kernel: int = 0, scale=None, active=None):
+        """The FP32 mechanics operator of the mixed-precision inner solve: kernel 0
+        tensor cores, 1 CUDA cores.  Returns (y, energy per column)."""
+        x = np.ascontiguousarray(x, np.float64)
+        ncols = x.shape[-1]
+        y = np.zeros_like(x)
+        en = np.zeros(ncols)
+        sc = None if scale is None else np.ascontiguousarray(scale, np.float64)
+        act = None if active is None else np.ascontiguousarray(active, np.int32)
+        _check(self.ctx.lib.rve_apply_operator_mixed(self.ctx.h, self.h, int(kernel), int(ncols), _ptr(x), _ptr(sc),
+                                                     _ptr(act), _ptr(y), _ptr(en)), "rve_apply_operator_mixed")
+        return y, en
 
     def operator_energy_noalloc(self, field: int, ncols: int, x_dev: int, y_dev: int, energy_dev: int):
         """Allocation-free operator apply on caller-owned device buffers (integer

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librve.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "surrogate.cu", "surrogate_api.cu", "macro.cu", "basis.cpp",
+SOURCES = ["kernels.cu", "operator_tc.cu", "api.cu", "noalloc.cu", "surrogate.cu", "surrogate_api.cu", "macro.cu", "basis.cpp",
            "mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -168,6 +168,8 @@ int build_constraints(rve_mesh m, FieldDev& f, const std::vector<double>& geo) {
     std::vector<int32_t> of_row(f.n_rows, -1);
     for (size_t i = 0; i < rows.size(); ++i) of_row[rows[i]] = (int32_t)i;
     f.n_sup = (int64_t)rows.size();
+    f.h_sup_row = rows;
+    f.h_sup_coef = coef;
     RVE_TRY(upload(f.sup_row, rows.data(), rows.size(), s));
     RVE_TRY(upload(f.sup_coef, coef.data(), coef.size(), s));
     RVE_TRY(upload(f.sup_of_row, of_row.data(), of_row.size(), s));
@@ -195,6 +197,7 @@ int build_field_data(rve_mesh m) {
 // Jacobi diagonals per phase (needs materials and the DOF map).
 int build_diagonals(rve_mesh m) {
     cudaStream_t s = m->ctx->stream;
+    m->ke_valid = false;   // the element matrices follow the map and the materials
     for (FieldDev* f : {&m->mech, &m->scal}) {
         const int64_t n = f->n_rows * 2 * f->nfield;
         RVE_TRY(f->diag64.ensure(sizeof(double) * n));
@@ -211,6 +214,22 @@ int build_diagonals(rve_mesh m) {
         m->ctx->launches += 2;
     }
     RVE_CUDA(cudaGetLastError());
+    return RVE_OK;
+}
+
+// Packed FP32 element matrices of the mechanics for the tensor-core operator,
+// formed in FP64 from the element data on first use after a change.
+int ensure_element_matrices(rve_mesh m, cudaStream_t s) {
+    if (m->ke_valid) return RVE_OK;
+    const int p = m->p, ne = n_local(p);
+    RVE_TRY(m->d_ke32.ensure((size_t)m->nt * element_matrix_floats(p) * sizeof(float)));
+    RVE_TRY(m->d_kepairs.ensure((size_t)element_matrix_pairs(p) * sizeof(uint16_t)));
+    RVE_TRY(m->d_keptab.ensure((size_t)9 * ne * ne * sizeof(double)));
+    RVE_CUDA(operator_tc_prepare(p));
+    RVE_CUDA(build_element_matrices(p, m->nt, m->d_geo64.as<double>(), m->d_matm64.as<double>(),
+                                    m->d_ke32.as<float>(), m->d_kepairs.as<uint16_t>(), m->d_keptab.as<double>(), s));
+    m->ctx->launches++;
+    m->ke_valid = true;
     return RVE_OK;
 }
 
@@ -459,6 +478,9 @@ struct Solver {
         // profile mode launches one iteration at a time so that the byte and flop
         // counts follow the set of columns still iterating
         const bool prof = m->ctx->opt.profile != 0;
+        // FP32 inner solve of the mechanics at p = 2, 3: the tensor-core operator
+        const bool use_tc = sizeof(T) == 4 && operator_tc_supported(m->p, f.nc) && m->ctx->opt.operator_kernel != 1;
+        if (use_tc) RVE_TRY(ensure_element_matrices(m, s));
         ColState cs = cs64;
         RVE_CUDA(cudaMemcpyAsync(const_cast<double*>(cs.tol), &tol, sizeof(double), cudaMemcpyHostToDevice, s));
         RowView<T> rvw = rv<T>(scale);
@@ -495,10 +517,24 @@ struct Solver {
         // in the graph body the compaction also runs the loop control
         bool loop_ctl = false;
         cudaGraphConditionalHandle loop_handle = 0;
+        cudaError_t tc_err = cudaSuccess;
         auto iteration = [&](const Launch& Lx) {
             evr(0, Lx.stream);
-            launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active, cs.list,
-                               cs.n_list);
+            if constexpr (sizeof(T) == 4) {
+                if (use_tc) {
+                    const cudaError_t e = launch_operator_tc(
+                        m->p, m->nt, m->d_edofs.as<int32_t>(), m->d_ke32.as<float>(), m->d_kepairs.as<uint16_t>(),
+                        m->d_phase.as<uint8_t>(), evw.scale, p, q, m->epart.as<double>(), cs.active, ncols, cs.list,
+                        cs.n_list, Lx.nby, cs.flags, Lx.stream);
+                    if (e != cudaSuccess) tc_err = e;
+                } else {
+                    launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active, cs.list,
+                                       cs.n_list);
+                }
+            } else {
+                launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active, cs.list,
+                                   cs.n_list);
+            }
             evr(1, Lx.stream);
             launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
             evr(2, Lx.stream);
@@ -523,9 +559,9 @@ struct Solver {
             // reused while every captured parameter is unchanged (the tolerance
             // lives in device memory).
             struct Key {
-                int ncols, cpb, rows, nby, p, nc, m, max_iter;
+                int ncols, cpb, rows, nby, p, nc, m, max_iter, tc;
                 int64_t n_rows, n_sup, nt;
-                const void* ptr[18];
+                const void* ptr[19];
             } key;
             std::memset(&key, 0, sizeof(key));
             key.ncols = L.ncols;
@@ -539,9 +575,10 @@ struct Solver {
             key.n_rows = rvw.n_rows;
             key.n_sup = rvw.n_sup;
             key.nt = evw.nt;
-            const void* ptrs[18] = {x, r, p, q, m->epart.p, m->rzp.p, m->cpart.p, cs.rz, rvw.scale, rvw.diag,
+            key.tc = use_tc ? 1 : 0;
+            const void* ptrs[19] = {x, r, p, q, m->epart.p, m->rzp.p, m->cpart.p, cs.rz, rvw.scale, rvw.diag,
                                     rvw.mask, rvw.sup_row, rvw.sup_coef, rvw.sup_of_row, evw.edofs, evw.geo,
-                                    evw.mat, evw.phase};
+                                    evw.mat, evw.phase, use_tc ? m->d_ke32.p : nullptr};
             std::memcpy(key.ptr, ptrs, sizeof(ptrs));
             auto& gc = m->graph_cache[fid][sizeof(T) == 4 ? 1 : 0];
             const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
@@ -577,6 +614,10 @@ struct Solver {
                 iteration(Lc);
                 loop_ctl = false;
                 RVE_CUDA(cudaStreamEndCapture(Lc.stream, &body));
+                if (tc_err != cudaSuccess) {
+                    set_error(std::string("tensor-core operator launch: ") + cudaGetErrorString(tc_err));
+                    return RVE_ERR_CUDA;
+                }
                 RVE_CUDA(cudaGraphInstantiate(&gc.exec, graph, 0));
                 gc.key.assign(kb, kb + sizeof(key));
                 std::lock_guard<std::mutex> lock(m->ctx->prof_mu);
@@ -599,6 +640,10 @@ struct Solver {
                 iteration(L);
                 *launches += 6;
                 RVE_CUDA(cudaGetLastError());
+                if (tc_err != cudaSuccess) {
+                    set_error(std::string("tensor-core operator launch: ") + cudaGetErrorString(tc_err));
+                    return RVE_ERR_CUDA;
+                }
                 const int n_act_run = n_act;    // columns the iteration just run worked on
                 RVE_TRY(read_active());
                 // algorithmic bytes / flops of one operator launch of this solve:
@@ -837,7 +882,8 @@ struct Solver {
         RVE_CUDA(cudaMemcpyAsync(Ms.data(), m->msum.p, Ms.size() * 8, cudaMemcpyDeviceToHost, s));
         RVE_CUDA(cudaMemcpyAsync(&flags, cs64.flags, 4, cudaMemcpyDeviceToHost, s));
         RVE_CUDA(cudaStreamSynchronize(s));
-        out.numeric = flags != 0;
+        out.numeric = (flags & 1) != 0;
+        out.timeout = (flags & 4) != 0;
         const double V = m->volume;
         out.tensor.assign((size_t)B * 36, 0.0);
         out.sig.assign((size_t)B * 36, 0.0);
@@ -1069,6 +1115,10 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
         st->hill_mandel_mech = std::max(st->hill_mandel_mech, hm_m);
         st->hill_mandel_scalar = std::max(st->hill_mandel_scalar, hm_s);
     }
+    if (om.timeout || osc.timeout) {
+        set_error("a bounded wait inside the tensor-core operator gave up");
+        return RVE_ERR_TIMEOUT;
+    }
     if (om.numeric || osc.numeric) {
         set_error("non-finite or non-positive value in a PCG reduction");
         return RVE_ERR_NUMERIC;
@@ -1120,6 +1170,7 @@ void rve_default_options(rve_options* o) {
     o->profile = 0;
     o->warm_start = 2;
     o->transport_once = 0;
+    o->operator_kernel = 0;
 }
 
 int rve_create(rve_ctx* out, const rve_options* opts) {
@@ -1409,6 +1460,28 @@ static void fill_profile(const ProfCounters& a, const ProfCounters& b, rve_stats
     }
 }
 
+static int weak_sigma(rve_mesh m, int fid, std::vector<double>& sig);
+
+int rve_homogenise_weak(rve_ctx c, rve_mesh m, double* C, double* K, double* D, double* C_energy,
+                        double* K_energy, double* D_energy, rve_stats* st) {
+    RVE_TRY(check_ctx(c));
+    if (!m) return RVE_ERR_INVALID_ARGUMENT;
+    const int rc = rve_homogenise(c, m, C_energy, K_energy, D_energy, st);
+    if (rc != RVE_OK) return rc;
+    std::vector<double> sm, ss;
+    RVE_TRY(weak_sigma(m, 0, sm));
+    RVE_TRY(weak_sigma(m, 1, ss));
+    for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J)
+            if (C) C[I * 6 + J] = sm[I * 6 + J] * m->mc.ref_mech;
+    for (int I = 0; I < 3; ++I)
+        for (int J = 0; J < 3; ++J) {
+            if (K) K[I * 3 + J] = ss[I * 6 + J] * m->mc.ref_k;
+            if (D) D[I * 3 + J] = ss[I * 6 + 3 + J] * m->mc.ref_d;
+        }
+    return RVE_OK;
+}
+
 int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_stats* st) {
     RVE_TRY(check_ctx(c));
     if (!m) return RVE_ERR_INVALID_ARGUMENT;
@@ -1441,6 +1514,158 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
         fill_profile(pc0, c->prof, st);
     }
     return rc;
+}
+
+// sigma_bar = -D^T lambda / V (Eq. eq_homo_stress) of one field from the solution
+// left by rve_homogenise (six columns), with the constraint rows C of the BC
+// written out (Eqs. eq_RVE_disc_Eqs, eq_mat_C_and_D) and lambda recovered from
+// the equilibrium K u + C^T lambda = 0 of the total field u = u_tilde + X:
+//   Dirichlet: one row per boundary DOF, lambda = -(K u) there;
+//   periodic:  one row u_s - u_master(s) per image DOF s of the unfolded mesh,
+//              lambda_s = -(K u)_s (each image DOF sits in exactly one row);
+//   Neumann:   the six (three) uniform-traction rows plus the rigid-mode rows,
+//              lambda = -(C C^T)^-1 C K u (the rigid-mode multipliers vanish).
+// D = C X, with X the nodal interpolant of the unit macro fields: in the
+// hierarchic basis a linear field lives on the vertex functions alone, so only
+// vertex rows carry D, and for Dirichlet and periodic only the vertex
+// multipliers are formed (K u at vertices, from the element-mean stresses).
+static int weak_sigma(rve_mesh m, int fid, std::vector<double>& sig /* [ni][6] */) {
+    cudaStream_t s = m->ctx->stream;
+    FieldDev& f = fid == 0 ? m->mech : m->scal;
+    const int nc = f.nc, ni = nc == 3 ? 6 : 3, ncols = 6;
+    ElemView<double> ev;
+    ev.nt = m->nt;
+    ev.edofs = m->d_edofs.as<int32_t>();
+    ev.geo = m->d_geo64.as<double>();
+    ev.mat = (nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
+    ev.phase = m->d_phase.as<uint8_t>();
+    ev.scale = m->scale64.as<double>();
+    const double* u = m->x64f[fid].as<double>();
+    // unit macro field of load case I at a point y (engineering shear: E_ab = E_ba = 1/2)
+    auto Xval = [&](int I, const double* y, int c) -> double {
+        if (nc == 1) return y[I];
+        static const int VI[6] = {0, 1, 2, 0, 1, 2}, VJ[6] = {0, 1, 2, 1, 2, 0};
+        if (I < 3) return c == I ? y[I] : 0.0;
+        double v = 0.0;
+        if (c == VI[I]) v += 0.5 * y[VJ[I]];
+        if (c == VJ[I]) v += 0.5 * y[VI[I]];
+        return v;
+    };
+    DevBuf dout;
+    RVE_TRY(dout.ensure((size_t)12 * ncols * 8));
+    std::vector<double> out((size_t)12 * ncols, 0.0);
+    sig.assign((size_t)ni * ncols, 0.0);
+    if (m->bc == RVE_BC_DIRICHLET || m->bc == RVE_BC_PERIODIC) {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int64_t v = 0; v < m->nv; ++v)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], m->xyz[3 * v + a]);
+                hi[a] = std::max(hi[a], m->xyz[3 * v + a]);
+            }
+        std::vector<int32_t> vid;
+        std::vector<double> w;
+        for (int64_t v = 0; v < m->nv; ++v) {
+            const double* y = &m->xyz[3 * v];
+            double dy[3] = {0, 0, 0};
+            bool on = false;
+            for (int a = 0; a < 3; ++a) {
+                const double tol = 1e-9 * (hi[a] - lo[a]);
+                const bool at_lo = std::fabs(y[a] - lo[a]) <= tol, at_hi = std::fabs(y[a] - hi[a]) <= tol;
+                if (m->bc == RVE_BC_DIRICHLET) {
+                    on = on || at_lo || at_hi;
+                } else if (at_hi) {   // image of the vertex with this coordinate at the low face
+                    on = true;
+                    dy[a] = hi[a] - lo[a];
+                }
+            }
+            if (!on) continue;
+            if (m->bc == RVE_BC_DIRICHLET)
+                for (int a = 0; a < 3; ++a) dy[a] = y[a];
+            vid.push_back((int32_t)v);
+            for (int I = 0; I < ni; ++I)
+                for (int c = 0; c < nc; ++c) w.push_back(Xval(I, dy, c));
+        }
+        DevBuf dr, dvid, dw;
+        RVE_TRY(dr.ensure((size_t)m->nv * nc * ncols * 8));
+        RVE_CUDA(cudaMemsetAsync(dr.p, 0, (size_t)m->nv * nc * ncols * 8, s));
+        RVE_TRY(upload(dvid, vid.data(), vid.size(), s));
+        RVE_TRY(upload(dw, w.data(), w.size(), s));
+        launch_vertex_reactions(m->p, nc, ev, m->d_lverts.as<int32_t>(), u, dr.as<double>(), ncols, s);
+        // sigma_I = -(1/V) sum_rows D_I lambda = (1/V) sum_constrained-vertices X_I . (K u)
+        launch_weighted_vertex_sum((int)vid.size(), ni, nc, dvid.as<int32_t>(), dw.as<double>(), dr.as<double>(),
+                                   ncols, dout.as<double>(), s);
+        m->ctx->launches += 2;
+        RVE_CUDA(cudaGetLastError());
+        RVE_CUDA(cudaMemcpyAsync(out.data(), dout.p, (size_t)ni * ncols * 8, cudaMemcpyDeviceToHost, s));
+        RVE_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < ni * ncols; ++i) sig[i] = out[i] / m->volume;
+        return RVE_OK;
+    }
+    // Neumann: K u on every DOF, then C K u over the constraint rows
+    const int mr = f.m;
+    DevBuf dy;
+    RVE_TRY(dy.ensure((size_t)f.n_rows * ncols * 8));
+    RVE_CUDA(cudaMemsetAsync(dy.p, 0, (size_t)f.n_rows * ncols * 8, s));
+    Launch L = make_launch(ncols, std::max<int64_t>(f.n_rows, m->nt), s);
+    launch_operator<double>(m->p, nc, true, ev, u, dy.as<double>(), nullptr, L);
+    launch_rows_dot(f.n_sup, mr, f.sup_row.as<int64_t>(), f.sup_coef.as<double>(), dy.as<double>(), ncols,
+                    dout.as<double>(), s);
+    m->ctx->launches += 2;
+    RVE_CUDA(cudaGetLastError());
+    RVE_CUDA(cudaMemcpyAsync(out.data(), dout.p, (size_t)mr * ncols * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    // C C^T and D = C X from the host copies of the rows
+    std::vector<double> CC((size_t)mr * mr, 0.0), Dm((size_t)mr * ni, 0.0);
+    const DofMap& M = m->map;
+    for (size_t i = 0; i < f.h_sup_row.size(); ++i) {
+        const double* cr = &f.h_sup_coef[i * mr];
+        for (int a = 0; a < mr; ++a)
+            for (int b = 0; b < mr; ++b) CC[a * mr + b] += cr[a] * cr[b];
+        const int64_t row = f.h_sup_row[i], dof = row / nc;
+        const int c = (int)(row % nc);
+        if (M.dof_vertex[dof] < 0) continue;
+        const double* y = &m->xyz[3 * (int64_t)M.dof_vertex[dof]];
+        for (int I = 0; I < ni; ++I) {
+            const double xv = Xval(I, y, c);
+            for (int a = 0; a < mr; ++a) Dm[a * ni + I] += cr[a] * xv;
+        }
+    }
+    // lambda = -(C C^T)^-1 C K u (Cholesky of the m x m Gram matrix)
+    std::vector<double> Lc((size_t)mr * mr, 0.0);
+    for (int j = 0; j < mr; ++j) {
+        double d = CC[j * mr + j];
+        for (int k = 0; k < j; ++k) d -= Lc[j * mr + k] * Lc[j * mr + k];
+        if (!(d > 0)) {
+            set_error("rve_homogenise_weak: constraint rows are linearly dependent");
+            return RVE_ERR_NUMERIC;
+        }
+        Lc[j * mr + j] = std::sqrt(d);
+        for (int r = j + 1; r < mr; ++r) {
+            double t = CC[r * mr + j];
+            for (int k = 0; k < j; ++k) t -= Lc[r * mr + k] * Lc[j * mr + k];
+            Lc[r * mr + j] = t / Lc[j * mr + j];
+        }
+    }
+    const int t0 = nc == 3 ? 6 : 1;   // first uniform-traction row (rigid-mode rows come first)
+    for (int col = 0; col < ncols; ++col) {
+        std::vector<double> z(mr);
+        for (int a = 0; a < mr; ++a) {
+            double t = -out[a * ncols + col];
+            for (int k = 0; k < a; ++k) t -= Lc[a * mr + k] * z[k];
+            z[a] = t / Lc[a * mr + a];
+        }
+        for (int a = mr - 1; a >= 0; --a) {
+            double t = z[a];
+            for (int k = a + 1; k < mr; ++k) t -= Lc[k * mr + a] * z[k];
+            z[a] = t / Lc[a * mr + a];
+        }
+        for (int I = 0; I < ni; ++I) {
+            double acc = 0.0;
+            for (int a = t0; a < t0 + ni; ++a) acc += Dm[a * ni + I] * z[a];
+            sig[I * ncols + col] = -acc / m->volume;
+        }
+    }
+    return RVE_OK;
 }
 
 // RVEs per device pass for one mesh: enough columns to fill the GPU (about 16M
@@ -1949,6 +2174,83 @@ int rve_apply_operator(rve_ctx c, rve_mesh m, int field, int ncols, const double
     const double ref = field == 0 ? m->mc.ref_mech : (field == 1 ? m->mc.ref_k : m->mc.ref_d);
     for (int64_t r = 0; r < n_rows; ++r)
         for (int j = 0; j < ncols; ++j) y[r * ncols + j] = yp[r * cpad2 + colmap[j]] * ref;
+    return RVE_OK;
+}
+
+int rve_apply_operator_mixed(rve_ctx c, rve_mesh m, int kernel, int ncols, const double* x, const double* scale,
+                             const int32_t* active, double* y, double* energy) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !x || !y || ncols <= 0 || ncols % 6 != 0 || (kernel != 0 && kernel != 1)) {
+        set_error("rve_apply_operator_mixed: invalid argument (kernel 0 or 1, ncols a positive multiple of 6)");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    if (!m->have_materials) return RVE_ERR_STATE;
+    if (kernel == 0 && !operator_tc_supported(m->p, 3)) {
+        set_error("rve_apply_operator_mixed: the tensor-core operator needs p = 2 or 3");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    cudaStream_t s = c->stream;
+    FieldDev& f = m->mech;
+    const int64_t n_rows = f.n_rows;
+    const size_t nv = (size_t)n_rows * ncols;
+    std::vector<float> x32(nv), sc32((size_t)ncols * 2, 1.f);
+    for (size_t i = 0; i < nv; ++i) x32[i] = (float)x[i];
+    if (scale)
+        for (int i = 0; i < 2 * ncols; ++i) sc32[i] = (float)scale[i];
+    std::vector<int32_t> act(ncols, 1);
+    if (active)
+        for (int i = 0; i < ncols; ++i) act[i] = active[i] != 0;
+    Launch L = make_launch(ncols, std::max<int64_t>(n_rows, m->nt), s);
+    DevBuf dx, dy, dsc, dact, dlist, dpart, dsum, dflag;
+    RVE_TRY(upload(dx, x32.data(), nv, s));
+    RVE_TRY(upload(dsc, sc32.data(), sc32.size(), s));
+    RVE_TRY(upload(dact, act.data(), act.size(), s));
+    RVE_TRY(dy.ensure(nv * 4));
+    RVE_TRY(dlist.ensure((size_t)ncols * 4 + 64));
+    RVE_TRY(dpart.ensure((size_t)L.nby * ncols * 8));
+    RVE_TRY(dsum.ensure((size_t)ncols * 8));
+    RVE_TRY(dflag.ensure(16));
+    RVE_CUDA(cudaMemsetAsync(dy.p, 0, nv * 4, s));
+    RVE_CUDA(cudaMemsetAsync(dpart.p, 0, (size_t)L.nby * ncols * 8, s));
+    RVE_CUDA(cudaMemsetAsync(dflag.p, 0, 16, s));
+    int32_t* list = dlist.as<int32_t>();
+    int32_t* n_list = list + ncols;
+    launch_compact_active(dact.as<int32_t>(), ncols, list, n_list, s);
+    if (kernel == 0) {
+        RVE_TRY(ensure_element_matrices(m, s));
+        RVE_CUDA(launch_operator_tc(m->p, m->nt, m->d_edofs.as<int32_t>(), m->d_ke32.as<float>(),
+                                    m->d_kepairs.as<uint16_t>(), m->d_phase.as<uint8_t>(), dsc.as<float>(),
+                                    dx.as<float>(), dy.as<float>(), dpart.as<double>(), dact.as<int32_t>(), ncols,
+                                    list, n_list, L.nby, dflag.as<int32_t>(), s));
+    } else {
+        ElemView<float> ev;
+        ev.nt = m->nt;
+        ev.edofs = m->d_edofs.as<int32_t>();
+        ev.geo = m->d_geo32.as<float>();
+        ev.mat = m->d_matm32.as<float>();
+        ev.phase = m->d_phase.as<uint8_t>();
+        ev.scale = dsc.as<float>();
+        launch_operator<float>(m->p, 3, false, ev, dx.as<float>(), dy.as<float>(), dpart.as<double>(), L,
+                               dact.as<int32_t>(), list, n_list);
+    }
+    launch_reduce_partials(L.nby, ncols, dpart.as<double>(), dsum.as<double>(), s);
+    c->launches += 3;
+    RVE_CUDA(cudaGetLastError());
+    std::vector<float> y32(nv);
+    std::vector<double> es(ncols);
+    int32_t flag = 0;
+    RVE_CUDA(cudaMemcpyAsync(y32.data(), dy.p, nv * 4, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(es.data(), dsum.p, (size_t)ncols * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaMemcpyAsync(&flag, dflag.p, 4, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    if (flag & 4) {
+        set_error("a bounded wait inside the tensor-core operator gave up");
+        return RVE_ERR_TIMEOUT;
+    }
+    const double ref = m->mc.ref_mech;
+    for (size_t i = 0; i < nv; ++i) y[i] = (double)y32[i] * ref;
+    if (energy)
+        for (int j = 0; j < ncols; ++j) energy[j] = act[j] ? es[j] * ref : 0.0;
     return RVE_OK;
 }
 

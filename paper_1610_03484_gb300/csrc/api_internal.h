@@ -99,6 +99,8 @@ struct FieldDev {
     int m = 0;
     int64_t n_sup = 0;
     DevBuf sup_row, sup_coef, sup_of_row;
+    std::vector<int64_t> h_sup_row;   // host copies of the rows (the multiplier route's D = C X)
+    std::vector<double> h_sup_coef;
 };
 
 }  // namespace rve
@@ -116,6 +118,7 @@ struct SolveOut {
     bool converged = true;
     double rel_res = 0;
     bool numeric = false;
+    bool timeout = false;   // a bounded device wait gave up
 };
 
 struct ProfCounters {
@@ -179,6 +182,10 @@ struct rve_mesh_s {
     // device mesh
     rve::DevBuf d_xyz, d_edofs, d_lverts, d_geo64, d_geo32, d_phase, d_tangent, d_flag;
     rve::DevBuf d_matm64, d_matm32, d_mats64, d_mats32;
+    // tensor-core operator: packed FP32 element matrices of the mechanics (formed lazily,
+    // invalidated whenever the DOF map or the materials change) and their index tables
+    rve::DevBuf d_ke32, d_kepairs, d_keptab;
+    bool ke_valid = false;
     rve::FieldDev mech, scal;
     bool have_materials = false;
     int tuned_batch = 0;   // batch size chosen by rve_autotune_batch (0: the built-in rule)

@@ -7,6 +7,7 @@
 // writes one FP64 partial per (blockIdx.y, column), summed by a finalize kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
@@ -1016,8 +1017,13 @@ struct ColJacobi {
 __global__ void __launch_bounds__(256) k_finalize_alpha(const double* __restrict__ ep, int nby, int ncols,
                                                         ColState cs) {
     const int col = blockIdx.x;
-    if (!cs.active[col]) {
-        if (threadIdx.x == 0) cs.alpha[col] = 0.0;
+    // a bounded wait in the operator gave up (flag bit 2): every column stops, so
+    // the device-side loop ends at the next compaction
+    if (!cs.active[col] || (cs.flags[0] & 4)) {
+        if (threadIdx.x == 0) {
+            cs.alpha[col] = 0.0;
+            cs.active[col] = 0;
+        }
         return;
     }
     double v = 0.0;
@@ -1590,6 +1596,120 @@ template void launch_mean_stress<float, double>(int, int, const ElemView<float>&
                                                 const Launch&);
 template void launch_mean_stress<float, float>(int, int, const ElemView<float>&, const float*, double*,
                                                const Launch&);
+
+// ------------------------------------------- multiplier route (Eq. eq_homo_stress)
+// Vertex reactions of the total field u = u_tilde + X (X the unit macro field of
+// the column): every vertex function has a constant gradient, so its entry of
+// K u on element e is |T| s grad(lam_a) . sigma_e with sigma_e the element-mean
+// stress (flux); it is scattered to the ORIGINAL vertex id of local vertex a,
+// i.e. onto the unfolded mesh, where the constraint rows of the BC live.
+template <int P, int NC>
+__global__ void __launch_bounds__(256) k_vertex_reactions(ElemView<double> ev, const int32_t* __restrict__ lverts,
+                                                          const double* __restrict__ u, double* __restrict__ r,
+                                                          int ncols) {
+    constexpr int NE = Order<P>::NE;
+    constexpr int NM = Order<P>::NM;
+    const int64_t n = ev.nt * ncols;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i / ncols;
+        const int col = (int)(i % ncols);
+        const int field = (col % 6) >= 3 ? 1 : 0;
+        const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
+        const int32_t* ed = ev.edofs + e * NE;
+        double G[9];
+        for (int q = 0; q < 9; ++q) G[q] = ev.geo[e * 10 + q];
+        const double sv = ev.scale[col * 2 + ev.phase[e]] * ev.geo[e * 10 + 9];
+        double V[3][NC];
+        const int d0 = ed[0];
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < NC; ++c)
+                V[k][c] = u[((int64_t)ed[k + 1] * NC + c) * ncols + col] - u[((int64_t)d0 * NC + c) * ncols + col];
+        for (int j = 4; j < NE; ++j)
+            for (int k = 0; k < 3; ++k) {
+                const double a = basis_a<P, double>((k * NM + 0) * NE + j);
+                if (a != 0.0)
+                    for (int c = 0; c < NC; ++c) V[k][c] += a * u[((int64_t)ed[j] * NC + c) * ncols + col];
+            }
+        double H[NC][3];
+        for (int c = 0; c < NC; ++c)
+            for (int l = 0; l < 3; ++l) H[c][l] = V[0][c] * G[l] + V[1][c] * G[3 + l] + V[2][c] * G[6 + l];
+        double S[NC][3];
+        if constexpr (NC == 3) {
+            double ev6[6] = {H[0][0], H[1][1], H[2][2], H[0][1] + H[1][0], H[1][2] + H[2][1], H[2][0] + H[0][2]};
+            ev6[macro_id] += 1.0;
+            double sg[6];
+            for (int a = 0; a < 6; ++a) {
+                double t = 0.0;
+                for (int b = 0; b < 6; ++b) t += ev.mat[e * 21 + ut6(a, b)] * ev6[b];
+                sg[a] = sv * t;
+            }
+            S[0][0] = sg[0]; S[0][1] = sg[3]; S[0][2] = sg[5];
+            S[1][0] = sg[3]; S[1][1] = sg[1]; S[1][2] = sg[4];
+            S[2][0] = sg[5]; S[2][1] = sg[4]; S[2][2] = sg[2];
+        } else {
+            const double* Km = ev.mat + e * 12 + 6 * field;
+            double g[3] = {H[0][0], H[0][1], H[0][2]};
+            g[macro_id] += 1.0;
+            for (int l = 0; l < 3; ++l) S[0][l] = sv * (Km[s3(l, 0)] * g[0] + Km[s3(l, 1)] * g[1] + Km[s3(l, 2)] * g[2]);
+        }
+        for (int a = 0; a < 4; ++a) {
+            double gl[3];
+            for (int l = 0; l < 3; ++l) gl[l] = a == 0 ? -(G[l] + G[3 + l] + G[6 + l]) : G[3 * (a - 1) + l];
+            const int64_t v = lverts[e * 4 + a];
+            for (int c = 0; c < NC; ++c)
+                atomicAdd(r + (v * NC + c) * ncols + col, gl[0] * S[c][0] + gl[1] * S[c][1] + gl[2] * S[c][2]);
+        }
+    }
+}
+
+void launch_vertex_reactions(int p, int nc, const ElemView<double>& ev, const int32_t* lverts, const double* u,
+                             double* r, int ncols, cudaStream_t s) {
+    const int64_t n = ev.nt * ncols;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16));
+#define RVE_VR_CASE(PP, NCC)                                                                      \
+    if (p == PP && nc == NCC) {                                                                   \
+        k_vertex_reactions<PP, NCC><<<grid, 256, 0, s>>>(ev, lverts, u, r, ncols);                 \
+        return;                                                                                   \
+    }
+    RVE_VR_CASE(1, 3) RVE_VR_CASE(2, 3) RVE_VR_CASE(3, 3)
+    RVE_VR_CASE(1, 1) RVE_VR_CASE(2, 1) RVE_VR_CASE(3, 1)
+#undef RVE_VR_CASE
+}
+
+// out[i][col] = sum_k sum_c w[k][i][c] r[vid[k]][c][col]: one block per (i, col)
+__global__ void __launch_bounds__(256) k_weighted_vertex_sum(int n, int ni, int nc, const int32_t* __restrict__ vid,
+                                                             const double* __restrict__ w,
+                                                             const double* __restrict__ r, int ncols,
+                                                             double* __restrict__ out) {
+    const int i = blockIdx.x / ncols, col = blockIdx.x % ncols;
+    double v = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+        for (int c = 0; c < nc; ++c)
+            v += w[((int64_t)k * ni + i) * nc + c] * r[((int64_t)vid[k] * nc + c) * ncols + col];
+    v = block_sum(v);
+    if (threadIdx.x == 0) out[i * ncols + col] = v;
+}
+
+void launch_weighted_vertex_sum(int n, int ni, int nc, const int32_t* vid, const double* w, const double* r,
+                                int ncols, double* out, cudaStream_t s) {
+    k_weighted_vertex_sum<<<ni * ncols, 256, 0, s>>>(n, ni, nc, vid, w, r, ncols, out);
+}
+
+// out[k][col] = sum_i coef[i][k] y[row[i]][col] (constraint rows applied to y): one block per (k, col)
+__global__ void __launch_bounds__(256) k_rows_dot(int64_t n_sup, int m, const int64_t* __restrict__ row,
+                                                  const double* __restrict__ coef, const double* __restrict__ y,
+                                                  int ncols, double* __restrict__ out) {
+    const int k = blockIdx.x / ncols, col = blockIdx.x % ncols;
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < n_sup; i += blockDim.x) v += coef[i * m + k] * y[row[i] * ncols + col];
+    v = block_sum(v);
+    if (threadIdx.x == 0) out[k * ncols + col] = v;
+}
+
+void launch_rows_dot(int64_t n_sup, int m, const int64_t* row, const double* coef, const double* y, int ncols,
+                     double* out, cudaStream_t s) {
+    k_rows_dot<<<m * ncols, 256, 0, s>>>(n_sup, m, row, coef, y, ncols, out);
+}
 
 // out[w] = sum_b part[b][w]: one block per output value (up to 128 outputs per
 // block row are handled by grid-striding over w).

@@ -166,6 +166,34 @@ void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 void launch_axpy_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
 void launch_neg(int64_t n, double* a, cudaStream_t s);
 
+// multiplier route of Eq. eq_homo_stress: vertex reactions of the total field
+// u + X (macro load of each column) scattered to original vertex ids, r [nv][nc][ncols]
+void launch_vertex_reactions(int p, int nc, const ElemView<double>& ev, const int32_t* lverts, const double* u,
+                             double* r, int ncols, cudaStream_t s);
+// out[i][col] = sum_k w[k][i][:] . r[vid[k]][:][col]
+void launch_weighted_vertex_sum(int n, int ni, int nc, const int32_t* vid, const double* w, const double* r,
+                                int ncols, double* out, cudaStream_t s);
+// out[k][col] = sum_i coef[i][k] y[row[i]][col]
+void launch_rows_dot(int64_t n_sup, int m, const int64_t* row, const double* coef, const double* y, int ncols,
+                     double* out, cudaStream_t s);
+
+// tensor-core operator of the mixed-precision inner solve (operator_tc.cu): mechanics, p = 2, 3
+bool operator_tc_supported(int p, int nc);
+int64_t element_matrix_floats(int p);   // packed FP32 floats per element (padded to 4)
+int element_matrix_pairs(int p);        // packed entries per element: n (n + 1) / 2, n = 3 n_local(p)
+// the packed element matrices ke [nt][element_matrix_floats(p)] from the FP64 element data;
+// pairs_dev [element_matrix_pairs(p)] and ptab_dev [9 n_local(p)^2] are caller-owned scratch
+cudaError_t build_element_matrices(int p, int64_t nt, const double* geo64, const double* matm64, float* ke,
+                                   uint16_t* pairs_dev, double* ptab_dev, cudaStream_t s);
+// sets the kernels' shared-memory limit; call once per device before the first launch
+cudaError_t operator_tc_prepare(int p);
+// y += s K x for the listed (or active) columns; energy partials [nby_total][ncols] like
+// launch_operator's; err bit 2 set when a bounded device wait gave up
+cudaError_t launch_operator_tc(int p, int64_t nt, const int32_t* edofs, const float* ke, const uint16_t* pairs,
+                               const uint8_t* phase, const float* scale, const float* x, float* y, double* epart,
+                               const int32_t* active, int ncols, const int32_t* list, const int32_t* n_list,
+                               int nby_total, int32_t* err, cudaStream_t s);
+
 // allocation-free entry point support (noalloc.cu)
 int noalloc_max_cols();
 int noalloc_max_blocks_y();
