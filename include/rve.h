@@ -273,6 +273,17 @@ int rve_autotune_batch(rve_ctx ctx, rve_mesh m, int64_t n, const double* T_C, co
                        const double* t_h, const int32_t* candidates, int n_cand, int32_t* best,
                        double* rates);
 
+/* Sharding of one batch of macro Gauss points over n_ranks processes, one GPU
+ * each (scheduling; the paper runs its RVEs on distributed-memory HPC, Secs. 1
+ * and 8).  cost[g] > 0 is an estimate of point g's solve cost (e.g. the DOFs
+ * of its RVE times its expected PCG iterations).  Writes offsets[n_ranks + 1]:
+ * rank r takes the contiguous points [offsets[r], offsets[r + 1]).  The
+ * boundaries minimise the largest block cost (the linear-partition optimum,
+ * found by bisection to 1e-12 of the total); imbalance (optional) receives
+ * the largest block cost over the mean.  Host computation only: no context,
+ * no device. */
+int rve_partition_blocks(int64_t G, const double* cost, int n_ranks, int64_t* offsets, double* imbalance);
+
 /* ------------------------------------------------------- learned surrogate
  * No counterpart in the paper: an ensemble of MLPs (8 features -> 4 x 256
  * SiLU -> 33 Cholesky-factor entries of the normalised C, K, D, diagonals

@@ -150,6 +150,7 @@ _SIGS = {
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_homogenise_weak": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(Stats)]),
+    "rve_partition_blocks": (C.c_int, [C.c_int64, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
     "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
@@ -203,6 +204,16 @@ def load_library(path: str = LIB_PATH):
 
 def exported_symbols():
     return list(_SIGS)
+
+
+def partition_blocks(cost, n_ranks: int):
+    """Contiguous cost-balanced blocks (rve_partition_blocks): (offsets [n+1], imbalance)."""
+    lib = load_library()
+    c = np.ascontiguousarray(cost, np.float64)
+    off = np.zeros(int(n_ranks) + 1, np.int64)
+    imb = C.c_double()
+    _check(lib.rve_partition_blocks(len(c), _ptr(c), int(n_ranks), _ptr(off), C.byref(imb)), "rve_partition_blocks")
+    return off, imb.value
 
 
 def _check(rc: int, where: str, allow=()):

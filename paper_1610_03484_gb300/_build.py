@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librve.so")
 SOURCES = ["kernels.cu", "operator_tc.cu", "api.cu", "noalloc.cu", "surrogate.cu", "surrogate_api.cu", "macro.cu", "basis.cpp",
-           "mesh.cpp"]
+           "mesh.cpp", "partition.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1460,7 +1460,7 @@ static void fill_profile(const ProfCounters& a, const ProfCounters& b, rve_stats
     }
 }
 
-static int weak_sigma(rve_mesh m, int fid, std::vector<double>& sig);
+static int weak_sigma(rve_mesh m, int fid, const double* d_w, std::vector<double>& sig);
 
 int rve_homogenise_weak(rve_ctx c, rve_mesh m, double* C, double* K, double* D, double* C_energy,
                         double* K_energy, double* D_energy, rve_stats* st) {
@@ -1468,9 +1468,17 @@ int rve_homogenise_weak(rve_ctx c, rve_mesh m, double* C, double* K, double* D, 
     if (!m) return RVE_ERR_INVALID_ARGUMENT;
     const int rc = rve_homogenise(c, m, C_energy, K_energy, D_energy, st);
     if (rc != RVE_OK) return rc;
+    cudaStream_t s = c->stream;
+    double state[3] = {m->T_C, m->c_wt, m->t_h};
+    DevBuf dstate;
+    RVE_TRY(dstate.ensure(4 * 8));
+    RVE_CUDA(cudaMemcpyAsync(dstate.p, state, sizeof(state), cudaMemcpyHostToDevice, s));
+    double* d = dstate.as<double>();
+    launch_degradation(1, d, d + 1, d + 2, m->deg.beta, m->deg.Tg_C, m->deg.c_sat_wt, d + 3, s);
+    c->launches++;
     std::vector<double> sm, ss;
-    RVE_TRY(weak_sigma(m, 0, sm));
-    RVE_TRY(weak_sigma(m, 1, ss));
+    RVE_TRY(weak_sigma(m, 0, d + 3, sm));
+    RVE_TRY(weak_sigma(m, 1, d + 3, ss));
     for (int I = 0; I < 6; ++I)
         for (int J = 0; J < 6; ++J)
             if (C) C[I * 6 + J] = sm[I * 6 + J] * m->mc.ref_mech;
@@ -1529,17 +1537,22 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
 // hierarchic basis a linear field lives on the vertex functions alone, so only
 // vertex rows carry D, and for Dirichlet and periodic only the vertex
 // multipliers are formed (K u at vertices, from the element-mean stresses).
-static int weak_sigma(rve_mesh m, int fid, std::vector<double>& sig /* [ni][6] */) {
+static int weak_sigma(rve_mesh m, int fid, const double* d_w, std::vector<double>& sig /* [ni][6] */) {
     cudaStream_t s = m->ctx->stream;
     FieldDev& f = fid == 0 ? m->mech : m->scal;
     const int nc = f.nc, ni = nc == 3 ? 6 : 3, ncols = 6;
+    // this field's column scales at the RVE's degradation factor (transport does not degrade)
+    DevBuf dscale;
+    RVE_TRY(dscale.ensure((size_t)ncols * 2 * 8));
+    launch_column_scales<double>(1, d_w, fid == 0 ? m->deg.apply_to_yarn : 0, fid == 0, dscale.as<double>(), s);
+    m->ctx->launches++;
     ElemView<double> ev;
     ev.nt = m->nt;
     ev.edofs = m->d_edofs.as<int32_t>();
     ev.geo = m->d_geo64.as<double>();
     ev.mat = (nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
     ev.phase = m->d_phase.as<uint8_t>();
-    ev.scale = m->scale64.as<double>();
+    ev.scale = dscale.as<double>();
     const double* u = m->x64f[fid].as<double>();
     // unit macro field of load case I at a point y (engineering shear: E_ab = E_ba = 1/2)
     auto Xval = [&](int I, const double* y, int c) -> double {
