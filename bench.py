@@ -1,8 +1,9 @@
 """Benchmark: batched RVE homogenisation throughput on one GB300 (or N, weak scaling).
 
-Workload (one step): the batched FE^2 evaluation of 4096 macro Gauss points,
-each with its own degradation state (T ~ U(20,60) C, moisture ~ U(0,1.5) wt%,
-time = 10^U(0,4) h, seed 2 + rank), RVE plain-weave grids 16x16x6 / 24x24x8 /
+Workload (one step): the batched FE^2 evaluation of 4096 macro Gauss points per
+GPU, each with its own degradation state (T ~ U(20,60) C, moisture ~ U(0,1.5)
+wt%, time = 10^U(0,4) h; one batch of 4096 x N points from seed 2, split over N
+ranks into blocks of equal estimated cost), RVE plain-weave grids 16x16x6 / 24x24x8 /
 32x32x10 and order p in {1,2} drawn uniformly, periodic BC; each point solves
 6 mechanical + 3 thermal + 3 moisture cell problems and returns C, K, D.
 Mixed precision: FP32 operator and vectors, FP64 scalars / reductions and
@@ -176,6 +177,7 @@ def build_meshes(ctx, rve):
 
 
 TUNE_SEED = 1000
+KERNEL_NAMES = {1: "cuda_core", 2: "tensor_tf32x3"}
 TUNE_MAX_ENTRIES = 64e6      # candidate batch sizes keep one FP64 vector within 512 MB
 
 
@@ -194,8 +196,15 @@ def autotune(meshes, classes, n_points, rank):
         if len(cand) == 1 or sel.sum() < 2:
             chosen[name] = {"batch": cand[0], "rates": None}
             continue
-        best, rates = m.autotune_batch(T[sel], c[sel], t[sel], cand)
-        chosen[name] = {"batch": best, "rates": {str(k): round(v, 1) for k, v in rates.items()}}
+        if q >= 2:
+            # schedule: batch size and operator kernel (tensor cores or CUDA cores)
+            best, kern, rates = m.autotune_schedule(T[sel], c[sel], t[sel], cand)
+            chosen[name] = {"batch": best, "kernel": KERNEL_NAMES[kern],
+                            "rates": {f"{KERNEL_NAMES[k]} b{b}": round(v, 1) for (k, b), v in rates.items()}}
+        else:
+            best, rates = m.autotune_batch(T[sel], c[sel], t[sel], cand)
+            chosen[name] = {"batch": best, "kernel": "cuda_core (matrix-free)",
+                            "rates": {str(k): round(v, 1) for k, v in rates.items()}}
     return chosen
 
 
@@ -217,10 +226,23 @@ def run_ours(args, world, rank, local):
                       batch=args.batch, stream=stream.cuda_stream, device=local,
                       warm_start=args.warm_start)
     meshes, classes = build_meshes(ctx, rve)
-    G = args.points
-    tuned = autotune(meshes, classes, G, rank) if not args.no_autotune and args.batch == 0 else None
-    T, c, t, size, p = ri.gauss_point_states(G, SEED + rank)
+    tuned = autotune(meshes, classes, args.points, rank) if not args.no_autotune and args.batch == 0 else None
+    # one seeded batch of points x world Gauss points; with several ranks it is split
+    # into contiguous blocks of equal estimated cost (DOFs x expected iterations)
+    # and every step ends with the gather of the 33 tensor values per point
+    G_total = args.points * world
+    T, c, t, size, p = ri.gauss_point_states(G_total, SEED)
     mid = mesh_ids(size, p, classes)
+    shard = None
+    if world > 1:
+        from paper_1610_03484_gb300 import sharding
+        dofs = [3 * m.info()["n_scalar_dofs"] for m in meshes]
+        cost = sharding.point_costs(dofs, [ri.SIZE_CLASSES[si] for si, _ in classes], [q for _, q in classes], mid)
+        off, imb = rve.partition_blocks(cost, world)
+        lo, hi = int(off[rank]), int(off[rank + 1])
+        T, c, t, size, p, mid = T[lo:hi], c[lo:hi], t[lo:hi], size[lo:hi], p[lo:hi], mid[lo:hi]
+        shard = {"offsets": off, "imbalance": imb, "module": sharding}
+    G = len(T)
     # device-resident inputs / outputs for `value`
     Td = torch.tensor(T, dtype=torch.float64, device=dev)
     cd = torch.tensor(c, dtype=torch.float64, device=dev)
@@ -234,6 +256,10 @@ def run_ours(args, world, rank, local):
     def step():
         st, rc = ctx.macro_update_dev(meshes, Td.data_ptr(), cd.data_ptr(), td.data_ptr(), mid,
                                       Cd.data_ptr(), Kd.data_ptr(), Dd.data_ptr(), Sd.data_ptr())
+        if shard is not None:   # the data-path collective: every rank gets the whole batch
+            sh = shard["module"]
+            local = sh.pack(Cd.cpu().numpy(), Kd.cpu().numpy(), Dd.cpu().numpy(), Sd.cpu().numpy())
+            shard["result"] = sh.gather_blocks(local, shard["offsets"])
         return st
 
     for _ in range(args.warmup):
@@ -306,6 +332,8 @@ def run_ours(args, world, rank, local):
     job_s = max_over_ranks(local_s, world)
     units = sum_over_ranks(G * args.steps, world)
     value = units / job_s
+    if shard is not None and not (shard["result"][:, 33] == 0).all():
+        raise RuntimeError("gathered batch: some points not converged")
 
     # end to end through the host-buffer entry point (pinned host memory)
     Th = torch.tensor(T).pin_memory()
@@ -332,7 +360,14 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": job_s * 1000.0 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "points_per_gpu": G, "seed": SEED, "bc": "periodic",
+        "config": {"workload": WORKLOAD, "points_per_gpu": G, "points_total": G_total, "seed": SEED,
+                   "bc": "periodic",
+                   "sharding": (None if shard is None else
+                                {"blocks": "contiguous, balanced by DOFs x expected iterations",
+                                 "offsets": [int(x) for x in shard["offsets"]],
+                                 "cost_imbalance": shard["imbalance"],
+                                 "collective": "all_gather of 33 FP64 values + status per point, "
+                                               "inside every timed step"}),
                    "precision": "FP32 operator and inner PCG; double-float true residual; FP64 scalars, "
                                 "reductions and solution", "rtol": RTOL,
                    "inner_rtol": INNER_RTOL, "warm_start": args.warm_start,

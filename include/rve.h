@@ -60,6 +60,10 @@ extern "C" {
 
 #define RVE_MODE_PCG     0   /* macro_update_gauss_points: plain batched PCG for every point */
 
+#define RVE_KERNEL_AUTO      0   /* operator kernel of the mixed inner solve (rve_options) */
+#define RVE_KERNEL_CUDA_CORE 1
+#define RVE_KERNEL_TENSOR    2
+
 /* ------------------------------------------------------------------ types */
 typedef struct rve_ctx_s*  rve_ctx;
 typedef struct rve_mesh_s* rve_mesh;
@@ -85,11 +89,13 @@ typedef struct rve_options {
                                 those K and D (transport is not degraded, Sec. 5, so they are the
                                 same problems); 0 (default) solves all twelve load cases for
                                 every point */
-    int     operator_kernel; /* MIXED inner solve, mechanics at p = 2 and 3: 0 (default) applies
-                                the operator on the tensor cores (element matrices stored once
-                                per mesh and materials, 3 x TF32 products with FP32 accumulation);
-                                1 uses the matrix-free CUDA-core kernel.  Other cases always use
-                                the matrix-free kernel. */
+    int     operator_kernel; /* MIXED inner solve, mechanics at p = 2 and 3: RVE_KERNEL_AUTO
+                                (default) takes the kernel rve_autotune_schedule chose for the
+                                mesh, else the matrix-free CUDA-core kernel; RVE_KERNEL_CUDA_CORE
+                                that kernel; RVE_KERNEL_TENSOR the tensor-core kernel (element
+                                matrices stored once per mesh and materials, 3 x TF32 products
+                                with FP32 accumulation).  Other cases always use the matrix-free
+                                kernel. */
 } rve_options;
 
 /* Isotropic matrix phase (Sec. 1, Sec. 7). */
@@ -283,6 +289,20 @@ int rve_autotune_batch(rve_ctx ctx, rve_mesh m, int64_t n, const double* T_C, co
  * the largest block cost over the mean.  Host computation only: no context,
  * no device. */
 int rve_partition_blocks(int64_t G, const double* cost, int n_ranks, int64_t* offsets, double* imbalance);
+
+/* Schedule autotuner for one mesh (no counterpart in the paper): times every
+ * pair of a batch size from batches[n_batch] and an operator kernel from
+ * kernels[n_kernel] (RVE_KERNEL_CUDA_CORE, RVE_KERNEL_TENSOR) as
+ * rve_autotune_batch does, on the n sample states, and keeps, of the pairs
+ * within 6 % of the fastest, the smallest batch (then the faster kernel):
+ * later calls with options.batch == 0 and options.operator_kernel ==
+ * RVE_KERNEL_AUTO use that pair for this mesh.  rates (optional,
+ * [n_kernel][n_batch]) receives homogenisations per second of each pair.
+ * The tensor kernel applies to the mechanics at p = 2, 3 in MIXED precision;
+ * elsewhere both candidates run the same kernel. */
+int rve_autotune_schedule(rve_ctx ctx, rve_mesh m, int64_t n, const double* T_C, const double* c_wt,
+                          const double* t_h, const int32_t* batches, int n_batch, const int32_t* kernels,
+                          int n_kernel, int32_t* best_batch, int32_t* best_kernel, double* rates);
 
 /* ------------------------------------------------------- learned surrogate
  * No counterpart in the paper: an ensemble of MLPs (8 features -> 4 x 256

@@ -24,6 +24,7 @@ ERRORS = {
 BC_DIRICHLET, BC_PERIODIC, BC_NEUMANN = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 MODE_PCG = 0
+KERNEL_AUTO, KERNEL_CUDA_CORE, KERNEL_TENSOR = 0, 1, 2
 
 
 class RveError(RuntimeError):
@@ -151,6 +152,9 @@ _SIGS = {
     "rve_homogenise_weak": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(Stats)]),
     "rve_partition_blocks": (C.c_int, [C.c_int64, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "rve_autotune_schedule": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32), C.c_void_p]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
     "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
@@ -248,7 +252,7 @@ class Context:
 
     def __init__(self, precision=PREC_FP64, rtol=1e-10, max_iter=20000, inner_rtol=1e-6,
                  max_refine=4, check_every=16, batch=0, stream=None, device=0, profile=False,
-                 warm_start=2, transport_once=False):
+                 warm_start=2, transport_once=False, operator_kernel=KERNEL_AUTO):
         lib = load_library()
         o = default_options()
         o.device, o.precision, o.rtol, o.max_iter = device, precision, rtol, max_iter
@@ -257,6 +261,7 @@ class Context:
         o.profile = int(profile)
         o.warm_start = (2 if warm_start else 0) if isinstance(warm_start, bool) else int(warm_start)
         o.transport_once = int(transport_once)
+        o.operator_kernel = int(operator_kernel)
         h = C.c_void_p()
         _check(lib.rve_create(C.byref(h), C.byref(o)), "rve_create")
         self.h = h
@@ -536,6 +541,23 @@ class Mesh:
                                                 _ptr(cand), len(cand), C.byref(best), _ptr(rates)),
                "rve_autotune_batch")
         return int(best.value), {int(b): float(r) for b, r in zip(cand, rates)}
+
+    def autotune_schedule(self, T_C, c_wt, t_h, batches, kernels=(KERNEL_CUDA_CORE, KERNEL_TENSOR)):
+        """Time (operator kernel, batch size) pairs on sample states of this mesh and keep
+        the choice for later batched calls; returns (batch, kernel, {(kernel, batch): rate})."""
+        T = np.ascontiguousarray(T_C, np.float64)
+        cw = np.ascontiguousarray(c_wt, np.float64)
+        th = np.ascontiguousarray(t_h, np.float64)
+        bc = np.ascontiguousarray(batches, np.int32)
+        kc = np.ascontiguousarray(kernels, np.int32)
+        rates = np.zeros(len(bc) * len(kc))
+        bb, bk = C.c_int32(0), C.c_int32(0)
+        _check(self.ctx.lib.rve_autotune_schedule(self.ctx.h, self.h, len(T), _ptr(T), _ptr(cw), _ptr(th), _ptr(bc),
+                                                  len(bc), _ptr(kc), len(kc), C.byref(bb), C.byref(bk), _ptr(rates)),
+               "rve_autotune_schedule")
+        rr = rates.reshape(len(kc), len(bc))
+        return int(bb.value), int(bk.value), {(int(k), int(b)): float(rr[i, j]) for i, k in enumerate(kc)
+                                              for j, b in enumerate(bc)}
 
     def homogenise_weak(self):
         """(sigma-route tensors C, K, D via the multipliers, energy-form C, K, D)."""

@@ -479,7 +479,9 @@ struct Solver {
         // counts follow the set of columns still iterating
         const bool prof = m->ctx->opt.profile != 0;
         // FP32 inner solve of the mechanics at p = 2, 3: the tensor-core operator
-        const bool use_tc = sizeof(T) == 4 && operator_tc_supported(m->p, f.nc) && m->ctx->opt.operator_kernel != 1;
+        int kern = m->ctx->opt.operator_kernel;
+        if (kern == RVE_KERNEL_AUTO) kern = m->tuned_kernel != 0 ? m->tuned_kernel : RVE_KERNEL_CUDA_CORE;
+        const bool use_tc = sizeof(T) == 4 && operator_tc_supported(m->p, f.nc) && kern == RVE_KERNEL_TENSOR;
         if (use_tc) RVE_TRY(ensure_element_matrices(m, s));
         ColState cs = cs64;
         RVE_CUDA(cudaMemcpyAsync(const_cast<double*>(cs.tol), &tol, sizeof(double), cudaMemcpyHostToDevice, s));
@@ -2090,6 +2092,60 @@ int rve_autotune_batch(rve_ctx c, rve_mesh m, int64_t n, const double* T_C, cons
     }
     m->tuned_batch = bestB;
     *best = bestB;
+    return RVE_OK;
+}
+
+int rve_autotune_schedule(rve_ctx c, rve_mesh m, int64_t n, const double* T_C, const double* c_wt,
+                          const double* t_h, const int32_t* batches, int n_batch, const int32_t* kernels,
+                          int n_kernel, int32_t* best_batch, int32_t* best_kernel, double* rates) {
+    RVE_TRY(check_ctx(c));
+    if (!m || n <= 0 || !T_C || !c_wt || !t_h || !best_batch || !best_kernel || n_batch < 1 || !batches ||
+        n_kernel < 1 || !kernels) {
+        set_error("rve_autotune_schedule: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    for (int k = 0; k < n_kernel; ++k)
+        if (kernels[k] != RVE_KERNEL_CUDA_CORE && kernels[k] != RVE_KERNEL_TENSOR) {
+            set_error("rve_autotune_schedule: kernel candidates are RVE_KERNEL_CUDA_CORE or RVE_KERNEL_TENSOR");
+            return RVE_ERR_INVALID_ARGUMENT;
+        }
+    const int saved = c->opt.operator_kernel;
+    std::vector<double> r((size_t)n_batch, 0.0), all((size_t)n_batch * n_kernel, 0.0);
+    int rc = RVE_OK;
+    for (int k = 0; k < n_kernel; ++k) {
+        c->opt.operator_kernel = kernels[k];
+        int32_t b = 0;
+        rc = rve_autotune_batch(c, m, n, T_C, c_wt, t_h, batches, n_batch, &b, r.data());
+        if (rc != RVE_OK) break;
+        for (int j = 0; j < n_batch; ++j) all[(size_t)k * n_batch + j] = r[j];
+    }
+    c->opt.operator_kernel = saved;
+    if (rc != RVE_OK) return rc;
+    if (rates) std::memcpy(rates, all.data(), all.size() * sizeof(double));
+    // as the batch tuner: of the pairs within 6 % of the best rate, the smallest
+    // batch, and of those the faster kernel
+    double top = 0;
+    for (double v : all) top = std::max(top, v);
+    int bk = -1, bb = 0;
+    double bv = 0;
+    for (int k = 0; k < n_kernel; ++k)
+        for (int j = 0; j < n_batch; ++j) {
+            const double v = all[(size_t)k * n_batch + j];
+            if (!(v > 0) || v < 0.94 * top) continue;
+            if (bk < 0 || batches[j] < bb || (batches[j] == bb && v > bv)) {
+                bk = k;
+                bb = batches[j];
+                bv = v;
+            }
+        }
+    if (bk < 0) {
+        set_error("rve_autotune_schedule: no candidate converged");
+        return RVE_ERR_NOT_CONVERGED;
+    }
+    m->tuned_batch = bb;
+    m->tuned_kernel = kernels[bk];
+    *best_batch = bb;
+    *best_kernel = kernels[bk];
     return RVE_OK;
 }
 

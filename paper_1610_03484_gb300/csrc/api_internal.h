@@ -189,6 +189,7 @@ struct rve_mesh_s {
     rve::FieldDev mech, scal;
     bool have_materials = false;
     int tuned_batch = 0;   // batch size chosen by rve_autotune_batch (0: the built-in rule)
+    int tuned_kernel = 0;  // operator kernel chosen by rve_autotune_schedule (0: not tuned)
     // batched call: the scalar-field solution of this mesh (independent of the
     // degradation state), formed by the call's first batch of the mesh
     bool scal_cached = false;

@@ -43,7 +43,21 @@ struct TcShape {
     static constexpr int TILE = NP * NP * 4;         // bytes of one B tile
     static constexpr int ATOM = NP * 128;            // bytes of one 32-wide K atom
     static constexpr uint32_t TCOLS = 3 * NP <= 128 ? 128 : 256;   // A_hi, A_lo, D
-    static constexpr int CTAS_PER_SM = TCOLS == 128 ? 4 : 2;
+    // operand prefetch ring depth and resident CTAs per SM (shared memory bound)
+    static constexpr int STAGES = 3;
+    static constexpr int CTAS_PER_SM = P == 2 ? 3 : 1;
+    static constexpr int KE_BYTES = PACKP * 4;            // one packed element matrix
+    static constexpr int XS_BYTES = N * 128 * 4;          // one element's values, 128 column slots
+    // shared-memory layout (byte offsets from a 1024-aligned base)
+    static constexpr int OFF_BHI = 0;
+    static constexpr int OFF_BLO = TILE;
+    static constexpr int OFF_KE = 2 * TILE;
+    static constexpr int OFF_XS = OFF_KE + STAGES * KE_BYTES;
+    static constexpr int OFF_OFFS = OFF_XS + STAGES * XS_BYTES;
+    static constexpr int OFF_ED = OFF_OFFS + (PACK * 4 + 15) / 16 * 16;
+    static constexpr int OFF_PH = OFF_ED + (STAGES * NE * 4 + 15) / 16 * 16;
+    static constexpr int OFF_BAR = OFF_PH + 16;
+    static constexpr int BYTES = OFF_BAR + 32;
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -131,6 +145,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr)
         : "memory");
 }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -222,21 +242,66 @@ struct TcView {
 constexpr uint64_t WAIT_NS = 1000000000ull;   // 1 s: one MMA group takes microseconds
 constexpr int WAIT_POLLS = 1 << 26;
 
+template <int NE>
+__device__ __forceinline__ void tc_load_ed(const TcView& v, int64_t e, int64_t e1, int (&ed)[NE]) {
+#pragma unroll
+    for (int j = 0; j < NE; ++j) ed[j] = e < e1 ? __ldg(v.edofs + e * NE + j) : 0;
+}
+
+// Operands of element e into ring stage s: the packed matrix and this thread's
+// column of the gathered values; one cp.async group per call (empty past the
+// chunk end).  Each thread copies exactly the packed entries it expands later
+// (q = t + 128 k) and the values it reads, so its own cp.async wait covers them.
+template <int P>
+__device__ __forceinline__ void tc_issue_loads(const TcView& v, const float* __restrict__ x, int64_t e, int64_t e1,
+                                               int s, const int (&ed)[TcShape<P>::NE], uint32_t ke_s0,
+                                               uint32_t xs_s0, int32_t* ed_ring, uint8_t* ph_ring, bool live,
+                                               int col, int ncols, int t) {
+    using S = TcShape<P>;
+    if (e < e1) {
+        const float* src = v.ke + e * S::PACKP;
+        for (int q = t; q < S::PACK; q += 128) cp_async4(ke_s0 + s * S::KE_BYTES + q * 4, src + q);
+        const uint32_t xs = xs_s0 + s * S::XS_BYTES;
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < S::N; ++q)
+                cp_async4(xs + (q * 128 + t) * 4, x + ((int64_t)ed[q / 3] * 3 + q % 3) * ncols + col);
+        }
+        if (t == 0) {
+#pragma unroll
+            for (int j = 0; j < S::NE; ++j) ed_ring[s * S::NE + j] = ed[j];
+            ph_ring[s] = v.phase[e];
+        }
+    }
+    cp_async_commit();
+}
+
+// One CTA of 128 threads: thread t owns column slot t (TMEM lane t) of a
+// 128-column tile and walks a contiguous chunk of elements.  Per element: the
+// B tiles are expanded from the packed matrix, the A operand is written to TMEM
+// from the gathered values, one thread issues the 3 x KS MMAs, one lane per warp
+// waits for their completion and every thread scatters its lane of the product.  The
+// operands of the next STAGES elements (packed matrix, this column's gathered
+// values) stream into a shared-memory ring with cp.async while the current one
+// is multiplied, so the per-element chain sees no global-memory latency.
 template <int P>
 __global__ void __launch_bounds__(128, TcShape<P>::CTAS_PER_SM)
     k_operator_tc(TcView v, const float* __restrict__ x, float* __restrict__ y, double* __restrict__ epart,
                   const int32_t* __restrict__ active, int ncols, const int32_t* __restrict__ list,
                   const int32_t* __restrict__ n_list, int nby_total, int32_t* __restrict__ err) {
     using S = TcShape<P>;
-    constexpr int NE = S::NE, N = S::N, NP = S::NP;
+    constexpr int NE = S::NE, N = S::N, NP = S::NP, ST = S::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t* Bhi = base;
-    uint8_t* Blo = base + S::TILE;
-    uint16_t* pairs = reinterpret_cast<uint16_t*>(base + 2 * S::TILE);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * S::TILE + ((S::PACK * 2 + 15) / 16) * 16);
+    uint8_t* Bhi = base + S::OFF_BHI;
+    uint8_t* Blo = base + S::OFF_BLO;
+    uint32_t* offs = reinterpret_cast<uint32_t*>(base + S::OFF_OFFS);   // swizzled (i,j) | (j,i) << 16
+    int32_t* ed_ring = reinterpret_cast<int32_t*>(base + S::OFF_ED);
+    uint8_t* ph_ring = base + S::OFF_PH;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + S::OFF_BAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const uint32_t ke_s0 = smem_u32(base + S::OFF_KE), xs_s0 = smem_u32(base + S::OFF_XS);
 
     const int t = threadIdx.x, warp = t >> 5;
     const int n_act = list ? *n_list : ncols;
@@ -251,9 +316,12 @@ __global__ void __launch_bounds__(128, TcShape<P>::CTAS_PER_SM)
     const float sc0 = live ? v.scale[col * 2] : 0.f, sc1 = live ? v.scale[col * 2 + 1] : 0.f;
     const int64_t e0 = v.nt * blockIdx.y / gridDim.y, e1 = v.nt * (blockIdx.y + 1) / gridDim.y;
 
-    // setup: packed-index table, zero B tiles (the padding rows and columns stay
-    // zero), the MMA completion barrier, tensor memory
-    for (int q = t; q < S::PACK; q += 128) pairs[q] = v.pairs[q];
+    // setup: swizzled offsets of the packed entries, zero B tiles (the padding
+    // rows and columns stay zero), the MMA completion barrier, tensor memory
+    for (int q = t; q < S::PACK; q += 128) {
+        const int i = v.pairs[q] >> 8, j = v.pairs[q] & 255;
+        offs[q] = sw128_offset<NP>(i, j) | (sw128_offset<NP>(j, i) << 16);
+    }
     for (int w = t; w < 2 * S::TILE / 16; w += 128) reinterpret_cast<float4*>(base)[w] = make_float4(0, 0, 0, 0);
     if (t == 0) {
         mbar_init(smem_u32(bar), 1);
@@ -273,44 +341,59 @@ __global__ void __launch_bounds__(128, TcShape<P>::CTAS_PER_SM)
     // kind::tf32, D FP32, A and B TF32, both K-major, N = NP, M = 128
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) | ((128u >> 4) << 24);
     const uint32_t bar_a = smem_u32(bar);
+
+    // operand prefetch: element e into ring stage s (one cp.async group per call,
+    // empty past the chunk), its DOF indices from registers
+    int ed_next[NE];
+    tc_load_ed<NE>(v, e0, e1, ed_next);
+#pragma unroll
+    for (int k = 0; k < ST; ++k) {
+        tc_issue_loads<P>(v, x, e0 + k, e1, k, ed_next, ke_s0, xs_s0, ed_ring, ph_ring, live, col, ncols, t);
+        tc_load_ed<NE>(v, e0 + k + 1, e1, ed_next);
+    }
+    __syncthreads();   // the ring's index entries of the first stages
+
     float esum = 0.f, ecomp = 0.f;   // compensated energy sum of this column
     uint32_t parity = 0;
     bool issued_pending = false, local_abort = false;
-
+    int s = 0;
     for (int64_t e = e0; e < e1; ++e) {
-        const int32_t* ed = v.edofs + e * NE;
+        // this thread's copies of element e have landed; the ring's index entries were
+        // written at least one CTA barrier ago (before the MMA issue of an earlier element)
+        cp_async_wait<ST - 1>();
+        int ed[NE];
+#pragma unroll
+        for (int j = 0; j < NE; ++j) ed[j] = ed_ring[s * NE + j];
+        const float sc = ph_ring[s] ? sc1 : sc0;
         // after a timed-out wait this thread writes no operand (an MMA may still read them)
         if (!local_abort) {
-        // ---- B: K_e expanded into the swizzled tiles, split into TF32 high and low parts
-        const float* ke = v.ke + e * S::PACKP;
-        for (int q = t; q < S::PACK; q += 128) {
-            const float val = __ldg(ke + q);
-            const uint32_t h = to_tf32(val);
-            const uint32_t l = to_tf32(val - __uint_as_float(h));
-            const int i = pairs[q] >> 8, j = pairs[q] & 255;
-            const uint32_t o1 = sw128_offset<NP>(i, j), o2 = sw128_offset<NP>(j, i);
-            *reinterpret_cast<uint32_t*>(Bhi + o1) = h;
-            *reinterpret_cast<uint32_t*>(Blo + o1) = l;
-            if (i != j) {
+            // ---- B: K_e expanded into the swizzled tiles, split into TF32 high and low parts
+            const float* kes = reinterpret_cast<const float*>(base + S::OFF_KE + s * S::KE_BYTES);
+            for (int q = t; q < S::PACK; q += 128) {
+                const float val = kes[q];
+                const uint32_t h = to_tf32(val);
+                const uint32_t l = to_tf32(val - __uint_as_float(h));
+                const uint32_t o = offs[q], o1 = o & 0xFFFFu, o2 = o >> 16;
+                *reinterpret_cast<uint32_t*>(Bhi + o1) = h;
+                *reinterpret_cast<uint32_t*>(Blo + o1) = l;
                 *reinterpret_cast<uint32_t*>(Bhi + o2) = h;
                 *reinterpret_cast<uint32_t*>(Blo + o2) = l;
             }
-        }
-        // ---- A: this column's element vector into TMEM lane t, high and low parts
+            // ---- A: this column's element vector into TMEM lane t, high and low parts
+            const float* xs = reinterpret_cast<const float*>(base + S::OFF_XS + s * S::XS_BYTES);
 #pragma unroll
-        for (int ch = 0; ch < NP / 16; ++ch) {
-            uint32_t hv[16], lv[16];
+            for (int ch = 0; ch < NP / 16; ++ch) {
+                uint32_t hv[16], lv[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int q = ch * 16 + u;
-                float xv = 0.f;
-                if (q < N && live) xv = x[((int64_t)__ldg(ed + q / 3) * 3 + q % 3) * ncols + col];
-                hv[u] = to_tf32(xv);
-                lv[u] = to_tf32(xv - __uint_as_float(hv[u]));
+                for (int u = 0; u < 16; ++u) {
+                    const int q = ch * 16 + u;
+                    const float xv = (q < N && live) ? xs[q * 128 + t] : 0.f;
+                    hv[u] = to_tf32(xv);
+                    lv[u] = to_tf32(xv - __uint_as_float(hv[u]));
+                }
+                tmem_st16(tAh + lane + ch * 16, hv);
+                tmem_st16(tAl + lane + ch * 16, lv);
             }
-            tmem_st16(tAh + lane + ch * 16, hv);
-            tmem_st16(tAl + lane + ch * 16, lv);
-        }
         }
         tmem_wait_st();
         fence_async_smem();
@@ -332,7 +415,12 @@ __global__ void __launch_bounds__(128, TcShape<P>::CTAS_PER_SM)
             tc_commit(bar_a);
         }
         issued_pending = true;
-        const bool ok = mbar_wait_bounded(bar_a, parity, WAIT_NS, WAIT_POLLS);
+        // one lane per warp polls the barrier; the others wait at the warp barrier
+        bool ok = true;
+        if ((t & 31) == 0) ok = mbar_wait_bounded(bar_a, parity, WAIT_NS, WAIT_POLLS);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        const int s_cur = s;
+        s = s + 1 == ST ? 0 : s + 1;
         if (!ok) {
             if (err) atomicOr(err, 4);
             *abort_flag = 1;
@@ -342,15 +430,14 @@ __global__ void __launch_bounds__(128, TcShape<P>::CTAS_PER_SM)
         issued_pending = false;
         parity ^= 1u;
         tc_fence_after();
-        // ---- epilogue: y += s K_e x_e for this column, energy s x_e . K_e x_e
-        const float sc = __ldg(v.phase + e) ? sc1 : sc0;
+        // ---- epilogue: y += s K_e x_e for this column, energy s x_e . K_e x_e (x_e
+        // from the ring stage, still this element's)
+        const float* xs = reinterpret_cast<const float*>(base + S::OFF_XS + s_cur * S::XS_BYTES);
         float en = 0.f;
 #pragma unroll
         for (int ch = 0; ch < NP / 16; ++ch) {
-            uint32_t dv[16], ah[16], al[16];
+            uint32_t dv[16];
             tmem_ld16(tD + lane + ch * 16, dv);
-            tmem_ld16(tAh + lane + ch * 16, ah);
-            tmem_ld16(tAl + lane + ch * 16, al);
             tmem_wait_ld();
             if (live) {
 #pragma unroll
@@ -358,8 +445,8 @@ __global__ void __launch_bounds__(128, TcShape<P>::CTAS_PER_SM)
                     const int q = ch * 16 + u;
                     if (q < N) {
                         const float yv = __uint_as_float(dv[u]);
-                        en = fmaf(__uint_as_float(ah[u]) + __uint_as_float(al[u]), yv, en);
-                        atomicAdd(y + ((int64_t)__ldg(ed + q / 3) * 3 + q % 3) * ncols + col, sc * yv);
+                        en = fmaf(xs[q * 128 + t], yv, en);
+                        atomicAdd(y + ((int64_t)ed[q / 3] * 3 + q % 3) * ncols + col, sc * yv);
                     }
                 }
             }
@@ -371,8 +458,16 @@ __global__ void __launch_bounds__(128, TcShape<P>::CTAS_PER_SM)
             esum = tk;
         }
         tc_fence_before();
+        // ---- refill the consumed ring stage with the element STAGES ahead (its
+        // last reader, this thread's energy sum, is done; the packed entries and
+        // gathered values of a thread are its own copies; the shared index
+        // entries are next read behind the MMA-issue barrier of a later element)
+        tc_issue_loads<P>(v, x, e + ST, e1, s_cur, ed_next, ke_s0, xs_s0, ed_ring, ph_ring, live, col, ncols, t);
+        tc_load_ed<NE>(v, e + ST + 1, e1, ed_next);
     }
-    // teardown: an MMA still in flight after a timeout gets one more bounded wait
+    // teardown: copies still in flight land before the CTA exits; an MMA still in
+    // flight after a timeout gets one more bounded wait
+    cp_async_wait<0>();
     tc_fence_before();
     __syncthreads();
     if (t == 0 && *abort_flag && issued_pending) mbar_wait_bounded(bar_a, parity, WAIT_NS, WAIT_POLLS);
@@ -392,8 +487,8 @@ __global__ void __launch_bounds__(128, TcShape<P>::CTAS_PER_SM)
 template <int P>
 constexpr size_t tc_smem_bytes() {
     using S = TcShape<P>;
-    const size_t used = 1024 + 2 * (size_t)S::TILE + ((S::PACK * 2 + 15) / 16) * 16 + 64;
-    // pad so that no more CTAs fit on an SM than its tensor memory holds
+    const size_t used = 1024 + (size_t)S::BYTES;
+    // pad so that no more CTAs fit on an SM than intended (tensor memory and registers)
     const size_t cap = (size_t)(232448 / (S::CTAS_PER_SM + 1)) + 1024;
     return used > cap ? used : cap;
 }

@@ -1,6 +1,6 @@
 """Batched homogenisation of a single RVE class, for profiling.
 
-    python -m paper_1610_03484_gb300.profile_batch 32,32,10 2 8 [n_points] [rtol] [calls] [profile]
+    python -m paper_1610_03484_gb300.profile_batch 32,32,10 2 8 [n_points] [rtol] [calls] [profile] [kernel]
 
 loads the plain-weave RVE on the given grid at order p, periodic BC, nominal
 constituents, and runs macro_update_gauss_points `calls` times (default 1) on the
@@ -10,7 +10,10 @@ more than one batch the later batches are warm-started, as in the batched
 workload; the first call also forms the per-mesh caches.  With profile = 1 the
 PCG iterations are launched one by one from the host (the context's profile
 mode) instead of as the device-side graph loop, so that a profiler that does not
-follow kernels inside conditional graph nodes sees every launch.
+follow kernels inside conditional graph nodes sees every launch.  kernel selects
+the operator of the FP32 inner solve: 0 automatic (the matrix-free CUDA-core
+kernel unless a schedule was tuned), 1 the matrix-free CUDA-core kernel, 2 the
+tensor-core kernel (p = 2, 3).
 """
 import os
 import sys
@@ -32,8 +35,9 @@ def main(argv):
     rtol = float(argv[5]) if len(argv) > 5 else 1e-8
     calls = int(argv[6]) if len(argv) > 6 else 1
     profile = bool(int(argv[7])) if len(argv) > 7 else False
+    kernel = int(argv[8]) if len(argv) > 8 else rve.KERNEL_AUTO
     ctx = rve.Context(precision=rve.PREC_MIXED, rtol=rtol, inner_rtol=min(1e-5, rtol), batch=B,
-                      profile=profile)
+                      profile=profile, operator_kernel=kernel)
     xyz, tets, ph, tg = ri.weave_rve(*grid)
     m = ctx.mesh_load(xyz, tets, p, ph, tg)
     m.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)

@@ -130,3 +130,52 @@ def test_meshes_solved_concurrently_match_separate_calls(rve):
         Co, Ko, Do = fem.homogenise(xyz, tets, grid, p, 1, D, K, Dd)
         assert rel(Ca[g], Co) < 1e-6
         assert rel(Ka[g], Ko) < 1e-6
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_every_schedule_matches_oracle_and_the_tuned_one_is_used(rve, p):
+    """Each (operator kernel, batch size) schedule the tuner can choose gives the
+    oracle's tensors at the mixed-precision bound (1e-6); the tuner's choice is
+    kept for the mesh and used by the next batched call."""
+    grid = (6, 6, 4)
+    xyz, tets, phase, tangent = ri.weave_rve(*grid)
+    Ts, cs, ts, _, _ = ri.gauss_point_states(24, seed=31)
+    T, c, t, _, _ = ri.gauss_point_states(16, seed=32)
+    w = [float(mt.one_minus_omega(T[g], c[g], t[g])) for g in (0, 15)]
+    oracle = {}
+    for g, wg in zip((0, 15), w):
+        m = ri.MatrixProps(E=ri.NOMINAL_MATRIX.E * wg, nu=ri.NOMINAL_MATRIX.nu, k=ri.NOMINAL_MATRIX.k,
+                           d=ri.NOMINAL_MATRIX.d)
+        D, K, Dd = mt.element_tensors(phase, tangent, m, ri.NOMINAL_YARN)
+        oracle[g] = fem.homogenise(xyz, tets, grid, p, 1, D, K, Dd)
+    results = {}
+    for kern in (rve.KERNEL_CUDA_CORE, rve.KERNEL_TENSOR):
+        for batch in (4, 8):
+            with rve.Context(precision=rve.PREC_MIXED, rtol=1e-8, inner_rtol=1e-6, batch=batch,
+                             operator_kernel=kern) as ctx:
+                mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
+                mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+                mesh.set_bc(1)
+                Cg, Kg, Dg, st, _, _ = ctx.macro_update([mesh], T, c, t, np.zeros(16, np.int32))
+                mesh.free()
+            assert (st == 0).all()
+            results[(kern, batch)] = Cg
+            for g in (0, 15):
+                Co, Ko, Do = oracle[g]
+                assert rel(Cg[g], Co) < 1e-6, (kern, batch, g)
+                assert rel(Kg[g], Ko) < 1e-6
+                assert rel(Dg[g], Do) < 1e-6
+    with rve.Context(precision=rve.PREC_MIXED, rtol=1e-8, inner_rtol=1e-6) as ctx:
+        mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
+        mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+        mesh.set_bc(1)
+        bb, bk, rates = mesh.autotune_schedule(Ts, cs, ts, [4, 8])
+        assert bb in (4, 8) and bk in (rve.KERNEL_CUDA_CORE, rve.KERNEL_TENSOR)
+        top = max(rates.values())
+        assert rates[(bk, bb)] >= 0.94 * top
+        assert all(b >= bb for (k, b), r in rates.items() if r >= 0.94 * top)
+        Ct, _, _, st, _, _ = ctx.macro_update([mesh], T, c, t, np.zeros(16, np.int32))
+        mesh.free()
+    assert (st == 0).all()
+    for g in range(16):
+        assert rel(Ct[g], results[(bk, bb)][g]) < 1e-8

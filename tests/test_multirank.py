@@ -19,16 +19,14 @@ def _worker(rank, world, port, out):
     os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
                        "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
     import bench
-    import rve_inputs as ri
     w, r, l = bench.dist_setup()
     assert (w, r, l) == (world, rank, rank)
-    T, c, t, size, p = ri.gauss_point_states(64, bench.SEED + r)
     t_local = 1.0 + r            # rank 1 is the slow one
     job = bench.max_over_ranks(t_local, w)
     units = bench.sum_over_ranks(64.0, w)
     bench.barrier(w)
     ref = bench.run_reference(type("A", (), {"steps": 1, "warmup": 0})(), w, r)
-    out.put((r, float(T[0]), job, units, ref is None))
+    out.put((r, job, units, ref is None))
     import torch.distributed as dist
     dist.destroy_process_group()
 
@@ -45,10 +43,9 @@ def test_two_gloo_ranks_weak_scaling():
     for pr in procs:
         pr.join(timeout=60)
         assert pr.exitcode == 0
-    (r0, T0, job0, u0, none0), (r1, T1, job1, u1, none1) = res
+    (r0, job0, u0, none0), (r1, job1, u1, none1) = res
     assert job0 == job1 == 2.0          # max over ranks
     assert u0 == u1 == 128.0            # whole-job units
-    assert T0 != T1                     # each rank draws its own points
     assert not none0 and none1          # the reference arm prints on rank 0 only
 
 
