@@ -499,14 +499,49 @@ def surrogate_leg(ctx, rve, n_points, rank):
         b = b.reshape(len(b), -1)
         return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
     err = max(rel(Cs[:ns], Cp).max(), rel(Ks[:ns], Kp).max(), rel(Ds[:ns], Dp).max())
+    mlp = mlp_inference(ctx, mesh, s, T, c, t, int(z["members"]))
     mesh.free()
     s.free()
     return {"value": n_points / sur_s, "unit": UNIT, "points": n_points, "seconds": sur_s,
             "fallback_frac": float(fb.mean()), "status_ok": int((st == 0).sum()), "gate_tau": SURROGATE_TAU,
-            "max_rel_err_vs_pcg": float(err), "err_sample": ns,
+            "max_rel_err_vs_pcg": float(err), "err_sample": ns, "mlp_inference": mlp,
             "pcg_same_class": {"value": ns / pcg_s, "unit": UNIT, "sample": ns},
             "workload": "24x24x8 p=2 plain weave, periodic; 4-member BF16 MLP ensemble (8 -> 4x256 SiLU -> 33), "
                         "spread gate -> batched mixed-precision PCG fallback; timed through the host-buffer call"}
+
+
+def mlp_inference(ctx, mesh, s, T, c, t, members):
+    """The ensemble's inference alone on the device (features in, tensors and
+    spread out, no host copies), timed with CUDA events: the BF16 tcgen05 GEMMs
+    of every member plus the head and ensemble kernels.  Flops count the four
+    layers' products of the useful rows (8 -> 256 padded to 64 inputs, 256 x 256
+    three times, 256 -> 33 padded to 64 outputs)."""
+    import torch
+    n = len(T)
+    feat = torch.tensor(ctx.features(mesh, T, c, t), dtype=torch.float64, device="cuda")
+    Cd = torch.empty((n, 36), dtype=torch.float64, device="cuda")
+    Kd = torch.empty((n, 9), dtype=torch.float64, device="cuda")
+    Dd = torch.empty((n, 9), dtype=torch.float64, device="cuda")
+    sp = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    args = (n, feat.data_ptr(), Cd.data_ptr(), Kd.data_ptr(), Dd.data_ptr(), sp.data_ptr())
+    s.predict_dev(*args)
+    torch.cuda.synchronize()
+    reps = 5
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        s.predict_dev(*args)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * n * members * (64 * 256 + 3 * 256 * 256 + 256 * 64)
+    pk, pk_kind = peaks()
+    tf = flops / (ms / 1e3) / 1e12
+    return {"points": n, "members": members, "ms": ms, "points_per_s": n / (ms / 1e3), "tflops": tf,
+            "peak_tflops": pk["bf16_tflops"], "peak_kind": f"{pk_kind} bf16 burst", "frac": tf / pk["bf16_tflops"],
+            "bound": "tensor"}
 
 
 # ------------------------------------------------------------ coupled macro leg

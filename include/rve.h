@@ -344,6 +344,13 @@ int rve_surrogate_gradients(rve_ctx ctx, rve_surrogate s, int member, int n, con
 int rve_surrogate_predict(rve_ctx ctx, rve_surrogate s, int64_t n, const double* feat, double* C,
                           double* K, double* D, double* spread);
 
+/* The same on the device: feat_dev [n][8], outputs C_dev [n][36], K_dev [n][9],
+ * D_dev [n][9] (SI units) and spread_dev [n], all on the context's device;
+ * enqueued on the context's stream (the caller synchronises).  Uses a
+ * library-owned work buffer of n x 54 doubles. */
+int rve_surrogate_predict_dev(rve_ctx ctx, rve_surrogate s, int64_t n, const double* feat_dev, double* C_dev,
+                              double* K_dev, double* D_dev, double* spread_dev);
+
 /* Save / load: a float array [52 + members * n_params] (feature mean and std,
  * output scales, reference tensor scales, then each member's FP32 weights and
  * biases layer by layer, weights [in][out]).  With buf NULL, get_params writes

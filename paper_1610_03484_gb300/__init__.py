@@ -155,6 +155,8 @@ _SIGS = {
     "rve_autotune_schedule": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int32),
                                         C.POINTER(C.c_int32), C.c_void_p]),
+    "rve_surrogate_predict_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p]),
     "macro_update_gauss_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
@@ -475,6 +477,12 @@ class Surrogate:
         _check(self.ctx.lib.rve_surrogate_predict(self.ctx.h, self.h, n, _ptr(feat), _ptr(Cc), _ptr(Kk), _ptr(Dd),
                                                   _ptr(sp)), "rve_surrogate_predict")
         return Cc, Kk, Dd, sp
+
+    def predict_dev(self, n: int, feat_dev: int, C_dev: int, K_dev: int, D_dev: int, spread_dev: int):
+        """Device-pointer inference (integer device addresses), on the context's stream."""
+        _check(self.ctx.lib.rve_surrogate_predict_dev(self.ctx.h, self.h, int(n), C.c_void_p(feat_dev),
+                                                      C.c_void_p(C_dev), C.c_void_p(K_dev), C.c_void_p(D_dev),
+                                                      C.c_void_p(spread_dev)), "rve_surrogate_predict_dev")
 
     def get_params(self) -> np.ndarray:
         n = C.c_int64()

@@ -5,10 +5,12 @@
 //   h_{l+1} = silu(h_l W_l + b_l), l = 0..3 (width 256), z = h_4 W_4 + b_4,
 //   L = tril(z) with softplus on the diagonal, tensor = L L^T (always SPD).
 // Weights and activations are BF16, every product accumulates in FP32 on the
-// tensor cores (mma.sync m16n8k16), master weights and Adam moments are FP32.
+// 5th-generation tensor cores (tcgen05.mma kind::f16, accumulator in tensor
+// memory), master weights and Adam moments are FP32.
 //
 // GEMM convention: C[M][N] = A[M][K] * B, with A row-major and B supplied as
-// Bt[N][K] row-major (K contiguous in both), M, N multiples of 64, K of 16.
+// Bt[N][K] row-major (K contiguous in both), M a multiple of 64, N 64 or a
+// multiple of 256, K a multiple of 64.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -25,14 +27,6 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 __device__ __forceinline__ float silu_f(float a) { return a / (1.f + __expf(-a)); }
 __device__ __forceinline__ float dsilu_f(float a) {
     const float s = 1.f / (1.f + __expf(-a));
@@ -41,73 +35,244 @@ __device__ __forceinline__ float dsilu_f(float a) {
 
 }  // namespace
 
-// Block tile 64 x 64, 4 warps (each 16 rows x 64 columns), K step 16.
-// epilogue: 0 = store FP32 only, 1 = bias + silu -> BF16 (pre-activation to zf if non-null),
-//           2 = bias, FP32 out, 3 = accumulate FP32 into Cf (C += A B)
-__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
-                                                   const __nv_bfloat16* __restrict__ Bt,
-                                                   const float* __restrict__ bias, int epilogue,
-                                                   __nv_bfloat16* __restrict__ Cb, float* __restrict__ Cf) {
-    __shared__ __nv_bfloat16 As[64][16 + 8];
-    __shared__ __nv_bfloat16 Bs[64][16 + 8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[8][4];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[i][r] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        // stage A and B tiles: 64 x 16 each, 128 threads x 8 elements
-        for (int i = threadIdx.x; i < 64 * 16; i += 128) {
-            const int r = i >> 4, c = i & 15;
-            As[r][c] = A[(int64_t)(m0 + r) * K + k0 + c];
-            Bs[r][c] = Bt[(int64_t)(n0 + r) * K + k0 + c];
-        }
-        __syncthreads();
-        uint32_t a[4];
-        const int ar = warp * 16 + g;
-        a[0] = pack_bf16(As[ar][2 * t], As[ar][2 * t + 1]);
-        a[1] = pack_bf16(As[ar + 8][2 * t], As[ar + 8][2 * t + 1]);
-        a[2] = pack_bf16(As[ar][2 * t + 8], As[ar][2 * t + 9]);
-        a[3] = pack_bf16(As[ar + 8][2 * t + 8], As[ar + 8][2 * t + 9]);
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            uint32_t b[2];
-            const int bn = nt * 8 + g;
-            b[0] = pack_bf16(Bs[bn][2 * t], Bs[bn][2 * t + 1]);
-            b[1] = pack_bf16(Bs[bn][2 * t + 8], Bs[bn][2 * t + 9]);
-            mma_bf16_16816(acc[nt], a, b);
-        }
-        __syncthreads();
+// ------------------------------------------------ tcgen05 GEMM (sm_103a)
+// C tile [128 rows x NT] = A [128 x K] * Bt [NT x K]^T on the 5th-generation tensor
+// cores: BF16 operands staged by cp.async into 128-byte-swizzled K-major shared
+// memory tiles (64 K values = 128 bytes per row), two K stages in flight, one
+// thread issuing kind::f16 MMAs (M = 128, N = NT, K = 16) into an FP32 TMEM
+// accumulator, thread t reading back row t for the epilogue.  Rows past M are
+// zero-filled on load and not stored.
+namespace {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gl_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool bar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait (1 s of the global timer, or a poll cap should the timer not advance)
+__device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity) {
+    if (bar_try(a, parity)) return true;
+    const uint64_t t0 = gl_ns();
+    for (int i = 0; i < (1 << 26); ++i) {
+        if (bar_try(a, parity)) return true;
+        if (gl_ns() - t0 > 1000000000ull) return false;
     }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int row = m0 + warp * 16 + g + (r >= 2 ? 8 : 0);
-            const int col = n0 + nt * 8 + 2 * t + (r & 1);
-            const int64_t o = (int64_t)row * N + col;
-            float v = acc[nt][r];
-            if (epilogue == 3) {
-                Cf[o] += v;
-                continue;
-            }
-            if (bias && epilogue != 0) v += bias[col];
-            if (epilogue == 1) {
-                if (Cf) Cf[o] = v;
-                Cb[o] = __float2bfloat16(silu_f(v));
-            } else {
-                Cf[o] = v;
-            }
-        }
+    return false;
+}
+__device__ __forceinline__ void cp16_zfill(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void mma_f16_tmem(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16x(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
 }
 
+__device__ int g_gemm_timeout;   // set when a bounded wait of the GEMM gave up
+
+}  // namespace
+
+// epilogue: 0 = store FP32 only, 1 = bias + silu -> BF16 (pre-activation to Cf if non-null),
+//           2 = bias, FP32 out, 3 = accumulate FP32 into Cf (C += A B)
+template <int NT>
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+                                                 const __nv_bfloat16* __restrict__ Bt,
+                                                 const float* __restrict__ bias, int epilogue,
+                                                 __nv_bfloat16* __restrict__ Cb, float* __restrict__ Cf) {
+    constexpr int A_BYTES = 128 * 128, B_BYTES = NT * 128, STAGE = A_BYTES + B_BYTES;
+    extern __shared__ uint8_t gsm_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * NT;
+    const int KB = K / 64;
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + 1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"((uint32_t)NT)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    // kind::f16, D FP32, A and B BF16, both K-major, N = NT, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
+    // one K step (64 values) of A and B into stage s: 16-byte chunks, chunk c of row r
+    // at r * 128 + ((c ^ (r mod 8)) << 4)
+    auto load_step = [&](int kb, int s) {
+        const uint32_t sa = smem_addr(base + s * STAGE), sb = sa + A_BYTES;
+        for (int i = t; i < 128 * 8; i += 128) {
+            const int r = i >> 3, c = i & 7;
+            const bool in = m0 + r < M;
+            const __nv_bfloat16* src = A + (int64_t)(in ? m0 + r : 0) * K + kb * 64 + c * 8;
+            cp16_zfill(sa + r * 128 + ((c ^ (r & 7)) << 4), src, in ? 16u : 0u);
+        }
+        for (int i = t; i < NT * 8; i += 128) {
+            const int r = i >> 3, c = i & 7;
+            cp16_zfill(sb + r * 128 + ((c ^ (r & 7)) << 4), Bt + (int64_t)(n0 + r) * K + kb * 64 + c * 8, 16u);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    bool ok = true;
+    load_step(0, 0);
+    for (int kb = 0; kb < KB && ok; ++kb) {
+        const int s = kb & 1;
+        if (kb + 1 < KB) {
+            // the stage of step kb + 1 was last read by the MMAs of step kb - 1
+            if (kb >= 1) {
+                bool w = true;
+                if ((t & 31) == 0) w = bar_wait(smem_addr(bar + ((kb + 1) & 1)), ((kb - 1) >> 1) & 1);
+                w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+                if (!w) {
+                    atomicOr(&g_gemm_timeout, 1);
+                    ok = false;
+                }
+            }
+            load_step(kb + 1, (kb + 1) & 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;
+        if (!ok) break;
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_addr(base + s * STAGE), sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_f16_tmem(tmem, desc_sw128(sa + kk * 32), desc_sw128(sb + kk * 32), idesc,
+                             (kb > 0 || kk > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(bar + s))
+                         : "memory");
+        }
+    }
+    // the last step's commit completes after every earlier MMA of the tile
+    if (ok) {
+        bool w = true;
+        if ((t & 31) == 0) w = bar_wait(smem_addr(bar + ((KB - 1) & 1)), ((KB - 1) >> 1) & 1);
+        w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+        if (!w) {
+            atomicOr(&g_gemm_timeout, 1);
+            ok = false;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + t;
+    const uint32_t lane = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+        uint32_t v[16];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                     "%12, %13, %14, %15}, [%16];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                       "=r"(v[14]), "=r"(v[15])
+                     : "r"(tmem + lane + c0)
+                     : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!ok || row >= M) continue;
+        const int col = n0 + c0;
+        const int64_t o = (int64_t)row * N + col;
+        float f[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) f[u] = __uint_as_float(v[u]);
+        if (epilogue == 3) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) Cf[o + u] += f[u];
+            continue;
+        }
+        if (bias && epilogue != 0)
+#pragma unroll
+            for (int u = 0; u < 16; ++u) f[u] += bias[col + u];
+        if (epilogue == 1) {
+            if (Cf)
+#pragma unroll
+                for (int u = 0; u < 16; u += 4)
+                    *reinterpret_cast<float4*>(Cf + o + u) = make_float4(f[u], f[u + 1], f[u + 2], f[u + 3]);
+            uint32_t pk[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                pk[u] = pack_bf16(__float2bfloat16(silu_f(f[2 * u])), __float2bfloat16(silu_f(f[2 * u + 1])));
+            *reinterpret_cast<uint4*>(Cb + o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(Cb + o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 16; u += 4)
+                *reinterpret_cast<float4*>(Cf + o + u) = make_float4(f[u], f[u + 1], f[u + 2], f[u + 3]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NT)
+                     : "memory");
+    }
+}
+
+template <int NT>
+static size_t gemm_smem() {
+    return 1024 + 2 * (size_t)(128 * 128 + NT * 128) + 64;
+}
+
+void gemm_tc_prepare() {
+    cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
+    cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<64>());
+}
+
+int gemm_tc_timed_out() {
+    int v = 0;
+    cudaMemcpyFromSymbol(&v, g_gemm_timeout, sizeof(int));
+    return v;
+}
+
+// M a multiple of 64 (rows past a 128-row tile are zero-filled), N 64 or a
+// multiple of 256, K a multiple of 64.
 void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, const float* bias,
                       int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s) {
-    dim3 grid(N / 64, M / 64);
-    k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, A, Bt, bias, epilogue, Cb, Cf);
+    if (N == 64) {
+        dim3 grid(1, (M + 127) / 128);
+        k_gemm_tc<64><<<grid, 128, gemm_smem<64>(), s>>>(M, N, K, A, Bt, bias, epilogue, Cb, Cf);
+    } else {
+        dim3 grid(N / 256, (M + 127) / 128);
+        k_gemm_tc<256><<<grid, 128, gemm_smem<256>(), s>>>(M, N, K, A, Bt, bias, epilogue, Cb, Cf);
+    }
 }
 
 // out[c][r] = in[r][c] (BF16), rows x cols
@@ -323,6 +488,27 @@ __global__ void k_ensemble(int n, int members, const double* __restrict__ T, dou
 
 void launch_ensemble(int n, int members, const double* T, double* Tm, double* spread, cudaStream_t s) {
     k_ensemble<<<(n + 127) / 128, 128, 0, s>>>(n, members, T, Tm, spread);
+}
+
+// Tm [n][54] (C 36, K 9, D 9 in the network's units) -> C [n][36], K [n][9], D [n][9] in SI units
+__global__ void k_split_tensors(int64_t n, const double* __restrict__ Tm, double rc, double rk, double rd,
+                                double* __restrict__ C, double* __restrict__ K, double* __restrict__ D) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * 54; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / 54;
+        const int c = (int)(i % 54);
+        const double v = Tm[i];
+        if (c < 36) C[r * 36 + c] = v * rc;
+        else if (c < 45) K[r * 9 + c - 36] = v * rk;
+        else D[r * 9 + c - 45] = v * rd;
+    }
+}
+
+void launch_split_tensors(int64_t n, const double* Tm, double rc, double rk, double rd, double* C, double* K,
+                          double* D, cudaStream_t s) {
+    int64_t b = (n * 54 + 255) / 256;
+    if (b > 8192) b = 8192;
+    if (b < 1) b = 1;
+    k_split_tensors<<<(unsigned)b, 256, 0, s>>>(n, Tm, rc, rk, rd, C, K, D);
 }
 
 }  // namespace rve

@@ -8,6 +8,10 @@
 
 namespace rve {
 
+// sets the GEMM kernels' shared-memory limit (once per device, before the first launch)
+void gemm_tc_prepare();
+// nonzero once a bounded wait inside the GEMM gave up (sticky for the process)
+int gemm_tc_timed_out();
 void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, const float* bias,
                       int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s);
 void launch_transpose_bf16(int rows, int cols, const __nv_bfloat16* in, __nv_bfloat16* out, cudaStream_t s);
@@ -22,6 +26,8 @@ void launch_adam_bias(int N, float* b, const float* g, float* m1, float* m2, flo
 void launch_features(int n, int M, int kin, const double* feat, const float* mean, const float* inv_std,
                      __nv_bfloat16* X, cudaStream_t s);
 void launch_head_tensors(int n, int noutp, const float* z, const uint8_t* diag, double* Te, cudaStream_t s);
+void launch_split_tensors(int64_t n, const double* Tm, double rc, double rk, double rd, double* C, double* K,
+                          double* D, cudaStream_t s);
 void launch_ensemble(int n, int members, const double* T, double* Tm, double* spread, cudaStream_t s);
 
 }  // namespace rve

@@ -181,6 +181,7 @@ int rve_surrogate_create(rve_ctx c, int members, uint64_t seed, rve_surrogate* o
         set_error("rve_surrogate_create: members must be 1..16");
         return RVE_ERR_INVALID_ARGUMENT;
     }
+    gemm_tc_prepare();
     auto* s = new rve_surrogate_s();
     s->ctx = c;
     s->members = members;
@@ -370,6 +371,10 @@ int rve_surrogate_train(rve_ctx c, rve_surrogate s, int64_t n, const double* fea
     RVE_CUDA(cudaGetLastError());
     if (loss_history) std::memcpy(loss_history, hist.data(), sizeof(double) * epochs);
     s->trained = true;
+    if (gemm_tc_timed_out()) {
+        set_error("a bounded wait inside the surrogate GEMM gave up");
+        return RVE_ERR_TIMEOUT;
+    }
     return RVE_OK;
 }
 
@@ -400,6 +405,10 @@ int rve_surrogate_gradients(rve_ctx c, rve_surrogate s, int member, int n, const
     RVE_CUDA(cudaMemcpyAsync(&l, s->loss.p, 4, cudaMemcpyDeviceToHost, st));
     RVE_CUDA(cudaStreamSynchronize(st));
     if (loss) *loss = l;
+    if (gemm_tc_timed_out()) {
+        set_error("a bounded wait inside the surrogate GEMM gave up");
+        return RVE_ERR_TIMEOUT;
+    }
     return RVE_OK;
 }
 
@@ -455,6 +464,28 @@ int rve_surrogate_predict(rve_ctx c, rve_surrogate s, int64_t n, const double* f
         for (int k = 0; k < 9; ++k) K[9 * i + k] = T[54 * i + 36 + k] * s->ref[1];
         for (int k = 0; k < 9; ++k) D[9 * i + k] = T[54 * i + 45 + k] * s->ref[2];
     }
+    if (gemm_tc_timed_out()) {
+        set_error("a bounded wait inside the surrogate GEMM gave up");
+        return RVE_ERR_TIMEOUT;
+    }
+    return RVE_OK;
+}
+
+int rve_surrogate_predict_dev(rve_ctx c, rve_surrogate s, int64_t n, const double* feat_dev, double* C_dev,
+                              double* K_dev, double* D_dev, double* spread_dev) {
+    RVE_TRY(check_ctx(c));
+    if (!s || n < 0 || (n > 0 && (!feat_dev || !C_dev || !K_dev || !D_dev || !spread_dev)))
+        return RVE_ERR_INVALID_ARGUMENT;
+    if (!s->trained) {
+        set_error("surrogate has not been trained or loaded");
+        return RVE_ERR_STATE;
+    }
+    if (n == 0) return RVE_OK;
+    RVE_TRY(s->Tm.ensure((size_t)n * 54 * 8));
+    RVE_TRY(predict_dev(s, n, feat_dev, s->Tm.as<double>(), spread_dev));
+    launch_split_tensors(n, s->Tm.as<double>(), s->ref[0], s->ref[1], s->ref[2], C_dev, K_dev, D_dev, c->stream);
+    c->launches++;
+    RVE_CUDA(cudaGetLastError());
     return RVE_OK;
 }
 
@@ -588,6 +619,10 @@ int macro_update_gauss_points_surrogate(rve_ctx c, const rve_mesh* meshes, const
     if (st) {
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st->kernel_launches = c->launches - l0;
+    }
+    if (gemm_tc_timed_out()) {
+        set_error("a bounded wait inside the surrogate GEMM gave up");
+        return RVE_ERR_TIMEOUT;
     }
     return rc;
 }
