@@ -484,6 +484,10 @@ struct Solver {
         const bool use_tc = sizeof(T) == 4 && operator_tc_supported(m->p, f.nc) && kern == RVE_KERNEL_TENSOR;
         if (use_tc) RVE_TRY(ensure_element_matrices(m, s));
         ColState cs = cs64;
+        // the operator of the iteration runs one wave of resident blocks; its energy
+        // partials (and the alpha reduction over them) have as many rows
+        Launch Lop = L;
+        Lop.nby_op = operator_grid_y<T>(m->p, f.nc, L, m->nt);
         RVE_CUDA(cudaMemcpyAsync(const_cast<double*>(cs.tol), &tol, sizeof(double), cudaMemcpyHostToDevice, s));
         RowView<T> rvw = rv<T>(scale);
         ElemView<T> evw = ev<T>(scale);
@@ -520,14 +524,16 @@ struct Solver {
         bool loop_ctl = false;
         cudaGraphConditionalHandle loop_handle = 0;
         cudaError_t tc_err = cudaSuccess;
-        auto iteration = [&](const Launch& Lx) {
+        auto iteration = [&](const Launch& Lx0) {
+            Launch Lx = Lx0;
+            Lx.nby_op = Lop.nby_op;
             evr(0, Lx.stream);
             if constexpr (sizeof(T) == 4) {
                 if (use_tc) {
                     const cudaError_t e = launch_operator_tc(
                         m->p, m->nt, m->d_edofs.as<int32_t>(), m->d_ke32.as<float>(), m->d_kepairs.as<uint16_t>(),
                         m->d_phase.as<uint8_t>(), evw.scale, p, q, m->epart.as<double>(), cs.active, ncols, cs.list,
-                        cs.n_list, Lx.nby, cs.flags, Lx.stream);
+                        cs.n_list, Lx.op_rows(), cs.flags, Lx.stream);
                     if (e != cudaSuccess) tc_err = e;
                 } else {
                     launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active, cs.list,
@@ -561,7 +567,7 @@ struct Solver {
             // reused while every captured parameter is unchanged (the tolerance
             // lives in device memory).
             struct Key {
-                int ncols, cpb, rows, nby, p, nc, m, max_iter, tc;
+                int ncols, cpb, rows, nby, nby_op, p, nc, m, max_iter, tc;
                 int64_t n_rows, n_sup, nt;
                 const void* ptr[19];
             } key;
@@ -570,6 +576,7 @@ struct Solver {
             key.cpb = L.cpb;
             key.rows = L.rows_per_block;
             key.nby = L.nby;
+            key.nby_op = Lop.nby_op;
             key.p = m->p;
             key.nc = f.nc;
             key.m = rvw.m;

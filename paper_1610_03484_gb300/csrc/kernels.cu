@@ -349,10 +349,29 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
 }
 
 template <typename T>
+int operator_grid_y(int p, int nc, const Launch& L, int64_t nt) {
+    const int threads = L.cpb * L.rows_per_block;
+    int per_sm = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define RVE_OCC_CASE(PP, NCC)                                                                           \
+    if (p == PP && nc == NCC)                                                                           \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_operator<PP, NCC, T, false>, threads, 0);
+    RVE_OCC_CASE(1, 3) RVE_OCC_CASE(2, 3) RVE_OCC_CASE(3, 3) RVE_OCC_CASE(1, 1) RVE_OCC_CASE(2, 1) RVE_OCC_CASE(3, 1)
+#undef RVE_OCC_CASE
+    if (e != cudaSuccess || per_sm < 1) return L.nby;
+    const int gx = L.ncols / L.cpb;
+    const int64_t want = (nt + L.rows_per_block - 1) / L.rows_per_block;
+    const int64_t wave = std::max<int64_t>(1, (int64_t)per_sm * sm_count() / gx);
+    return (int)std::max<int64_t>(1, std::min<int64_t>({want, wave, (int64_t)L.nby}));
+}
+template int operator_grid_y<float>(int, int, const Launch&, int64_t);
+template int operator_grid_y<double>(int, int, const Launch&, int64_t);
+
+template <typename T>
 void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
                      double* energy_partial, const Launch& L, const int32_t* active, const int32_t* list,
                      const int32_t* n_list) {
-    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+    dim3 grid(L.ncols / L.cpb, L.op_rows()), block(L.cpb * L.rows_per_block);
     if (grid.x != 1) list = n_list = nullptr;   // the list maps one block column
 #define RVE_OP_CASE(PP, NCC, MM)                                                                \
     if (p == PP && nc == NCC && macro == MM) {                                                  \
@@ -466,12 +485,29 @@ __device__ __forceinline__ void df_split(double v, float& h, float& l) {
     l = __double2float_rn(v - (double)h);
 }
 
-template <int P, int NC>
-__global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, const float* __restrict__ xh,
+// True when local function j (>= 4) has a nonzero table entry in modes [M0, M1).
+template <int P, int M0, int M1>
+__host__ __device__ constexpr bool df_group_touches(int j) {
+    constexpr int NE = Order<P>::NE, NM = Order<P>::NM;
+    for (int m = M0; m < M1; ++m)
+        for (int k = 0; k < 3; ++k)
+            if (basis_a<P, float>((k * NM + m) * NE + j) != 0.f) return true;
+    return false;
+}
+
+// The contribution of the reference-gradient modes [M0, M1) of every element: the
+// modes are independent until the scatter (the stress of mode m depends on mode m
+// alone), so the kernel runs once per group of modes and the groups' scatters
+// add up.  Fewer modes per pass keep the double-float state of a thread small
+// enough for two resident blocks per SM.
+template <int P, int NC, int M0, int M1>
+__global__ void __launch_bounds__(256, 2) k_residual_df(ElemView<float> ev, const float* __restrict__ xh,
                                                         const float* __restrict__ xl, double* __restrict__ r,
                                                         float* __restrict__ rlo, int ncols, int cpb) {
     constexpr int NE = Order<P>::NE;
     constexpr int NM = Order<P>::NM;
+    constexpr int G_ = M1 - M0;
+    constexpr bool HAS0 = M0 == 0;
     const int rows = blockDim.x / cpb;
     const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
     const int col = blockIdx.x * cpb + cl;
@@ -479,64 +515,59 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
     const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
     for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < ev.nt; e += (int64_t)gridDim.y * rows) {
         const int32_t* ed = ev.edofs + e * NE;
-        float Vh[NM][3][NC], Vl[NM][3][NC];
-        if (xh == nullptr) {   // macro load only
+        float Vh[G_][3][NC], Vl[G_][3][NC];
 #pragma unroll
-            for (int m = 0; m < NM; ++m)
+        for (int m = 0; m < G_; ++m)
 #pragma unroll
-                for (int k = 0; k < 3; ++k)
+            for (int k = 0; k < 3; ++k)
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) Vh[m][k][c] = Vl[m][k][c] = 0.f;
-        } else {
-            const int d0 = __ldg(ed);
-            float x0h[NC], x0l[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int64_t i0 = ((int64_t)d0 * NC + c) * ncols + col;
-                x0h[c] = -xh[i0];
-                x0l[c] = -xl[i0];
-            }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int dk = __ldg(ed + k + 1);
+                for (int c = 0; c < NC; ++c) Vh[m][k][c] = Vl[m][k][c] = 0.f;
+        if (xh != nullptr) {
+            if constexpr (HAS0) {
+                const int d0 = __ldg(ed);
+                float x0h[NC], x0l[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const int64_t ik = ((int64_t)dk * NC + c) * ncols + col;
-                    Vh[0][k][c] = xh[ik];
-                    Vl[0][k][c] = xl[ik];
-                    df_add(Vh[0][k][c], Vl[0][k][c], x0h[c], x0l[c]);
+                    const int64_t i0 = ((int64_t)d0 * NC + c) * ncols + col;
+                    x0h[c] = -xh[i0];
+                    x0l[c] = -xl[i0];
                 }
-            }
-#pragma unroll
-            for (int m = 1; m < NM; ++m)
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) Vh[m][k][c] = Vl[m][k][c] = 0.f;
-        }
-#pragma unroll
-        for (int j = 4; j < NE; ++j) {
-            if (xh == nullptr) break;
-            const int dj = __ldg(ed + j);
-            float vh[NC], vl[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int64_t ij = ((int64_t)dj * NC + c) * ncols + col;
-                vh[c] = xh[ij];
-                vl[c] = xl[ij];
-            }
-#pragma unroll
-            for (int m = 0; m < NM; ++m)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float a = basis_a<P, float>((k * NM + m) * NE + j);
-                    if (a != 0.f)
+                    const int dk = __ldg(ed + k + 1);
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) df_mac(Vh[m][k][c], Vl[m][k][c], a, vh[c], vl[c]);
+                    for (int c = 0; c < NC; ++c) {
+                        const int64_t ik = ((int64_t)dk * NC + c) * ncols + col;
+                        Vh[0][k][c] = xh[ik];
+                        Vl[0][k][c] = xl[ik];
+                        df_add(Vh[0][k][c], Vl[0][k][c], x0h[c], x0l[c]);
+                    }
                 }
+            }
+#pragma unroll
+            for (int j = 4; j < NE; ++j) {
+                if (!df_group_touches<P, M0, M1>(j)) continue;
+                const int dj = __ldg(ed + j);
+                float vh[NC], vl[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int64_t ij = ((int64_t)dj * NC + c) * ncols + col;
+                    vh[c] = xh[ij];
+                    vl[c] = xl[ij];
+                }
+#pragma unroll
+                for (int m = 0; m < G_; ++m)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float a = basis_a<P, float>((k * NM + M0 + m) * NE + j);
+                        if (a != 0.f)
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) df_mac(Vh[m][k][c], Vl[m][k][c], a, vh[c], vl[c]);
+                    }
+            }
         }
 #pragma unroll
-        for (int m = 0; m < NM; ++m)
+        for (int m = 0; m < G_; ++m)
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -552,7 +583,7 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
         for (int i = 0; i < NMAT; ++i)
             Dm[i] = sv * __ldg(ev.mat + e * (NC == 3 ? 21 : 12) + (NC == 3 ? 0 : 6 * field) + i);
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
+        for (int m = 0; m < G_; ++m) {
             float Hh[NC][3], Hl[NC][3];
 #pragma unroll
             for (int c = 0; c < NC; ++c)
@@ -562,19 +593,19 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
 #pragma unroll
                     for (int k = 0; k < 3; ++k) df_mac(Hh[c][l], Hl[c][l], G[3 * k + l], Vh[m][k][c], Vl[m][k][c]);
                 }
-            if (m == 0) {
-                if constexpr (NC == 3) {
-                    if (macro_id < 3) {
-                        df_add(Hh[macro_id][macro_id], Hl[macro_id][macro_id], 1.f, 0.f);
-                    } else {
-                        const int a = macro_id == 3 ? 0 : (macro_id == 4 ? 1 : 2);
-                        const int b = macro_id == 3 ? 1 : (macro_id == 4 ? 2 : 0);
-                        df_add(Hh[a][b], Hl[a][b], 0.5f, 0.f);
-                        df_add(Hh[b][a], Hl[b][a], 0.5f, 0.f);
-                    }
-                } else {
-                    df_add(Hh[0][macro_id], Hl[0][macro_id], 1.f, 0.f);
-                }
+            if (HAS0 && m == 0) {
+                // the column's unit macro gradient, added entry by entry with
+                // compile-time indices (keeps H in registers)
+                const int ma = NC == 3 ? (macro_id < 3 ? macro_id : (macro_id == 3 ? 0 : (macro_id == 4 ? 1 : 2))) : 0;
+                const int mb = NC == 3 ? (macro_id < 3 ? macro_id : (macro_id == 3 ? 1 : (macro_id == 4 ? 2 : 0)))
+                                       : macro_id;
+                const float v = (NC == 3 && macro_id >= 3) ? 0.5f : 1.f;
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int l = 0; l < 3; ++l)
+                        if ((c == ma && l == mb) || (NC == 3 && macro_id >= 3 && c == mb && l == ma))
+                            df_add(Hh[c][l], Hl[c][l], v, 0.f);
             }
             float Sh[NC][3], Sl[NC][3];
             if constexpr (NC == 3) {
@@ -626,32 +657,35 @@ __global__ void __launch_bounds__(256, 1) k_residual_df(ElemView<float> ev, cons
                     Vl[m][k][c] = wl;
                 }
         }
-        // backward and scatter of -(K (x + u_macro))
+        // backward and scatter of -(K (x + u_macro)) for these modes
+        if constexpr (HAS0) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            float sh = Vh[0][0][c], sl = Vl[0][0][c];
-            df_add(sh, sl, Vh[0][1][c], Vl[0][1][c]);
-            df_add(sh, sl, Vh[0][2][c], Vl[0][2][c]);
-            const int64_t i0 = ((int64_t)__ldg(ed) * NC + c) * ncols + col;
-            atomicAdd(r + i0, (double)sh);
-            atomicAdd(rlo + i0, sl);
+            for (int c = 0; c < NC; ++c) {
+                float sh = Vh[0][0][c], sl = Vl[0][0][c];
+                df_add(sh, sl, Vh[0][1][c], Vl[0][1][c]);
+                df_add(sh, sl, Vh[0][2][c], Vl[0][2][c]);
+                const int64_t i0 = ((int64_t)__ldg(ed) * NC + c) * ncols + col;
+                atomicAdd(r + i0, (double)sh);
+                atomicAdd(rlo + i0, sl);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int64_t ik = ((int64_t)__ldg(ed + k + 1) * NC + c) * ncols + col;
-                atomicAdd(r + ik, (double)-Vh[0][k][c]);
-                atomicAdd(rlo + ik, -Vl[0][k][c]);
+                for (int k = 0; k < 3; ++k) {
+                    const int64_t ik = ((int64_t)__ldg(ed + k + 1) * NC + c) * ncols + col;
+                    atomicAdd(r + ik, (double)-Vh[0][k][c]);
+                    atomicAdd(rlo + ik, -Vl[0][k][c]);
+                }
             }
         }
 #pragma unroll
         for (int j = 4; j < NE; ++j) {
+            if (!df_group_touches<P, M0, M1>(j)) continue;
             float yh[NC], yl[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) yh[c] = yl[c] = 0.f;
 #pragma unroll
-            for (int m = 0; m < NM; ++m)
+            for (int m = 0; m < G_; ++m)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float a = basis_a<P, float>((k * NM + m) * NE + j);
+                    const float a = basis_a<P, float>((k * NM + M0 + m) * NE + j);
                     if (a != 0.f)
 #pragma unroll
                         for (int c = 0; c < NC; ++c) df_mac(yh[c], yl[c], a, Vh[m][k][c], Vl[m][k][c]);
@@ -688,14 +722,20 @@ void launch_split_d2ff(int64_t n, const double* x, float* xh, float* xl, cudaStr
 void launch_residual_df(int p, int nc, const ElemView<float>& ev, const float* xh, const float* xl,
                         double* r, float* rlo, const Launch& L) {
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
-#define RVE_DF_CASE(PP, NCC)                                                                          \
-    if (p == PP && nc == NCC) {                                                                       \
-        k_residual_df<PP, NCC><<<grid, block, 0, L.stream>>>(ev, xh, xl, r, rlo, L.ncols, L.cpb);     \
-        return;                                                                                       \
+    // mode groups: p = 1 has one mode, p = 2 four (two passes of two), p = 3 ten
+    // (passes of four, three and three)
+#define RVE_DF_RUN(PP, NCC, A, B) \
+    k_residual_df<PP, NCC, A, B><<<grid, block, 0, L.stream>>>(ev, xh, xl, r, rlo, L.ncols, L.cpb);
+    if (p == 1) {
+        if (nc == 3) { RVE_DF_RUN(1, 3, 0, 1) } else { RVE_DF_RUN(1, 1, 0, 1) }
+    } else if (p == 2) {
+        if (nc == 3) { RVE_DF_RUN(2, 3, 0, 2) RVE_DF_RUN(2, 3, 2, 4) }
+        else { RVE_DF_RUN(2, 1, 0, 4) }
+    } else if (p == 3) {
+        if (nc == 3) { RVE_DF_RUN(3, 3, 0, 4) RVE_DF_RUN(3, 3, 4, 7) RVE_DF_RUN(3, 3, 7, 10) }
+        else { RVE_DF_RUN(3, 1, 0, 5) RVE_DF_RUN(3, 1, 5, 10) }
     }
-    RVE_DF_CASE(1, 3) RVE_DF_CASE(2, 3) RVE_DF_CASE(3, 3)
-    RVE_DF_CASE(1, 1) RVE_DF_CASE(2, 1) RVE_DF_CASE(3, 1)
-#undef RVE_DF_CASE
+#undef RVE_DF_RUN
 }
 
 // ------------------------------------------------------ Jacobi diagonal (K6)
@@ -1042,7 +1082,7 @@ __global__ void __launch_bounds__(256) k_finalize_alpha(const double* __restrict
 
 template <typename T>
 void launch_finalize_alpha(const double* energy_partial, ColState cs, const Launch& L) {
-    k_finalize_alpha<<<L.ncols, 256, 0, L.stream>>>(energy_partial, L.nby, L.ncols, cs);
+    k_finalize_alpha<<<L.ncols, 256, 0, L.stream>>>(energy_partial, L.op_rows(), L.ncols, cs);
 }
 template void launch_finalize_alpha<float>(const double*, ColState, const Launch&);
 template void launch_finalize_alpha<double>(const double*, ColState, const Launch&);

@@ -17,7 +17,9 @@ struct Launch {
     int cpb = 6;          // columns per block (divides ncols)
     int rows_per_block = 42;
     int nby = 1;          // grid.y of the 2-D launches (partials are [nby][ncols][...])
+    int nby_op = 0;       // grid.y of the operator and rows of its energy partials (0: nby)
     cudaStream_t stream = 0;
+    int op_rows() const { return nby_op > 0 ? nby_op : nby; }
 };
 
 template <typename T>
@@ -76,6 +78,10 @@ template <typename T>
 void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
                      double* energy_partial, const Launch& L, const int32_t* active = nullptr,
                      const int32_t* list = nullptr, const int32_t* n_list = nullptr);
+// grid.y of the operator for a launch shape: one wave of the blocks that fit on the
+// GPU at once (grid-stride over elements), at most L.nby
+template <typename T>
+int operator_grid_y(int p, int nc, const Launch& L, int64_t nt);
 // list[0 .. n) = the columns with active != 0, ascending (one block)
 void launch_compact_active(const int32_t* active, int ncols, int32_t* list, int32_t* n_list, cudaStream_t s);
 

@@ -10,7 +10,7 @@
 //
 // GEMM convention: C[M][N] = A[M][K] * B, with A row-major and B supplied as
 // Bt[N][K] row-major (K contiguous in both), M a multiple of 64, N 64 or a
-// multiple of 256, K a multiple of 64.
+// multiple of 128, K a multiple of 64.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -252,7 +252,7 @@ static size_t gemm_smem() {
 }
 
 void gemm_tc_prepare() {
-    cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
+    cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
     cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<64>());
 }
 
@@ -263,15 +263,17 @@ int gemm_tc_timed_out() {
 }
 
 // M a multiple of 64 (rows past a 128-row tile are zero-filled), N 64 or a
-// multiple of 256, K a multiple of 64.
+// multiple of 128, K a multiple of 64.  128-column tiles: 128 TMEM columns and
+// 64 KB of operand stages per CTA, so three CTAs share an SM and hide each
+// other's load latency and epilogue.
 void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, const float* bias,
                       int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s) {
     if (N == 64) {
         dim3 grid(1, (M + 127) / 128);
         k_gemm_tc<64><<<grid, 128, gemm_smem<64>(), s>>>(M, N, K, A, Bt, bias, epilogue, Cb, Cf);
     } else {
-        dim3 grid(N / 256, (M + 127) / 128);
-        k_gemm_tc<256><<<grid, 128, gemm_smem<256>(), s>>>(M, N, K, A, Bt, bias, epilogue, Cb, Cf);
+        dim3 grid(N / 128, (M + 127) / 128);
+        k_gemm_tc<128><<<grid, 128, gemm_smem<128>(), s>>>(M, N, K, A, Bt, bias, epilogue, Cb, Cf);
     }
 }
 
@@ -423,70 +425,90 @@ void launch_features(int n, int M, int kin, const double* feat, const float* mea
     k_features<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, M, kin, feat, mean, inv_std, X);
 }
 
-// Head: z [M][noutp] of member e -> factor entries (softplus diagonals), accumulated
-// into the ensemble mean tensors; writes member tensors to T_e [n][54] (C 36, K 9, D 9).
-__global__ void k_head_tensors(int n, int noutp, const float* __restrict__ z, const uint8_t* __restrict__ diag,
-                               double* __restrict__ Te) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double L[33];
-    for (int c = 0; c < 33; ++c) {
-        const double zz = z[(int64_t)r * noutp + c];
-        L[c] = diag[c] ? (zz > 30 ? zz : log1p(exp(zz))) : zz;
-    }
-    double* out = Te + (int64_t)r * 54;
-    const int sizes[3] = {6, 3, 3}, offs[3] = {0, 21, 27}, oofs[3] = {0, 36, 45};
-    for (int b = 0; b < 3; ++b) {
-        const int nn = sizes[b];
-        double Lm[6][6] = {};
-        int k = 0;
-        for (int i = 0; i < nn; ++i)
-            for (int j = 0; j <= i; ++j) Lm[i][j] = L[offs[b] + k++];
-        for (int i = 0; i < nn; ++i)
-            for (int j = 0; j < nn; ++j) {
-                double sacc = 0;
-                for (int q = 0; q <= (i < j ? i : j); ++q) sacc += Lm[i][q] * Lm[j][q];
-                out[oofs[b] + i * nn + j] = sacc;
-            }
-    }
+// L L^T of one lower-triangular factor of size NN stored row-major from L[OFF]
+// into out[OO ..] (compile-time indices keep L in registers).
+template <int NN, int OFF, int OO>
+__device__ __forceinline__ void head_block(const float (&L)[33], float* out) {
+#pragma unroll
+    for (int i = 0; i < NN; ++i)
+#pragma unroll
+        for (int j = 0; j < NN; ++j) {
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q <= (i < j ? i : j); ++q)
+                acc = fmaf(L[OFF + i * (i + 1) / 2 + q], L[OFF + j * (j + 1) / 2 + q], acc);
+            out[OO + i * NN + j] = acc;
+        }
 }
 
-void launch_head_tensors(int n, int noutp, const float* z, const uint8_t* diag, double* Te, cudaStream_t s) {
+// Head: z [M][noutp] of member e -> factor entries (softplus diagonals), member
+// tensors L L^T into Te [n][54] (C 36, K 9, D 9).  FP32 arithmetic (the network
+// itself is BF16 with FP32 accumulation; FP64 runs at a small fraction of the FP32
+// rate on this GPU).
+__global__ void k_head_tensors(int n, int noutp, const float* __restrict__ z, const uint8_t* __restrict__ diag,
+                               float* __restrict__ Te) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float L[33];
+#pragma unroll
+    for (int c = 0; c < 33; ++c) {
+        const float zz = z[(int64_t)r * noutp + c];
+        L[c] = diag[c] ? (zz > 20.f ? zz : log1pf(expf(zz))) : zz;
+    }
+    float* out = Te + (int64_t)r * 54;
+    head_block<6, 0, 0>(L, out);
+    head_block<3, 21, 36>(L, out);
+    head_block<3, 27, 45>(L, out);
+}
+
+void launch_head_tensors(int n, int noutp, const float* z, const uint8_t* diag, float* Te, cudaStream_t s) {
     k_head_tensors<<<(n + 127) / 128, 128, 0, s>>>(n, noutp, z, diag, Te);
 }
 
-// Ensemble mean and spread: Tm [n][54] = mean over members, spread[n] = max over
-// the three tensors of max_e ||T_e - Tm||_F / ||Tm||_F.
-__global__ void k_ensemble(int n, int members, const double* __restrict__ T, double* __restrict__ Tm,
+// Mean over the members of entries [LO, HI) of row r (written to Tm in FP64) and
+// the largest relative member deviation max_e ||T_e - mean|| / ||mean|| over them.
+template <int LO, int HI>
+__device__ __forceinline__ float ensemble_block(int n, int r, int members, const float* __restrict__ T,
+                                                double* __restrict__ Tm) {
+    float mean[HI - LO];
+    const float inv = 1.f / (float)members;
+#pragma unroll
+    for (int c = 0; c < HI - LO; ++c) {
+        float sacc = 0.f;
+        for (int e = 0; e < members; ++e) sacc += T[((int64_t)e * n + r) * 54 + LO + c];
+        mean[c] = sacc * inv;
+        Tm[(int64_t)r * 54 + LO + c] = (double)mean[c];
+    }
+    float den = 0.f;
+#pragma unroll
+    for (int c = 0; c < HI - LO; ++c) den = fmaf(mean[c], mean[c], den);
+    float worst = 0.f;
+    for (int e = 0; e < members; ++e) {
+        float num = 0.f;
+#pragma unroll
+        for (int c = 0; c < HI - LO; ++c) {
+            const float d = T[((int64_t)e * n + r) * 54 + LO + c] - mean[c];
+            num = fmaf(d, d, num);
+        }
+        const float q = den > 0.f ? sqrtf(num / den) : 0.f;
+        worst = q > worst ? q : worst;
+    }
+    return worst;
+}
+
+// Ensemble mean and spread: Tm [n][54] = mean over members (FP64 storage),
+// spread[n] = max over the three tensors of max_e ||T_e - Tm||_F / ||Tm||_F.
+__global__ void k_ensemble(int n, int members, const float* __restrict__ T, double* __restrict__ Tm,
                            double* __restrict__ spread) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    double mean[54];
-    for (int c = 0; c < 54; ++c) {
-        double sacc = 0;
-        for (int e = 0; e < members; ++e) sacc += T[((int64_t)e * n + r) * 54 + c];
-        mean[c] = sacc / members;
-        Tm[(int64_t)r * 54 + c] = mean[c];
-    }
-    const int lo[3] = {0, 36, 45}, hi[3] = {36, 45, 54};
-    double worst = 0;
-    for (int b = 0; b < 3; ++b) {
-        double den = 0;
-        for (int c = lo[b]; c < hi[b]; ++c) den += mean[c] * mean[c];
-        for (int e = 0; e < members; ++e) {
-            double num = 0;
-            for (int c = lo[b]; c < hi[b]; ++c) {
-                const double d = T[((int64_t)e * n + r) * 54 + c] - mean[c];
-                num += d * d;
-            }
-            const double q = den > 0 ? sqrt(num / den) : 0.0;
-            worst = q > worst ? q : worst;
-        }
-    }
-    spread[r] = worst;
+    const float a = ensemble_block<0, 36>(n, r, members, T, Tm);
+    const float b = ensemble_block<36, 45>(n, r, members, T, Tm);
+    const float c = ensemble_block<45, 54>(n, r, members, T, Tm);
+    spread[r] = (double)fmaxf(a, fmaxf(b, c));
 }
 
-void launch_ensemble(int n, int members, const double* T, double* Tm, double* spread, cudaStream_t s) {
+void launch_ensemble(int n, int members, const float* T, double* Tm, double* spread, cudaStream_t s) {
     k_ensemble<<<(n + 127) / 128, 128, 0, s>>>(n, members, T, Tm, spread);
 }
 

@@ -417,7 +417,7 @@ static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, doubl
     cudaStream_t st = s->ctx->stream;
     const int64_t chunk = 65536;
     RVE_TRY(alloc_work(s, (int)chunk));
-    RVE_TRY(s->Tmem.ensure((size_t)s->members * chunk * 54 * 8));
+    RVE_TRY(s->Tmem.ensure((size_t)s->members * chunk * 54 * 4));
     DevBuf dmean, dstd;
     std::vector<float> fis(8);
     for (int k = 0; k < 8; ++k) fis[k] = 1.f / s->feat_std[k];
@@ -431,9 +431,9 @@ static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, doubl
         for (int e = 0; e < s->members; ++e) {
             forward(s, e, M, false);
             launch_head_tensors(nn, NOUTP, s->zout.as<float>(), s->d_diag.as<uint8_t>(),
-                                s->Tmem.as<double>() + (size_t)e * nn * 54, st);
+                                s->Tmem.as<float>() + (size_t)e * nn * 54, st);
         }
-        launch_ensemble(nn, s->members, s->Tmem.as<double>(), Tm_dev + off * 54, spread_dev + off, st);
+        launch_ensemble(nn, s->members, s->Tmem.as<float>(), Tm_dev + off * 54, spread_dev + off, st);
         s->ctx->launches += 2 + s->members;
     }
     RVE_CUDA(cudaGetLastError());
