@@ -47,6 +47,8 @@ extern "C" {
 #define RVE_ERR_OUT_OF_MEMORY    (-8)  /* device allocation failed */
 #define RVE_ERR_STATE            (-9)  /* call order violated (e.g. homogenise before set_materials) */
 #define RVE_ERR_TIMEOUT         (-10)  /* a bounded device wait gave up */
+#define RVE_ERR_BOUNDS          (-11)  /* checking build only: an element's DOF index or column was
+                                          out of range; the element was skipped (rve_debug_bounds) */
 
 /* ------------------------------------------------------------- enumerations */
 /* RVE boundary conditions of Sec. 2 (unified constraint approach,
@@ -96,6 +98,14 @@ typedef struct rve_options {
                                 matrices stored once per mesh and materials, 3 x TF32 products
                                 with FP32 accumulation).  Other cases always use the matrix-free
                                 kernel. */
+    int     deterministic;   /* 1: bit-reproducible cell solves.  The scatter kernels (operator,
+                                true residual, right-hand side) run once per element colour (no
+                                two elements of a colour share a DOF; greedy colouring of the DOF
+                                map at rve_set_bc), so every entry receives its element
+                                contributions in one fixed order; forces the CUDA-core operator.
+                                Slower (one launch per colour).  0 (default): one launch, the
+                                atomic additions in arrival order (results agree to rounding).
+                                The Jacobi diagonal is always formed colour by colour. */
 } rve_options;
 
 /* Isotropic matrix phase (Sec. 1, Sec. 7). */
@@ -584,6 +594,32 @@ int rve_operator_energy_noalloc(rve_ctx ctx, rve_mesh mesh, int field, int ncols
  * each local function (4 vertex, then 6 quadratic edge, 6 cubic edge, 4 face
  * functions as p allows) and the vertex order used by each tet [nt][4]. */
 int rve_mesh_get_dofmap(rve_ctx ctx, rve_mesh mesh, int32_t* edofs, int32_t* local_vertices);
+
+/* Element colouring of the current DOF map (used by the deterministic mode):
+ * colour_of[nt] (may be NULL) receives each element's colour; returns the number
+ * of colours in *n_colours.  No two elements of one colour share a DOF. */
+int rve_mesh_get_colouring(rve_ctx ctx, rve_mesh mesh, int32_t* colour_of, int32_t* n_colours);
+
+/* ---------------------------------------------------------------- debugging
+ * The library can be built as a checking build (RVE_BOUNDS_CHECK=1): the
+ * operator, the double-float residual and the diagonal kernels then test every
+ * element's DOF indices against the map's DOF count and its column against the
+ * column count before any gather or scatter, count the violations, record the
+ * first (element, column) and skip that element.  rve_homogenise and
+ * macro_update_gauss_points[_w][_dev] then return RVE_ERR_BOUNDS when a
+ * violation was counted during the call.  A release build compiles the checks out.
+ *
+ * rve_debug_bounds: *checking_build = 1 in a checking build; *violations, the
+ * first element and column since the last reset (-1 when none); reset != 0 clears
+ * the count afterwards.  Any pointer may be NULL. */
+int rve_debug_bounds(rve_ctx ctx, int32_t* checking_build, int64_t* violations, int64_t* first_element,
+                     int32_t* first_column, int reset);
+
+/* Test hook of the checking build: the kernels of this mesh compare DOF indices
+ * against n_nodes instead of the map's own count (0 restores it).  With a bound
+ * below the count, the elements touching higher DOFs are reported and skipped,
+ * while every access that does run stays inside the mesh's arrays. */
+int rve_debug_set_node_bound(rve_ctx ctx, rve_mesh mesh, int64_t n_nodes);
 
 #ifdef __cplusplus
 }

@@ -14,12 +14,13 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "librve.so")
+# RVE_LIBRARY selects another build of the library (the checking build, librve_check.so)
+LIB_PATH = os.environ.get("RVE_LIBRARY") or os.path.join(HERE, "librve.so")
 
 RVE_OK = 0
 ERRORS = {
     -1: "INVALID_ARGUMENT", -2: "BAD_MESH", -3: "NOT_SPD", -4: "NOT_CONVERGED", -5: "NUMERIC",
-    -6: "CUDA", -7: "NO_DEVICE", -8: "OUT_OF_MEMORY", -9: "STATE", -10: "TIMEOUT",
+    -6: "CUDA", -7: "NO_DEVICE", -8: "OUT_OF_MEMORY", -9: "STATE", -10: "TIMEOUT", -11: "BOUNDS",
 }
 BC_DIRICHLET, BC_PERIODIC, BC_NEUMANN = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
@@ -37,7 +38,8 @@ class Options(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_iter", C.c_int), ("inner_rtol", C.c_double), ("max_refine", C.c_int),
                 ("check_every", C.c_int), ("batch", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("warm_start", C.c_int), ("transport_once", C.c_int), ("operator_kernel", C.c_int)]
+                ("warm_start", C.c_int), ("transport_once", C.c_int), ("operator_kernel", C.c_int),
+                ("deterministic", C.c_int)]
 
 
 class MatrixProps(C.Structure):
@@ -171,6 +173,10 @@ _SIGS = {
     "rve_mesh_get_tensors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "rve_mesh_get_dofmap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_mesh_get_colouring": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "rve_debug_bounds": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int32), C.c_int]),
+    "rve_debug_set_node_bound": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "rve_operator_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                               C.c_void_p]),
     "rve_surrogate_create": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.POINTER(C.c_void_p)]),
@@ -254,7 +260,7 @@ class Context:
 
     def __init__(self, precision=PREC_FP64, rtol=1e-10, max_iter=20000, inner_rtol=1e-6,
                  max_refine=4, check_every=16, batch=0, stream=None, device=0, profile=False,
-                 warm_start=2, transport_once=False, operator_kernel=KERNEL_AUTO):
+                 warm_start=2, transport_once=False, operator_kernel=KERNEL_AUTO, deterministic=False):
         lib = load_library()
         o = default_options()
         o.device, o.precision, o.rtol, o.max_iter = device, precision, rtol, max_iter
@@ -264,6 +270,7 @@ class Context:
         o.warm_start = (2 if warm_start else 0) if isinstance(warm_start, bool) else int(warm_start)
         o.transport_once = int(transport_once)
         o.operator_kernel = int(operator_kernel)
+        o.deterministic = int(deterministic)
         h = C.c_void_p()
         _check(lib.rve_create(C.byref(h), C.byref(o)), "rve_create")
         self.h = h
@@ -280,6 +287,14 @@ class Context:
         for k, v in kw.items():
             setattr(o, k, v)
         _check(self.lib.rve_set_options(self.h, C.byref(o)), "rve_set_options")
+
+    def debug_bounds(self, reset: bool = False) -> dict:
+        """Counters of the checking build (checking_build = 0 in a release build)."""
+        cb, n, fe, fc = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+        _check(self.lib.rve_debug_bounds(self.h, C.byref(cb), C.byref(n), C.byref(fe), C.byref(fc), int(reset)),
+               "rve_debug_bounds")
+        return {"checking_build": cb.value, "violations": n.value, "first_element": fe.value,
+                "first_column": fc.value}
 
     def close(self):
         if self.h:
@@ -629,6 +644,17 @@ class Mesh:
         lv = np.zeros((self.nt, 4), np.int32)
         _check(self.ctx.lib.rve_mesh_get_dofmap(self.ctx.h, self.h, _ptr(ed), _ptr(lv)), "rve_mesh_get_dofmap")
         return ed, lv
+
+    def colouring(self):
+        """(colour of every element, number of colours) of the current DOF map."""
+        col = np.zeros(self.nt, np.int32)
+        n = C.c_int32()
+        _check(self.ctx.lib.rve_mesh_get_colouring(self.ctx.h, self.h, _ptr(col), C.byref(n)),
+               "rve_mesh_get_colouring")
+        return col, n.value
+
+    def debug_set_node_bound(self, n_nodes: int):
+        _check(self.ctx.lib.rve_debug_set_node_bound(self.ctx.h, self.h, int(n_nodes)), "rve_debug_set_node_bound")
 
 
 __all__ = ["Context", "Mesh", "Surrogate", "RveError", "load_library", "exported_symbols", "BC_DIRICHLET", "BC_PERIODIC",

@@ -41,6 +41,82 @@ namespace {
 int table_nonzeros(int p);
 
 // ------------------------------------------------------------ geometry + map
+// Greedy colouring of the elements over the current DOF map: elements in mesh
+// order, each taking the smallest colour that none of its DOFs has met yet, so
+// that no two elements of one colour share a DOF.  The elements are then sorted
+// by colour (stable) for the deterministic launches.
+int build_colouring(rve_mesh m) {
+    const int ne = n_local(m->p);
+    const int64_t nt = m->nt, N = m->map.N;
+    constexpr int W = 4;   // colour bit sets of 256 colours
+    std::vector<uint64_t> used((size_t)N * W, 0);
+    std::vector<int32_t> colour(nt);
+    int ncol = 0;
+    for (int64_t e = 0; e < nt; ++e) {
+        const int32_t* ed = &m->map.edofs[(size_t)e * ne];
+        uint64_t seen[W] = {0, 0, 0, 0};
+        for (int j = 0; j < ne; ++j) {
+            if (ed[j] < 0 || ed[j] >= N) {
+                set_error("DOF index out of range in the map");
+                return RVE_ERR_BAD_MESH;
+            }
+            for (int w = 0; w < W; ++w) seen[w] |= used[(size_t)ed[j] * W + w];
+        }
+        int c = -1;
+        for (int w = 0; w < W && c < 0; ++w)
+            if (~seen[w]) c = 64 * w + __builtin_ctzll(~seen[w]);
+        if (c < 0) {
+            set_error("element colouring needs more than 256 colours");
+            return RVE_ERR_BAD_MESH;
+        }
+        colour[e] = c;
+        ncol = std::max(ncol, c + 1);
+        for (int j = 0; j < ne; ++j) used[(size_t)ed[j] * W + c / 64] |= 1ull << (c % 64);
+    }
+    m->colour_off.assign(ncol + 1, 0);
+    for (int64_t e = 0; e < nt; ++e) m->colour_off[colour[e] + 1]++;
+    for (int k = 0; k < ncol; ++k) m->colour_off[k + 1] += m->colour_off[k];
+    std::vector<int64_t> pos(m->colour_off.begin(), m->colour_off.end() - 1);
+    std::vector<int32_t> order(nt);
+    for (int64_t e = 0; e < nt; ++e) order[pos[colour[e]]++] = (int32_t)e;
+    RVE_TRY(upload(m->d_colour_elems, order.data(), order.size(), m->ctx->stream));
+    m->ncolour = ncol;
+    return RVE_OK;
+}
+
+// Element-view fields common to every launch: the DOF-node bound of the checking
+// build and, in deterministic mode (or when forced), the colouring.
+template <typename T>
+void set_view_extras(ElemView<T>& ev, rve_mesh m, bool force_colours = false) {
+    ev.n_nodes = m->debug_node_bound > 0 ? m->debug_node_bound : m->map.N;
+    if ((force_colours || m->ctx->opt.deterministic) && m->ncolour > 0) {
+        ev.elist_all = m->d_colour_elems.as<int32_t>();
+        ev.coff = m->colour_off.data();
+        ev.ncolour = m->ncolour;
+    }
+}
+
+// Checking build: the counter starts from zero at each checked call, and the
+// violations counted during the call turn its result into RVE_ERR_BOUNDS (the
+// counter keeps them for rve_debug_bounds).
+void bounds_begin(cudaStream_t s) {
+    if (!bounds_check_built()) return;
+    cudaStreamSynchronize(s);
+    bounds_reset();
+}
+
+int bounds_verdict(int rc, cudaStream_t s) {
+    if (!bounds_check_built()) return rc;
+    cudaStreamSynchronize(s);
+    unsigned long long n = 0;
+    long long fe = -1;
+    int fc = -1;
+    if (bounds_status(&n, &fe, &fc) != 0 || n == 0) return rc;
+    set_error("bounds check: " + std::to_string(n) + " element visits out of range (first: element " +
+              std::to_string(fe) + ", column " + std::to_string(fc) + "), skipped");
+    return RVE_ERR_BOUNDS;
+}
+
 int rebuild_map(rve_mesh m) {
     cudaStream_t s = m->ctx->stream;
     std::string err;
@@ -52,6 +128,7 @@ int rebuild_map(rve_mesh m) {
     }
     const int ne = n_local(m->p);
     RVE_TRY(upload(m->d_edofs, m->map.edofs.data(), (size_t)m->nt * ne, s));
+    RVE_TRY(build_colouring(m));
     RVE_TRY(upload(m->d_lverts, m->map.lverts.data(), (size_t)m->nt * 4, s));
     RVE_TRY(m->d_geo64.ensure(sizeof(double) * m->nt * 10));
     RVE_TRY(m->d_geo32.ensure(sizeof(float) * m->nt * 10));
@@ -209,6 +286,7 @@ int build_diagonals(rve_mesh m) {
         ev.geo = m->d_geo64.as<double>();
         ev.mat = (f->nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
         ev.phase = m->d_phase.as<uint8_t>();
+        set_view_extras(ev, m, true);   // colour by colour: the diagonal is bit-reproducible
         launch_diag<double>(m->p, f->nc, f->n_rows, ev, f->diag64.as<double>(), s);
         launch_cast_d2f(n, f->diag64.as<double>(), f->diag32.as<float>(), s);
         m->ctx->launches += 2;
@@ -307,6 +385,7 @@ struct Solver {
         }
         e.phase = m->d_phase.as<uint8_t>();
         e.scale = scale.as<T>();
+        set_view_extras(e, m);
         return e;
     }
     template <typename T>
@@ -328,6 +407,10 @@ struct Solver {
 
     int alloc(bool mixed) {
         const size_t nv = (size_t)n_rows * ncols;
+        if (nv >= ((size_t)1 << 31)) {   // the scatter kernels index vectors in 32 bits
+            set_error("batch too large: a solve vector would exceed 2^31 entries");
+            return RVE_ERR_INVALID_ARGUMENT;
+        }
         RVE_TRY(m->x64f[fid].ensure(nv * 8));
         RVE_TRY(m->r64f[fid].ensure(nv * 8));
         RVE_TRY(m->b64.ensure(nv * 8));
@@ -341,7 +424,8 @@ struct Solver {
             RVE_TRY(m->q64.ensure(nv * 8));
         }
         const size_t np = (size_t)L.nby * ncols;
-        RVE_TRY(m->epart.ensure(np * 8));
+        // deterministic mode: one block of operator partials per colour
+        RVE_TRY(m->epart.ensure(np * 8 * (m->ctx->opt.deterministic ? std::max(1, m->ncolour) : 1)));
         RVE_TRY(m->rzp.ensure(np * 8));
         RVE_TRY(m->cpart.ensure(np * 12 * 8));
         RVE_TRY(m->gpart.ensure(np * 12 * 8));
@@ -416,6 +500,7 @@ struct Solver {
 
     // y = b - K x in mixed mode: the double-float evaluation of the FP32-data operator
     int residual_df(const double* x, double* y) {
+        NvtxRange nvtx_("true residual, double-float, field %d, %d columns", fid, ncols);
         const bool prof = m->ctx->opt.profile != 0;
         auto& evs = m->ctx->ev;
         while (prof && evs.size() < 2) {
@@ -449,6 +534,7 @@ struct Solver {
 
     // y = -(K x + macro)  (FP64): the fluctuation residual b - K x
     int residual64(const double* x, double* y) {
+        NvtxRange nvtx_("true residual, FP64, field %d, %d columns", fid, ncols);
         const bool prof = m->ctx->opt.profile != 0;
         auto& evs = m->ctx->ev;
         while (prof && evs.size() < 2) {
@@ -481,13 +567,16 @@ struct Solver {
         // FP32 inner solve of the mechanics at p = 2, 3: the tensor-core operator
         int kern = m->ctx->opt.operator_kernel;
         if (kern == RVE_KERNEL_AUTO) kern = m->tuned_kernel != 0 ? m->tuned_kernel : RVE_KERNEL_CUDA_CORE;
-        const bool use_tc = sizeof(T) == 4 && operator_tc_supported(m->p, f.nc) && kern == RVE_KERNEL_TENSOR;
+        const bool det = m->ctx->opt.deterministic != 0;
+        const bool use_tc =
+            !det && sizeof(T) == 4 && operator_tc_supported(m->p, f.nc) && kern == RVE_KERNEL_TENSOR;
         if (use_tc) RVE_TRY(ensure_element_matrices(m, s));
         ColState cs = cs64;
         // the operator of the iteration runs one wave of resident blocks; its energy
         // partials (and the alpha reduction over them) have as many rows
         Launch Lop = L;
         Lop.nby_op = operator_grid_y<T>(m->p, f.nc, L, m->nt);
+        Lop.n_colour = det ? m->ncolour : 0;
         RVE_CUDA(cudaMemcpyAsync(const_cast<double*>(cs.tol), &tol, sizeof(double), cudaMemcpyHostToDevice, s));
         RowView<T> rvw = rv<T>(scale);
         ElemView<T> evw = ev<T>(scale);
@@ -527,6 +616,7 @@ struct Solver {
         auto iteration = [&](const Launch& Lx0) {
             Launch Lx = Lx0;
             Lx.nby_op = Lop.nby_op;
+            Lx.n_colour = Lop.n_colour;
             evr(0, Lx.stream);
             if constexpr (sizeof(T) == 4) {
                 if (use_tc) {
@@ -567,8 +657,8 @@ struct Solver {
             // reused while every captured parameter is unchanged (the tolerance
             // lives in device memory).
             struct Key {
-                int ncols, cpb, rows, nby, nby_op, p, nc, m, max_iter, tc;
-                int64_t n_rows, n_sup, nt;
+                int ncols, cpb, rows, nby, nby_op, p, nc, m, max_iter, tc, ncolour;
+                int64_t n_rows, n_sup, nt, n_nodes;
                 const void* ptr[19];
             } key;
             std::memset(&key, 0, sizeof(key));
@@ -584,7 +674,9 @@ struct Solver {
             key.n_rows = rvw.n_rows;
             key.n_sup = rvw.n_sup;
             key.nt = evw.nt;
+            key.n_nodes = evw.n_nodes;
             key.tc = use_tc ? 1 : 0;
+            key.ncolour = Lop.n_colour;
             const void* ptrs[19] = {x, r, p, q, m->epart.p, m->rzp.p, m->cpart.p, cs.rz, rvw.scale, rvw.diag,
                                     rvw.mask, rvw.sup_row, rvw.sup_coef, rvw.sup_of_row, evw.edofs, evw.geo,
                                     evw.mat, evw.phase, use_tc ? m->d_ke32.p : nullptr};
@@ -732,6 +824,8 @@ struct Solver {
 
     // warm: optional starting data from the previous batch (see WarmStart).
     int run(int precision, SolveOut& out, const WarmStart* warm = nullptr) {
+        NvtxRange nvtx_("cell solve, field %d, p = %d, %d columns, %s", fid, m->p, ncols,
+                     precision == RVE_PREC_MIXED ? "mixed" : "fp64");
         const rve_options& o = m->ctx->opt;
         const bool mixed = precision == RVE_PREC_MIXED;
         RVE_TRY(alloc(mixed));
@@ -978,6 +1072,7 @@ static int warm_sources(const std::vector<double>& pw, double w, int order, int*
 // Solve B RVEs of one mesh whose degradation factors are in d_w (device).
 int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D,
                           rve_stats* st, const double* w_host) {
+    NvtxRange nvtx_("homogenise batch of %d RVEs (%d tets, p = %d)", B, (int)m->nt, m->p);
     cudaStream_t s = m->on_own_streams ? m->stream : m->ctx->stream;
     const int ncols = 6 * B;
     RVE_TRY(m->scale64.ensure((size_t)ncols * 2 * 8));
@@ -1180,6 +1275,7 @@ void rve_default_options(rve_options* o) {
     o->warm_start = 2;
     o->transport_once = 0;
     o->operator_kernel = 0;
+    o->deterministic = 0;
 }
 
 int rve_create(rve_ctx* out, const rve_options* opts) {
@@ -1500,6 +1596,7 @@ int rve_homogenise_weak(rve_ctx c, rve_mesh m, double* C, double* K, double* D, 
 }
 
 int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_stats* st) {
+    NvtxRange nvtx_("rve_homogenise");
     RVE_TRY(check_ctx(c));
     if (!m) return RVE_ERR_INVALID_ARGUMENT;
     if (!m->have_materials) {
@@ -1513,6 +1610,7 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
         st->converged = 1;
     }
     cudaStream_t s = c->stream;
+    bounds_begin(s);
     double Th[1] = {m->T_C}, ch[1] = {m->c_wt}, th[1] = {m->t_h};
     DevBuf tmp;
     RVE_TRY(tmp.ensure(4 * 8));
@@ -1525,6 +1623,7 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
     const ProfCounters pc0 = c->prof;
     int rc = homogenise_batch(m, 1, d + 3, C, K, D, st);
     RVE_CUDA(cudaStreamSynchronize(s));
+    rc = bounds_verdict(rc, s);
     if (st) {
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st->kernel_launches = c->launches - l0;
@@ -1562,6 +1661,7 @@ static int weak_sigma(rve_mesh m, int fid, const double* d_w, std::vector<double
     ev.mat = (nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
     ev.phase = m->d_phase.as<uint8_t>();
     ev.scale = dscale.as<double>();
+    set_view_extras(ev, m);
     const double* u = m->x64f[fid].as<double>();
     // unit macro field of load case I at a point y (engineering shear: E_ab = E_ba = 1/2)
     auto Xval = [&](int I, const double* y, int c) -> double {
@@ -1705,6 +1805,8 @@ static int macro_update_impl(rve_ctx c, const rve_mesh* meshes, int n_meshes, in
                              const double* T_dev, const double* c_dev, const double* t_dev,
                              const int32_t* mesh_id, double* C_dev, double* K_dev, double* D_dev,
                              int32_t* status_dev, rve_stats* st, const double* W_dev = nullptr) {
+    NvtxRange nvtx_("macro_update_gauss_points: %lld points on %d meshes", (long long)G, n_meshes);
+    bounds_begin(c->stream);
     cudaStream_t s = c->stream;
     // group points by mesh
     std::vector<std::vector<int64_t>> groups(n_meshes);
@@ -1937,6 +2039,7 @@ int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshe
     const ProfCounters pc0 = c->prof;
     int rc = macro_update_impl(c, meshes, n_meshes, G, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev,
                                D_dev, status_dev, st);
+    rc = bounds_verdict(rc, c->stream);
     if (st) {
         cudaStreamSynchronize(c->stream);
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1997,6 +2100,7 @@ int macro_update_gauss_points_w_dev(rve_ctx c, const rve_mesh* meshes, int n_mes
     const ProfCounters pc0 = c->prof;
     int rc = macro_update_impl(c, meshes, n_meshes, G, nullptr, nullptr, nullptr, mesh_id_host, C_dev, K_dev,
                                D_dev, status_dev, st, W_dev);
+    rc = bounds_verdict(rc, c->stream);
     if (st) {
         cudaStreamSynchronize(c->stream);
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -2228,6 +2332,10 @@ int rve_apply_operator(rve_ctx c, rve_mesh m, int field, int ncols, const double
     }
     for (int64_t r = 0; r < n_rows; ++r)
         for (int j = 0; j < ncols; ++j) xp[r * cpad2 + colmap[j]] = x[r * ncols + j];
+    if (xp.size() >= ((size_t)1 << 31)) {
+        set_error("rve_apply_operator: more than 2^31 vector entries");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
     DevBuf dx, dy, sc;
     RVE_TRY(upload(dx, xp.data(), xp.size(), s));
     RVE_TRY(dy.ensure(yp.size() * 8));
@@ -2241,6 +2349,7 @@ int rve_apply_operator(rve_ctx c, rve_mesh m, int field, int ncols, const double
     ev.mat = (f.nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
     ev.phase = m->d_phase.as<uint8_t>();
     ev.scale = sc.as<double>();
+    set_view_extras(ev, m);
     Launch L = make_launch(cpad2, m->nt, s);
     launch_operator<double>(m->p, f.nc, false, ev, dx.as<double>(), dy.as<double>(), nullptr, L);
     c->launches++;
@@ -2269,6 +2378,10 @@ int rve_apply_operator_mixed(rve_ctx c, rve_mesh m, int kernel, int ncols, const
     FieldDev& f = m->mech;
     const int64_t n_rows = f.n_rows;
     const size_t nv = (size_t)n_rows * ncols;
+    if (nv >= ((size_t)1 << 31)) {
+        set_error("rve_apply_operator_mixed: more than 2^31 vector entries");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
     std::vector<float> x32(nv), sc32((size_t)ncols * 2, 1.f);
     for (size_t i = 0; i < nv; ++i) x32[i] = (float)x[i];
     if (scale)
@@ -2306,6 +2419,7 @@ int rve_apply_operator_mixed(rve_ctx c, rve_mesh m, int kernel, int ncols, const
         ev.mat = m->d_matm32.as<float>();
         ev.phase = m->d_phase.as<uint8_t>();
         ev.scale = dsc.as<float>();
+        ev.n_nodes = m->debug_node_bound > 0 ? m->debug_node_bound : m->map.N;   // no colours: L.nby partial rows
         launch_operator<float>(m->p, 3, false, ev, dx.as<float>(), dy.as<float>(), dpart.as<double>(), L,
                                dact.as<int32_t>(), list, n_list);
     }
@@ -2355,6 +2469,10 @@ int rve_operator_energy_noalloc(rve_ctx c, rve_mesh m, int field, int ncols, con
     }
     cudaStream_t s = c->stream;
     FieldDev& f = field == 0 ? m->mech : m->scal;
+    if ((size_t)f.n_rows * ncols >= ((size_t)1 << 31)) {
+        set_error("rve_operator_energy_noalloc: more than 2^31 vector entries");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
     Launch L = make_launch(ncols, std::max<int64_t>(f.n_rows, m->nt), s);
     L.nby = std::min(L.nby, noalloc_max_blocks_y());
     double* partial = scratch;                                                   // [nby][ncols]
@@ -2368,6 +2486,7 @@ int rve_operator_energy_noalloc(rve_ctx c, rve_mesh m, int field, int ncols, con
     ev.mat = (f.nc == 3 ? m->d_matm64 : m->d_mats64).as<double>();
     ev.phase = m->d_phase.as<uint8_t>();
     ev.scale = scale;
+    ev.n_nodes = m->debug_node_bound > 0 ? m->debug_node_bound : m->map.N;   // no colours: fixed partial rows
     launch_operator<double>(m->p, f.nc, false, ev, x_dev, y_dev, partial, L);
     launch_reduce_partials(L.nby, ncols, partial, energy_dev, s);
     const double lo = field == 0 ? m->mc.ref_mech : m->mc.ref_k;
@@ -2384,6 +2503,47 @@ int rve_mesh_get_dofmap(rve_ctx c, rve_mesh m, int32_t* edofs, int32_t* lverts) 
     if (!m) return RVE_ERR_INVALID_ARGUMENT;
     if (edofs) std::memcpy(edofs, m->map.edofs.data(), m->map.edofs.size() * 4);
     if (lverts) std::memcpy(lverts, m->map.lverts.data(), m->map.lverts.size() * 4);
+    return RVE_OK;
+}
+
+int rve_mesh_get_colouring(rve_ctx c, rve_mesh m, int32_t* colour_of, int32_t* n_colours) {
+    RVE_TRY(check_ctx(c));
+    if (!m || !n_colours) return RVE_ERR_INVALID_ARGUMENT;
+    *n_colours = m->ncolour;
+    if (colour_of) {
+        std::vector<int32_t> order(m->nt);
+        if (m->nt > 0) {
+            RVE_CUDA(cudaMemcpy(order.data(), m->d_colour_elems.p, order.size() * 4, cudaMemcpyDeviceToHost));
+        }
+        for (int k = 0; k < m->ncolour; ++k)
+            for (int64_t i = m->colour_off[k]; i < m->colour_off[k + 1]; ++i) colour_of[order[i]] = k;
+    }
+    return RVE_OK;
+}
+
+int rve_debug_bounds(rve_ctx c, int32_t* checking_build, int64_t* violations, int64_t* first_element,
+                     int32_t* first_column, int reset) {
+    RVE_TRY(check_ctx(c));
+    RVE_CUDA(cudaStreamSynchronize(c->stream));
+    unsigned long long n = 0;
+    long long fe = -1;
+    int fc = -1;
+    if (bounds_status(&n, &fe, &fc) != 0) {
+        set_error("rve_debug_bounds: reading the device counters failed");
+        return RVE_ERR_CUDA;
+    }
+    if (checking_build) *checking_build = bounds_check_built() ? 1 : 0;
+    if (violations) *violations = (int64_t)n;
+    if (first_element) *first_element = fe;
+    if (first_column) *first_column = fc;
+    if (reset && bounds_reset() != 0) return RVE_ERR_CUDA;
+    return RVE_OK;
+}
+
+int rve_debug_set_node_bound(rve_ctx c, rve_mesh m, int64_t n_nodes) {
+    RVE_TRY(check_ctx(c));
+    if (!m || n_nodes < 0) return RVE_ERR_INVALID_ARGUMENT;
+    m->debug_node_bound = n_nodes;
     return RVE_OK;
 }
 

@@ -3,8 +3,11 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
+#include <cstdarg>
+#include <cstdio>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -30,6 +33,22 @@
 namespace rve {
 
 const std::string& last_error();
+
+// NVTX range over a host scope (header-only NVTX v3: a no-op unless a profiler is
+// attached); the name is printf-formatted.
+struct NvtxRange {
+    explicit NvtxRange(const char* fmt, ...) {
+        char buf[128];
+        va_list ap;
+        va_start(ap, fmt);
+        std::vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------ device buffer
 struct DevBuf {
@@ -186,6 +205,13 @@ struct rve_mesh_s {
     // invalidated whenever the DOF map or the materials change) and their index tables
     rve::DevBuf d_ke32, d_kepairs, d_keptab;
     bool ke_valid = false;
+    // element colouring of the current DOF map (no two elements of a colour share a
+    // DOF): elements sorted by colour on the device, colour offsets on the host
+    rve::DevBuf d_colour_elems;
+    std::vector<int64_t> colour_off;
+    int ncolour = 0;
+    // checking build: DOF-index bound the kernels test against (0: the map's own count)
+    int64_t debug_node_bound = 0;
     rve::FieldDev mech, scal;
     bool have_materials = false;
     int tuned_batch = 0;   // batch size chosen by rve_autotune_batch (0: the built-in rule)

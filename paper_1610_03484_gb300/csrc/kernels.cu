@@ -31,6 +31,57 @@ int sm_count() {
     return n;
 }
 
+// ------------------------------------------------------ checking build
+#ifndef RVE_BOUNDS_CHECK
+#define RVE_BOUNDS_CHECK 0
+#endif
+__device__ unsigned long long g_bounds_count;
+__device__ long long g_bounds_first[2];   // element, column of the first violation
+
+// True (and counted) when element e, its DOF indices or column col lie outside
+// the arrays the kernel is about to index; always false in release builds.
+template <int NE, typename T>
+__device__ __forceinline__ bool elem_out_of_bounds(const ElemView<T>& ev, int64_t e, int col, int ncols) {
+#if RVE_BOUNDS_CHECK
+    // (a listed element comes from a colouring the host validated against the mesh)
+    bool bad = e < 0 || (ev.elist == nullptr && e >= ev.nt) || col < 0 || col >= ncols;
+    if (!bad)
+        for (int j = 0; j < NE; ++j) {
+            const int d = ev.edofs[e * NE + j];
+            bad = bad || d < 0 || (ev.n_nodes > 0 && (int64_t)d >= ev.n_nodes);
+        }
+    if (bad && atomicAdd(&g_bounds_count, 1ull) == 0ull) {
+        g_bounds_first[0] = (long long)e;
+        g_bounds_first[1] = col;
+    }
+    return bad;
+#else
+    (void)ev;
+    (void)e;
+    (void)col;
+    (void)ncols;
+    return false;
+#endif
+}
+
+bool bounds_check_built() { return RVE_BOUNDS_CHECK != 0; }
+
+int bounds_status(unsigned long long* count, long long* first_elem, int* first_col) {
+    unsigned long long c = 0;
+    long long f[2] = {-1, -1};
+    if (cudaMemcpyFromSymbol(&c, g_bounds_count, sizeof c) != cudaSuccess) return -1;
+    if (c && cudaMemcpyFromSymbol(f, g_bounds_first, sizeof f) != cudaSuccess) return -1;
+    if (count) *count = c;
+    if (first_elem) *first_elem = c ? f[0] : -1;
+    if (first_col) *first_col = c ? (int)f[1] : -1;
+    return 0;
+}
+
+int bounds_reset() {
+    const unsigned long long z = 0;
+    return cudaMemcpyToSymbol(g_bounds_count, &z, sizeof z) == cudaSuccess ? 0 : -1;
+}
+
 // ------------------------------------------------------------ basis tables
 // A[k][m][j] of the hierarchic basis (see rve_internal.h), per order p.
 __constant__ double cA64[3][3 * 10 * 20];
@@ -160,6 +211,13 @@ __device__ __forceinline__ double block_sum(double v) {
     return total;
 }
 
+// Index of (DOF node d, component c, column col) in an n_rows x ncols vector, in
+// 32-bit arithmetic (the hosts keep every vector of a solve below 2^31 entries).
+template <int NC>
+__device__ __forceinline__ uint32_t vix(int d, int c, int ncols, int col) {
+    return ((uint32_t)d * (uint32_t)NC + (uint32_t)c) * (uint32_t)ncols + (uint32_t)col;
+}
+
 // ------------------------------------------------------------- the operator
 // y += sum_e A_e^T K_e A_e x  for every column, matrix-free (Eq. RVE_Eq_var_final):
 // per element, the reference gradient of the field is expanded on the
@@ -198,7 +256,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
     PartialSum<T> energy;
     const int64_t e_end = live ? ev.nt : 0;
 
-    for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < e_end; e += (int64_t)gridDim.y * rows) {
+    for (int64_t ei = (int64_t)blockIdx.y * rows + rr; ei < e_end; ei += (int64_t)gridDim.y * rows) {
+        const int64_t e = ev.elist ? (int64_t)__ldg(ev.elist + ei) : ei;
+        if (elem_out_of_bounds<NE>(ev, e, col, ncols)) continue;
         const int32_t* ed = ev.edofs + e * NE;
         // ---- forward: reference-gradient modes V[m][k][c] = sum_j A[k][m][j] x_j,c.
         // Each gathered value is used for every mode at once and then dropped.
@@ -215,12 +275,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
             const int d0 = __ldg(ed);
             T x0[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) x0[c] = x[((int64_t)d0 * NC + c) * ncols + col];
+            for (int c = 0; c < NC; ++c) x0[c] = x[vix<NC>(d0, c, ncols, col)];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int dk = __ldg(ed + k + 1);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) V[0][k][c] = x[((int64_t)dk * NC + c) * ncols + col] - x0[c];
+                for (int c = 0; c < NC; ++c) V[0][k][c] = x[vix<NC>(dk, c, ncols, col)] - x0[c];
             }
 #pragma unroll
             for (int m = 1; m < NM; ++m)
@@ -235,7 +295,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
             const int dj = __ldg(ed + j);
             T xj[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) xj[c] = x[((int64_t)dj * NC + c) * ncols + col];
+            for (int c = 0; c < NC; ++c) xj[c] = x[vix<NC>(dj, c, ncols, col)];
 #pragma unroll
             for (int m = 0; m < NM; ++m)
 #pragma unroll
@@ -318,10 +378,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const T w0 = V[0][0][c], w1 = V[0][1][c], w2 = V[0][2][c];
-            atomicAdd(y + ((int64_t)__ldg(ed) * NC + c) * ncols + col, -(w0 + w1 + w2));
-            atomicAdd(y + ((int64_t)__ldg(ed + 1) * NC + c) * ncols + col, w0);
-            atomicAdd(y + ((int64_t)__ldg(ed + 2) * NC + c) * ncols + col, w1);
-            atomicAdd(y + ((int64_t)__ldg(ed + 3) * NC + c) * ncols + col, w2);
+            atomicAdd(y + vix<NC>(__ldg(ed), c, ncols, col), -(w0 + w1 + w2));
+            atomicAdd(y + vix<NC>(__ldg(ed + 1), c, ncols, col), w0);
+            atomicAdd(y + vix<NC>(__ldg(ed + 2), c, ncols, col), w1);
+            atomicAdd(y + vix<NC>(__ldg(ed + 3), c, ncols, col), w2);
         }
 #pragma unroll
         for (int j = 4; j < NE; ++j) {
@@ -339,7 +399,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
                 }
             const int dj = __ldg(ed + j);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) atomicAdd(y + ((int64_t)dj * NC + c) * ncols + col, yj[c]);
+            for (int c = 0; c < NC; ++c) atomicAdd(y + vix<NC>(dj, c, ncols, col), yj[c]);
         }
     }
     if (epart) {
@@ -371,6 +431,20 @@ template <typename T>
 void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* x, T* y,
                      double* energy_partial, const Launch& L, const int32_t* active, const int32_t* list,
                      const int32_t* n_list) {
+    if (ev.ncolour > 0 && ev.coff && ev.elist_all) {
+        // deterministic: one launch per colour, each with its own rows of partials
+        Launch Lc = L;
+        Lc.n_colour = 0;
+        for (int k = 0; k < ev.ncolour; ++k) {
+            ElemView<T> evk = ev;
+            evk.ncolour = 0;
+            evk.elist = ev.elist_all + ev.coff[k];
+            evk.nt = ev.coff[k + 1] - ev.coff[k];
+            double* ep = energy_partial ? energy_partial + (size_t)k * L.op_rows() * L.ncols : nullptr;
+            launch_operator<T>(p, nc, macro, evk, x, y, ep, Lc, active, list, n_list);
+        }
+        return;
+    }
     dim3 grid(L.ncols / L.cpb, L.op_rows()), block(L.cpb * L.rows_per_block);
     if (grid.x != 1) list = n_list = nullptr;   // the list maps one block column
 #define RVE_OP_CASE(PP, NCC, MM)                                                                \
@@ -513,7 +587,9 @@ __global__ void __launch_bounds__(256, 2) k_residual_df(ElemView<float> ev, cons
     const int col = blockIdx.x * cpb + cl;
     const int field = (col % 6) >= 3 ? 1 : 0;
     const int macro_id = NC == 3 ? (col % 6) : ((col % 6) % 3);
-    for (int64_t e = (int64_t)blockIdx.y * rows + rr; e < ev.nt; e += (int64_t)gridDim.y * rows) {
+    for (int64_t ei = (int64_t)blockIdx.y * rows + rr; ei < ev.nt; ei += (int64_t)gridDim.y * rows) {
+        const int64_t e = ev.elist ? (int64_t)__ldg(ev.elist + ei) : ei;
+        if (elem_out_of_bounds<NE>(ev, e, col, ncols)) continue;
         const int32_t* ed = ev.edofs + e * NE;
         float Vh[G_][3][NC], Vl[G_][3][NC];
 #pragma unroll
@@ -721,6 +797,16 @@ void launch_split_d2ff(int64_t n, const double* x, float* xh, float* xl, cudaStr
 
 void launch_residual_df(int p, int nc, const ElemView<float>& ev, const float* xh, const float* xl,
                         double* r, float* rlo, const Launch& L) {
+    if (ev.ncolour > 0 && ev.coff && ev.elist_all) {
+        for (int k = 0; k < ev.ncolour; ++k) {
+            ElemView<float> evk = ev;
+            evk.ncolour = 0;
+            evk.elist = ev.elist_all + ev.coff[k];
+            evk.nt = ev.coff[k + 1] - ev.coff[k];
+            launch_residual_df(p, nc, evk, xh, xl, r, rlo, L);
+        }
+        return;
+    }
     dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
     // mode groups: p = 1 has one mode, p = 2 four (two passes of two), p = 3 ten
     // (passes of four, three and three)
@@ -744,8 +830,10 @@ template <int P, int NC, typename T>
 __global__ void k_diag(ElemView<T> ev, int64_t n_rows, T* __restrict__ diag) {
     constexpr int NE = Order<P>::NE;
     constexpr int NM = Order<P>::NM;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ev.nt) return;
+    const int64_t ei = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ei >= ev.nt) return;
+    const int64_t e = ev.elist ? (int64_t)ev.elist[ei] : ei;
+    if (elem_out_of_bounds<NE>(ev, e, 0, 1)) return;
     double G[9];
     for (int i = 0; i < 9; ++i) G[i] = ev.geo[e * 10 + i];
     const double vol = ev.geo[e * 10 + 9];
@@ -797,6 +885,16 @@ __global__ void k_diag(ElemView<T> ev, int64_t n_rows, T* __restrict__ diag) {
 
 template <typename T>
 void launch_diag(int p, int nc, int64_t n_rows, const ElemView<T>& ev, T* diag, cudaStream_t s) {
+    if (ev.ncolour > 0 && ev.coff && ev.elist_all) {
+        for (int k = 0; k < ev.ncolour; ++k) {
+            ElemView<T> evk = ev;
+            evk.ncolour = 0;
+            evk.elist = ev.elist_all + ev.coff[k];
+            evk.nt = ev.coff[k + 1] - ev.coff[k];
+            if (evk.nt > 0) launch_diag<T>(p, nc, n_rows, evk, diag, s);
+        }
+        return;
+    }
     const int bs = 128;
     const int64_t nb = (ev.nt + bs - 1) / bs;
 #define RVE_DG_CASE(PP, NCC)                                                                  \
@@ -1082,7 +1180,7 @@ __global__ void __launch_bounds__(256) k_finalize_alpha(const double* __restrict
 
 template <typename T>
 void launch_finalize_alpha(const double* energy_partial, ColState cs, const Launch& L) {
-    k_finalize_alpha<<<L.ncols, 256, 0, L.stream>>>(energy_partial, L.op_rows(), L.ncols, cs);
+    k_finalize_alpha<<<L.ncols, 256, 0, L.stream>>>(energy_partial, L.op_partials(), L.ncols, cs);
 }
 template void launch_finalize_alpha<float>(const double*, ColState, const Launch&);
 template void launch_finalize_alpha<double>(const double*, ColState, const Launch&);

@@ -18,8 +18,11 @@ struct Launch {
     int rows_per_block = 42;
     int nby = 1;          // grid.y of the 2-D launches (partials are [nby][ncols][...])
     int nby_op = 0;       // grid.y of the operator and rows of its energy partials (0: nby)
+    int n_colour = 0;     // deterministic mode: element colours, one operator launch (and one
+                          // block of op_rows() partial rows) per colour
     cudaStream_t stream = 0;
     int op_rows() const { return nby_op > 0 ? nby_op : nby; }
+    int op_partials() const { return op_rows() * (n_colour > 0 ? n_colour : 1); }
 };
 
 template <typename T>
@@ -30,7 +33,27 @@ struct ElemView {
     const T* mat = nullptr;           // mech [nt][21] upper-triangular Voigt D; scalar [nt][12] k(6), d(6)
     const uint8_t* phase = nullptr;   // [nt]
     const T* scale = nullptr;         // [ncols][2] factor per column and phase
+    // element list: the scatter kernels visit elist[0 .. nt) instead of 0 .. nt
+    const int32_t* elist = nullptr;
+    // deterministic mode (host side): the elements sorted by colour, no two elements of a
+    // colour sharing a DOF; colour k is elist_all[coff[k] .. coff[k+1]).  The launchers run
+    // one launch per colour, so every (DOF, column) entry receives one addition per
+    // launch, in colour order: the sums are bit-reproducible.
+    const int32_t* elist_all = nullptr;   // device
+    const int64_t* coff = nullptr;        // host, [ncolour + 1]
+    int ncolour = 0;
+    // DOF nodes of the map (bound of edofs), used by the checking build only
+    int64_t n_nodes = 0;
 };
+
+// Checking build (compiled with -DRVE_BOUNDS_CHECK=1): every element visited by the
+// operator, the double-float residual and the diagonal has its DOF indices and its
+// column checked before the gather; an element out of range is counted and skipped.
+// Release builds compile the check out and report checking_build = 0.
+bool bounds_check_built();
+// violations since the last reset, and the (element, column) of the first one
+int bounds_status(unsigned long long* count, long long* first_elem, int* first_col);
+int bounds_reset();
 
 // Per-row preconditioner / constraint data of one field.
 template <typename T>

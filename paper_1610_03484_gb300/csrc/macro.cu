@@ -761,6 +761,7 @@ static int transport_solve(rve_macro mm, double dt_s, double rtol, int max_iter,
 
 int rve_macro_step(rve_ctx c, rve_macro m, double dt_h, const rve_degradation* deg, double rtol, int max_iter,
                    rve_macro_stats* st) {
+    NvtxRange nvtx_("macro transport and degradation step");
     RVE_TRY(check_ctx(c));
     if (!m || !(dt_h > 0) || !(rtol > 0) || max_iter < 1) {
         set_error("rve_macro_step: invalid argument");
@@ -865,6 +866,7 @@ int rve_macro_gauss_dev(rve_ctx c, rve_macro m, const double** T_gp, const doubl
 }
 
 int rve_macro_solve_steady(rve_ctx c, rve_macro m, double rtol, int max_iter, rve_macro_stats* st) {
+    NvtxRange nvtx_("macro steady transport solve");
     RVE_TRY(check_ctx(c));
     if (!m || !(rtol > 0) || max_iter < 1) {
         set_error("rve_macro_solve_steady: invalid argument");
@@ -915,6 +917,7 @@ int rve_macro_gradients(rve_ctx c, rve_macro m, int field, double* grad) {
 int rve_fibre_directions(rve_ctx c, const double* xyz, int64_t nv, const int32_t* tets, int64_t nt,
                          const int32_t* yarn_of_tet, int n_yarn, const int32_t* yarn_axis, double rtol,
                          double* dir) {
+    NvtxRange nvtx_("yarn directions (potential flow)");
     RVE_TRY(check_ctx(c));
     if (!xyz || !tets || !yarn_of_tet || !yarn_axis || !dir || nv < 4 || nt < 1 || n_yarn < 0 || !(rtol > 0)) {
         set_error("rve_fibre_directions: invalid argument");
@@ -1089,6 +1092,7 @@ int rve_macro_mech_set_traction(rve_ctx c, rve_macro m, const uint8_t* face_node
 
 int rve_macro_mech_solve(rve_ctx c, rve_macro m, const double* C_gp, int C_on_device, double rtol, int max_iter,
                          rve_macro_mech_stats* st) {
+    NvtxRange nvtx_("macro elastic solve");
     RVE_TRY(check_ctx(c));
     if (!m || !C_gp || !(rtol > 0) || max_iter < 1) {
         set_error("rve_macro_mech_solve: invalid argument");

@@ -11,12 +11,16 @@
 // GEMM convention: C[M][N] = A[M][K] * B, with A row-major and B supplied as
 // Bt[N][K] row-major (K contiguous in both), M a multiple of 64, N 64 or a
 // multiple of 128, K a multiple of 64.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
+#include "kernels.h"
 #include "surrogate.h"
 
 namespace rve {
@@ -27,7 +31,8 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__device__ __forceinline__ float silu_f(float a) { return a / (1.f + __expf(-a)); }
+// a sigmoid(a) with the fast reciprocal division (a / inf -> 0 for very negative a)
+__device__ __forceinline__ float silu_f(float a) { return __fdividef(a, 1.f + __expf(-a)); }
 __device__ __forceinline__ float dsilu_f(float a) {
     const float s = 1.f / (1.f + __expf(-a));
     return s * (1.f + a * (1.f - s));
@@ -69,9 +74,6 @@ __device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity) {
     }
     return false;
 }
-__device__ __forceinline__ void cp16_zfill(uint32_t dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
@@ -99,27 +101,60 @@ __device__ int g_gemm_timeout;   // set when a bounded wait of the GEMM gave up
 
 // epilogue: 0 = store FP32 only, 1 = bias + silu -> BF16 (pre-activation to Cf if non-null),
 //           2 = bias, FP32 out, 3 = accumulate FP32 into Cf (C += A B)
+//
+// Persistent and warp-specialised: each CTA walks the output tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... (the N tiles of one row block are
+// neighbours, so the A rows are read from L2 once per row block).
+//   warp 0   TMA producer: K steps of 64 values of A and Bt into a ring of
+//            GemmShape::S stages (128-byte swizzle; rows past M zero-filled by the
+//            tensor map's bounds), each stage a "full" barrier counting its bytes;
+//   warp 1   MMA issuer: kind::f16 MMAs into one of two FP32 TMEM accumulators,
+//            releasing each stage through an "empty" barrier and each finished
+//            tile through "tmem full";
+//   warps 2.. epilogue (NT / 8 of them): a warp reads 32 rows (its TMEM lane
+//            quarter) x 32 columns of the finished accumulator, hands it back through
+//            "tmem empty" and runs bias / SiLU / conversion and the stores while
+//            the MMAs of the next tile fill the other accumulator.
+// Every wait is bounded; a role that gives up sets g_gemm_timeout and leaves its
+// loop, after which the producer waits for its copies in flight and the MMA
+// issuer for its MMAs, so the tensor memory is idle when it is freed.
 template <int NT>
-__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
-                                                 const __nv_bfloat16* __restrict__ Bt,
-                                                 const float* __restrict__ bias, int epilogue,
-                                                 __nv_bfloat16* __restrict__ Cb, float* __restrict__ Cf) {
-    constexpr int A_BYTES = 128 * 128, B_BYTES = NT * 128, STAGE = A_BYTES + B_BYTES;
+struct GemmShape {
+    static constexpr int S = NT == 128 ? 6 : 8;
+    static constexpr int A_BYTES = 128 * 128, B_BYTES = NT * 128, STAGE = A_BYTES + B_BYTES;
+    // epilogue warps: four lane quarters x column groups of 32
+    static constexpr int EPI_WARPS = 4 * (NT / 32), THREADS = 64 + 32 * EPI_WARPS;
+    static constexpr int NBAR = 2 * S + 5;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(GemmShape<NT>::THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+              uint32_t stage_tx, const float* __restrict__ bias, int epilogue, __nv_bfloat16* __restrict__ Cb,
+              float* __restrict__ Cf) {
+    using G = GemmShape<NT>;
+    constexpr int S = G::S;
     extern __shared__ uint8_t gsm_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * STAGE);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-    const int t = threadIdx.x, warp = t >> 5;
-    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * NT;
-    const int KB = K / 64;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + S * G::STAGE);
+    uint64_t* empty = full + S;
+    uint64_t* tfull = empty + S;    // [2]
+    uint64_t* tempty = tfull + 2;   // [2]
+    uint64_t* done = tempty + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int KB = K / 64, n_tn = N / NT, n_tiles = ((M + 127) / 128) * n_tn;
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + 1)) : "memory");
+        for (int k = 0; k < G::NBAR; ++k) {
+            const uint32_t cnt = (k == 2 * S + 2 || k == 2 * S + 3) ? (uint32_t)G::EPI_WARPS : 1u;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(full + k)), "r"(cnt) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
-                     "r"((uint32_t)NT)
+                     "r"((uint32_t)(2 * NT))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -127,128 +162,203 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const __nv
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    // kind::f16, D FP32, A and B BF16, both K-major, N = NT, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
-    // one K step (64 values) of A and B into stage s: 16-byte chunks, chunk c of row r
-    // at r * 128 + ((c ^ (r mod 8)) << 4)
-    auto load_step = [&](int kb, int s) {
-        const uint32_t sa = smem_addr(base + s * STAGE), sb = sa + A_BYTES;
-        for (int i = t; i < 128 * 8; i += 128) {
-            const int r = i >> 3, c = i & 7;
-            const bool in = m0 + r < M;
-            const __nv_bfloat16* src = A + (int64_t)(in ? m0 + r : 0) * K + kb * 64 + c * 8;
-            cp16_zfill(sa + r * 128 + ((c ^ (r & 7)) << 4), src, in ? 16u : 0u);
-        }
-        for (int i = t; i < NT * 8; i += 128) {
-            const int r = i >> 3, c = i & 7;
-            cp16_zfill(sb + r * 128 + ((c ^ (r & 7)) << 4), Bt + (int64_t)(n0 + r) * K + kb * 64 + c * 8, 16u);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    bool ok = true;
-    load_step(0, 0);
-    for (int kb = 0; kb < KB && ok; ++kb) {
-        const int s = kb & 1;
-        if (kb + 1 < KB) {
-            // the stage of step kb + 1 was last read by the MMAs of step kb - 1
-            if (kb >= 1) {
-                bool w = true;
-                if ((t & 31) == 0) w = bar_wait(smem_addr(bar + ((kb + 1) & 1)), ((kb - 1) >> 1) & 1);
-                w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
-                if (!w) {
-                    atomicOr(&g_gemm_timeout, 1);
-                    ok = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            int it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                const int m0 = (tile / n_tn) * 128, n0 = (tile % n_tn) * NT;
+                for (int kb = 0; kb < KB; ++kb, ++it) {
+                    const int s = it % S;
+                    if (it >= S && !bar_wait(smem_addr(empty + s), ((it / S) & 1) ^ 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = smem_addr(base + s * G::STAGE), sb = sa + G::A_BYTES, fb = smem_addr(full + s);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(stage_tx)
+                                 : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                        "%3}], [%4];" ::"r"(sa),
+                        "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kb * 64), "r"(m0), "r"(fb)
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                        "%3}], [%4];" ::"r"(sb),
+                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kb * 64), "r"(n0), "r"(fb)
+                        : "memory");
                 }
             }
-            load_step(kb + 1, (kb + 1) & 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (!ok) atomicOr(&g_gemm_timeout, 1);
+            // the copies of the last min(S, it) steps may still be in flight
+            for (int k = it - 1; k >= 0 && k >= it - S; --k)
+                if (!bar_wait(smem_addr(full + k % S), (k / S) & 1)) atomicOr(&g_gemm_timeout, 1);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        ok = __syncthreads_and(ok ? 1 : 0) != 0;
-        if (!ok) break;
-        if (t == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_addr(base + s * STAGE), sb = sa + A_BYTES;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: kind::f16, D FP32, A and B BF16, both K-major, N = NT, M = 128
+            const uint32_t idesc =
+                (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
+            int it = 0, i = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
+                const int acc = i & 1;
+                if (i >= 2 && !bar_wait(smem_addr(tempty + acc), ((i >> 1) & 1) ^ 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(acc * NT);
+                for (int kb = 0; kb < KB; ++kb, ++it) {
+                    const int s = it % S;
+                    if (!bar_wait(smem_addr(full + s), (it / S) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_addr(base + s * G::STAGE), sb = sa + G::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma_f16_tmem(tmem, desc_sw128(sa + kk * 32), desc_sw128(sb + kk * 32), idesc,
-                             (kb > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_f16_tmem(d, desc_sw128(sa + kk * 32), desc_sw128(sb + kk * 32), idesc,
+                                     (kb > 0 || kk > 0) ? 1u : 0u);
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            smem_addr(empty + s))
+                        : "memory");
+                }
+                if (ok)
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            smem_addr(tfull + acc))
+                        : "memory");
+            }
+            if (!ok) atomicOr(&g_gemm_timeout, 1);
+            // every MMA issued has completed once this commit arrives
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(bar + s))
+                             smem_addr(done))
                          : "memory");
+            if (!bar_wait(smem_addr(done), 0)) atomicOr(&g_gemm_timeout, 1);
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, column group (w - 2) / 4
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        constexpr int HC = 32;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+            __syncwarp();
+            const int acc = i & 1;
+            const int m0 = (tile / n_tn) * 128, n0 = (tile % n_tn) * NT;
+            bool w = true;
+            if (lane == 0) w = bar_wait(smem_addr(tfull + acc), (i >> 1) & 1);
+            w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+            if (!w) {
+                if (lane == 0) atomicOr(&g_gemm_timeout, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[HC];
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NT + h * HC);
+#pragma unroll
+            for (int c = 0; c < HC; c += 16) tmem_ld16x(ta + c, *reinterpret_cast<uint32_t(*)[16]>(v + c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(tempty + acc)) : "memory");
+            const int row = m0 + 32 * q + lane;
+            if (row >= M) continue;   // (rows past M hold the zero fill or, for M < 128, stale data)
+            const int col0 = n0 + h * HC;
+            const int64_t o = (int64_t)row * N + col0;
+#pragma unroll
+            for (int c = 0; c < HC; c += 16) {
+                float f[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) f[u] = __uint_as_float(v[c + u]);
+                if (epilogue == 3) {
+#pragma unroll
+                    for (int u = 0; u < 16; u += 4) {
+                        float4* ptr = reinterpret_cast<float4*>(Cf + o + c + u);
+                        float4 a = *ptr;
+                        a.x += f[u]; a.y += f[u + 1]; a.z += f[u + 2]; a.w += f[u + 3];
+                        *ptr = a;
+                    }
+                    continue;
+                }
+                if (bias && epilogue != 0)
+#pragma unroll
+                    for (int u = 0; u < 16; u += 4) {
+                        const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col0 + c + u));
+                        f[u] += b4.x;
+                        f[u + 1] += b4.y;
+                        f[u + 2] += b4.z;
+                        f[u + 3] += b4.w;
+                    }
+                if (epilogue == 1) {
+                    if (Cf)
+#pragma unroll
+                        for (int u = 0; u < 16; u += 4)
+                            *reinterpret_cast<float4*>(Cf + o + c + u) = make_float4(f[u], f[u + 1], f[u + 2], f[u + 3]);
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        pk[u] = pack_bf16(__float2bfloat16(silu_f(f[2 * u])), __float2bfloat16(silu_f(f[2 * u + 1])));
+                    *reinterpret_cast<uint4*>(Cb + o + c) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    *reinterpret_cast<uint4*>(Cb + o + c + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 16; u += 4)
+                        *reinterpret_cast<float4*>(Cf + o + c + u) = make_float4(f[u], f[u + 1], f[u + 2], f[u + 3]);
+                }
+            }
         }
     }
-    // the last step's commit completes after every earlier MMA of the tile
-    if (ok) {
-        bool w = true;
-        if ((t & 31) == 0) w = bar_wait(smem_addr(bar + ((KB - 1) & 1)), ((KB - 1) >> 1) & 1);
-        w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
-        if (!w) {
-            atomicOr(&g_gemm_timeout, 1);
-            ok = false;
-        }
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = m0 + t;
-    const uint32_t lane = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-    for (int c0 = 0; c0 < NT; c0 += 16) {
-        uint32_t v[16];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                     "%12, %13, %14, %15}, [%16];"
-                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                       "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                       "=r"(v[14]), "=r"(v[15])
-                     : "r"(tmem + lane + c0)
-                     : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (!ok || row >= M) continue;
-        const int col = n0 + c0;
-        const int64_t o = (int64_t)row * N + col;
-        float f[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) f[u] = __uint_as_float(v[u]);
-        if (epilogue == 3) {
-#pragma unroll
-            for (int u = 0; u < 16; ++u) Cf[o + u] += f[u];
-            continue;
-        }
-        if (bias && epilogue != 0)
-#pragma unroll
-            for (int u = 0; u < 16; ++u) f[u] += bias[col + u];
-        if (epilogue == 1) {
-            if (Cf)
-#pragma unroll
-                for (int u = 0; u < 16; u += 4)
-                    *reinterpret_cast<float4*>(Cf + o + u) = make_float4(f[u], f[u + 1], f[u + 2], f[u + 3]);
-            uint32_t pk[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                pk[u] = pack_bf16(__float2bfloat16(silu_f(f[2 * u])), __float2bfloat16(silu_f(f[2 * u + 1])));
-            *reinterpret_cast<uint4*>(Cb + o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *reinterpret_cast<uint4*>(Cb + o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-        } else {
-#pragma unroll
-            for (int u = 0; u < 16; u += 4)
-                *reinterpret_cast<float4*>(Cf + o + u) = make_float4(f[u], f[u + 1], f[u + 2], f[u + 3]);
-        }
-    }
+    __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
+        __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NT)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * NT))
                      : "memory");
     }
 }
 
 template <int NT>
 static size_t gemm_smem() {
-    return 1024 + 2 * (size_t)(128 * 128 + NT * 128) + 64;
+    return 1024 + (size_t)GemmShape<NT>::S * GemmShape<NT>::STAGE + 8 * GemmShape<NT>::NBAR + 16;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2-D BF16 row-major matrix [rows][cols] (cols contiguous), box of 64 columns x box_rows
+// rows with the 128-byte swizzle; rows past `rows` read as zero
+static bool make_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, int cols, int box_rows) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 void gemm_tc_prepare() {
@@ -263,18 +373,26 @@ int gemm_tc_timed_out() {
 }
 
 // M a multiple of 64 (rows past a 128-row tile are zero-filled), N 64 or a
-// multiple of 128, K a multiple of 64.  128-column tiles: 128 TMEM columns and
-// 64 KB of operand stages per CTA, so three CTAs share an SM and hide each
-// other's load latency and epilogue.
-void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, const float* bias,
-                      int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s) {
-    if (N == 64) {
-        dim3 grid(1, (M + 127) / 128);
-        k_gemm_tc<64><<<grid, 128, gemm_smem<64>(), s>>>(M, N, K, A, Bt, bias, epilogue, Cb, Cf);
-    } else {
-        dim3 grid(N / 128, (M + 127) / 128);
-        k_gemm_tc<128><<<grid, 128, gemm_smem<128>(), s>>>(M, N, K, A, Bt, bias, epilogue, Cb, Cf);
-    }
+// multiple of 128, K a multiple of 64; A and Bt 16-byte aligned.  One CTA per
+// SM (at most one per tile), two accumulators of NT TMEM columns each.
+cudaError_t launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt,
+                             const float* bias, int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s) {
+    const int NT = N == 64 ? 64 : 128;
+    if (M <= 0 || M % 64 || K <= 0 || K % 64 || (N != 64 && N % 128)) return cudaErrorInvalidValue;
+    // with M = 64 the A box is 64 rows and the MMA's rows 64..127 are never stored
+    const int a_rows = M < 128 ? M : 128;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, A, M, K, a_rows) || !make_map(&tb, Bt, N, K, NT)) return cudaErrorInvalidValue;
+    const uint32_t tx = (uint32_t)(a_rows + NT) * 128u;
+    const int tiles = (N / NT) * ((M + 127) / 128);
+    const int grid = std::min(tiles, sm_count());
+    if (NT == 64)
+        k_gemm_tc<64><<<grid, GemmShape<64>::THREADS, gemm_smem<64>(), s>>>(ta, tb, M, N, K, tx, bias, epilogue, Cb,
+                                                                            Cf);
+    else
+        k_gemm_tc<128><<<grid, GemmShape<128>::THREADS, gemm_smem<128>(), s>>>(ta, tb, M, N, K, tx, bias, epilogue,
+                                                                              Cb, Cf);
+    return cudaGetLastError();
 }
 
 // out[c][r] = in[r][c] (BF16), rows x cols

@@ -12,8 +12,9 @@ namespace rve {
 void gemm_tc_prepare();
 // nonzero once a bounded wait inside the GEMM gave up (sticky for the process)
 int gemm_tc_timed_out();
-void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, const float* bias,
-                      int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s);
+// C = A Bt^T on the tensor cores (TMA-fed); an error if a tensor map cannot be encoded
+cudaError_t launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt,
+                             const float* bias, int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s);
 void launch_transpose_bf16(int rows, int cols, const __nv_bfloat16* in, __nv_bfloat16* out, cudaStream_t s);
 void launch_silu_backward(int64_t n, const float* dY, const float* Z, __nv_bfloat16* g, cudaStream_t s);
 void launch_head_loss(int M, int m_valid, int noutp, const float* z, const float* target, const float* sigma,

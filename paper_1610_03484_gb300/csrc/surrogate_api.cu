@@ -104,20 +104,22 @@ int alloc_work(rve_surrogate s, int M) {
 }
 
 // forward pass of member e on M rows already in s->H[0] (BF16 [M][KIN]); z -> s->zout
-void forward(rve_surrogate s, int e, int M, bool keep_pre) {
+int forward(rve_surrogate s, int e, int M, bool keep_pre) {
     cudaStream_t st = s->ctx->stream;
     for (int l = 0; l < NLAYER; ++l) {
         const int64_t o = layer_w_off(l);
         const __nv_bfloat16* wt = s->Wt[e].as<__nv_bfloat16>() + o;
         const float* b = s->P[e].as<float>() + o + (int64_t)LK[l] * LN[l];
         if (l < NLAYER - 1)
-            launch_gemm_bf16(M, LN[l], LK[l], s->H[l].as<__nv_bfloat16>(), wt, b, 1,
-                             s->H[l + 1].as<__nv_bfloat16>(), keep_pre ? s->Z[l].as<float>() : nullptr, st);
+            RVE_CUDA(launch_gemm_bf16(M, LN[l], LK[l], s->H[l].as<__nv_bfloat16>(), wt, b, 1,
+                                      s->H[l + 1].as<__nv_bfloat16>(), keep_pre ? s->Z[l].as<float>() : nullptr,
+                                      st));
         else
-            launch_gemm_bf16(M, LN[l], LK[l], s->H[l].as<__nv_bfloat16>(), wt, b, 2, nullptr,
-                             s->zout.as<float>(), st);
+            RVE_CUDA(launch_gemm_bf16(M, LN[l], LK[l], s->H[l].as<__nv_bfloat16>(), wt, b, 2, nullptr,
+                                      s->zout.as<float>(), st));
     }
     s->ctx->launches += NLAYER;
+    return RVE_OK;
 }
 
 // Backward pass of member e after forward(keep_pre) and the head loss (dz
@@ -134,13 +136,13 @@ int backward_step(rve_surrogate s, int e, int M, int step, float lr, float* grad
         // dW^T [N][K] = G^T H_l
         launch_transpose_bf16(M, N, Gcur, s->Gt.as<__nv_bfloat16>(), st);
         launch_transpose_bf16(M, K, s->H[l].as<__nv_bfloat16>(), s->Ht.as<__nv_bfloat16>(), st);
-        launch_gemm_bf16(N, K, M, s->Gt.as<__nv_bfloat16>(), s->Ht.as<__nv_bfloat16>(), nullptr, 0, nullptr,
-                         s->gradT.as<float>(), st);
+        RVE_CUDA(launch_gemm_bf16(N, K, M, s->Gt.as<__nv_bfloat16>(), s->Ht.as<__nv_bfloat16>(), nullptr, 0,
+                                  nullptr, s->gradT.as<float>(), st));
         launch_colsum_bf16(M, N, Gcur, s->gradb.as<float>(), st);
         if (l > 0) {
             // dH_l = G W_l^T, then through the silu of layer l-1
-            launch_gemm_bf16(M, K, N, Gcur, s->Wn[e].as<__nv_bfloat16>() + o, nullptr, 0, nullptr,
-                             s->dH.as<float>(), st);
+            RVE_CUDA(launch_gemm_bf16(M, K, N, Gcur, s->Wn[e].as<__nv_bfloat16>() + o, nullptr, 0, nullptr,
+                                      s->dH.as<float>(), st));
             launch_silu_backward((int64_t)M * K, s->dH.as<float>(), s->Z[l - 1].as<float>(),
                                  s->G.as<__nv_bfloat16>(), st);
         }
@@ -260,6 +262,7 @@ int rve_gauss_point_features(rve_ctx c, rve_mesh m, int64_t G, const double* T_C
 int rve_surrogate_train(rve_ctx c, rve_surrogate s, int64_t n, const double* feat, const double* Ct,
                         const double* Kt, const double* Dt, int epochs, int batch, double lr,
                         uint64_t seed, double* loss_history) {
+    NvtxRange nvtx_("surrogate training: %lld points, %d members", (long long)n, s ? s->members : 0);
     RVE_TRY(check_ctx(c));
     if (!s || n < 64 || !feat || !Ct || !Kt || !Dt || epochs < 1 || batch < 64 || batch % 64 || !(lr > 0)) {
         set_error("rve_surrogate_train: invalid argument (n >= 64, batch a multiple of 64)");
@@ -353,7 +356,7 @@ int rve_surrogate_train(rve_ctx c, rve_surrogate s, int64_t n, const double* fea
                 RVE_CUDA(cudaMemcpyAsync(btgt.p, ht.data(), ht.size() * 4, cudaMemcpyHostToDevice, st));
                 launch_features(M, M, KIN, bfeat.as<double>(), dmean.as<float>(), dstd.as<float>(),
                                 s->H[0].as<__nv_bfloat16>(), st);
-                forward(s, e, M, true);
+                RVE_TRY(forward(s, e, M, true));
                 launch_head_loss(M, M, NOUTP, s->zout.as<float>(), btgt.as<float>(), dsig.as<float>(),
                                  s->d_diag.as<uint8_t>(), s->dz.as<__nv_bfloat16>(), s->loss.as<float>(), st);
                 ++step;
@@ -397,7 +400,7 @@ int rve_surrogate_gradients(rve_ctx c, rve_surrogate s, int member, int n, const
     RVE_TRY(upload(dstd, fis.data(), 8, st));
     RVE_CUDA(cudaMemsetAsync(s->loss.p, 0, 4, st));
     launch_features(n, n, KIN, df.as<double>(), dmean.as<float>(), dstd.as<float>(), s->H[0].as<__nv_bfloat16>(), st);
-    forward(s, member, n, true);
+    RVE_TRY(forward(s, member, n, true));
     launch_head_loss(n, n, NOUTP, s->zout.as<float>(), dt.as<float>(), dsig.as<float>(), s->d_diag.as<uint8_t>(),
                      s->dz.as<__nv_bfloat16>(), s->loss.as<float>(), st);
     RVE_TRY(backward_step(s, member, n, 1, 0.f, grads));
@@ -414,6 +417,7 @@ int rve_surrogate_gradients(rve_ctx c, rve_surrogate s, int member, int n, const
 
 // Ensemble prediction on device features: member tensors, mean and spread.
 static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, double* Tm_dev, double* spread_dev) {
+    NvtxRange nvtx_("surrogate inference: %lld points, %d members", (long long)n, s->members);
     cudaStream_t st = s->ctx->stream;
     const int64_t chunk = 65536;
     RVE_TRY(alloc_work(s, (int)chunk));
@@ -429,7 +433,7 @@ static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, doubl
         launch_features(nn, M, KIN, feat_dev + off * 8, dmean.as<float>(), dstd.as<float>(),
                         s->H[0].as<__nv_bfloat16>(), st);
         for (int e = 0; e < s->members; ++e) {
-            forward(s, e, M, false);
+            RVE_TRY(forward(s, e, M, false));
             launch_head_tensors(nn, NOUTP, s->zout.as<float>(), s->d_diag.as<uint8_t>(),
                                 s->Tmem.as<float>() + (size_t)e * nn * 54, st);
         }
