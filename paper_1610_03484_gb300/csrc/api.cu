@@ -432,9 +432,10 @@ struct Solver {
         RVE_TRY(m->mpart.ensure(np * 12 * 8));
         RVE_TRY(m->gsum.ensure((size_t)ncols * 12 * 8));
         RVE_TRY(m->msum.ensure((size_t)ncols * 12 * 8));
-        // col state: rz, rz0, alpha, beta (4*ncols) + mu (12*ncols) + schur (144*ncols) doubles,
+        // col state: rz, rz0, alpha, beta (4*ncols) + mu (12*ncols) + schur (144*ncols) + the fused
+        // iteration's pq and rz accumulators (2*ACC_SLOTS*ncols) doubles,
         // then active, iters (ints) and flags
-        const size_t nd = (size_t)ncols * (4 + 12 + 144);
+        const size_t nd = (size_t)ncols * (4 + 12 + 144 + 2 * ACC_SLOTS);
         RVE_TRY(m->colstate.ensure(nd * 8 + (size_t)ncols * 12 + 64));
         double* base = m->colstate.as<double>();
         cs64.rz = base;
@@ -443,6 +444,8 @@ struct Solver {
         cs64.beta = base + 3 * ncols;
         cs64.mu = base + 4 * ncols;
         cs64.schur = base + 16 * ncols;
+        cs64.pq_acc = base + 160 * ncols;
+        cs64.rz_acc = base + (160 + ACC_SLOTS) * ncols;
         int32_t* ib = reinterpret_cast<int32_t*>(base + nd);
         cs64.active = ib;
         cs64.iters = ib + ncols;
@@ -577,6 +580,16 @@ struct Solver {
         Launch Lop = L;
         Lop.nby_op = operator_grid_y<T>(m->p, f.nc, L, m->nt);
         Lop.n_colour = det ? m->ncolour : 0;
+        // fused iteration (four kernels: operator, update, beta + loop control,
+        // p-update): FP64 atomic accumulators replace the alpha and beta partial-row
+        // reductions.  Not with constraint rows (their multipliers need the partial
+        // rows), the tensor-core operator or the deterministic mode (atomic order).
+        const bool fused = !det && !use_tc && f.m == 0;
+        if (fused) {
+            Lop.energy_acc = cs.pq_acc;
+            RVE_CUDA(cudaMemsetAsync(cs.pq_acc, 0, sizeof(double) * 2 * ACC_SLOTS * ncols, s));   // pq_acc, rz_acc
+        }
+        const int kernels_per_iter = fused ? 4 : 6;
         RVE_CUDA(cudaMemcpyAsync(const_cast<double*>(cs.tol), &tol, sizeof(double), cudaMemcpyHostToDevice, s));
         RowView<T> rvw = rv<T>(scale);
         ElemView<T> evw = ev<T>(scale);
@@ -617,6 +630,8 @@ struct Solver {
             Launch Lx = Lx0;
             Lx.nby_op = Lop.nby_op;
             Lx.n_colour = Lop.n_colour;
+            Lx.energy_acc = Lop.energy_acc;
+            double* epart_it = fused ? nullptr : m->epart.as<double>();
             evr(0, Lx.stream);
             if constexpr (sizeof(T) == 4) {
                 if (use_tc) {
@@ -626,24 +641,29 @@ struct Solver {
                         cs.n_list, Lx.op_rows(), cs.flags, Lx.stream);
                     if (e != cudaSuccess) tc_err = e;
                 } else {
-                    launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active, cs.list,
-                                       cs.n_list);
+                    launch_operator<T>(m->p, f.nc, false, evw, p, q, epart_it, Lx, cs.active, cs.list, cs.n_list);
                 }
             } else {
-                launch_operator<T>(m->p, f.nc, false, evw, p, q, m->epart.as<double>(), Lx, cs.active, cs.list,
-                                   cs.n_list);
+                launch_operator<T>(m->p, f.nc, false, evw, p, q, epart_it, Lx, cs.active, cs.list, cs.n_list);
             }
             evr(1, Lx.stream);
-            launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
+            if (!fused) launch_finalize_alpha<T>(m->epart.as<double>(), cs, Lx);
             evr(2, Lx.stream);
-            launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx, m->cpart.as<double>());
-            evr(3, Lx.stream);
-            launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, Lx);
-            if (loop_ctl)
-                launch_compact_continue(cs.active, ncols, cs.list, cs.n_list, loop_handle, cs.flags + 1, max_iter,
-                                        Lx.stream);
+            if (fused)
+                launch_update_fused<T>(rvw, x, r, p, q, cs, Lx);
             else
-                launch_compact_active(cs.active, ncols, cs.list, cs.n_list, Lx.stream);
+                launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), true, Lx, m->cpart.as<double>());
+            evr(3, Lx.stream);
+            if (fused) {
+                launch_beta_compact_continue(cs, ncols, loop_handle, cs.flags + 1, max_iter, loop_ctl, Lx.stream);
+            } else {
+                launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, false, Lx);
+                if (loop_ctl)
+                    launch_compact_continue(cs.active, ncols, cs.list, cs.n_list, loop_handle, cs.flags + 1,
+                                            max_iter, Lx.stream);
+                else
+                    launch_compact_active(cs.active, ncols, cs.list, cs.n_list, Lx.stream);
+            }
             evr(4, Lx.stream);
             launch_pupdate<T>(rvw, r, p, q, cs, false, Lx);
             evr(5, Lx.stream);
@@ -657,7 +677,7 @@ struct Solver {
             // reused while every captured parameter is unchanged (the tolerance
             // lives in device memory).
             struct Key {
-                int ncols, cpb, rows, nby, nby_op, p, nc, m, max_iter, tc, ncolour;
+                int ncols, cpb, rows, nby, nby_op, p, nc, m, max_iter, tc, ncolour, fused;
                 int64_t n_rows, n_sup, nt, n_nodes;
                 const void* ptr[19];
             } key;
@@ -677,6 +697,7 @@ struct Solver {
             key.n_nodes = evw.n_nodes;
             key.tc = use_tc ? 1 : 0;
             key.ncolour = Lop.n_colour;
+            key.fused = fused ? 1 : 0;
             const void* ptrs[19] = {x, r, p, q, m->epart.p, m->rzp.p, m->cpart.p, cs.rz, rvw.scale, rvw.diag,
                                     rvw.mask, rvw.sup_row, rvw.sup_coef, rvw.sup_of_row, evw.edofs, evw.geo,
                                     evw.mat, evw.phase, use_tc ? m->d_ke32.p : nullptr};
@@ -733,13 +754,13 @@ struct Solver {
             int32_t loops = 0;
             RVE_CUDA(cudaMemcpyAsync(&loops, cs.flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             RVE_TRY(read_active());
-            *launches += (int64_t)loops * 6;
+            *launches += (int64_t)loops * kernels_per_iter;
             conv = n_act == 0;
         } else {
             RVE_TRY(read_active());
             for (int it = 0; it < max_iter && n_act > 0; ++it) {
                 iteration(L);
-                *launches += 6;
+                *launches += kernels_per_iter;
                 RVE_CUDA(cudaGetLastError());
                 if (tc_err != cudaSuccess) {
                     set_error(std::string("tensor-core operator launch: ") + cudaGetErrorString(tc_err));
@@ -897,13 +918,16 @@ struct Solver {
                             any_alpha |= sc32[2 * c + ph] != 0.0f;
                         }
                     if (any_alpha) {
-                        // r0 -= alpha K_deg u_macro (macro load only, double-float)
-                        float* lo = m->q32.as<float>();
-                        RVE_TRY(upload(m->dscale32, sc32.data(), sc32.size(), s));
-                        RVE_CUDA(cudaMemsetAsync(lo, 0, nv * 4, s));
-                        launch_residual_df(m->p, f.nc, ev<float>(m->dscale32), nullptr, nullptr, r64, lo, L);
-                        launch_axpy_f2d((int64_t)nv, lo, r64, s);
-                        *launches += 2;
+                        // r0 -= alpha K_deg u_macro: the macro load of each phase at unit
+                        // modulus is cached per mesh (the right-hand side's bph, formed by
+                        // the same double-float operator), so this is a column combination
+                        std::vector<double> sc64((size_t)ncols * 2);
+                        for (int c = 0; c < ncols; ++c)
+                            for (int ph = 0; ph < 2; ++ph) sc64[2 * c + ph] = warm->alpha[c] * warm->degrade[ph];
+                        RVE_TRY(upload(m->dscale64, sc64.data(), sc64.size(), s));
+                        launch_rhs_combine(n_rows, B, m->bph[fid].as<double>(), m->dscale64.as<double>(), r64, s,
+                                           true);
+                        *launches += 1;
                     }
                 }
             } else {

@@ -175,7 +175,7 @@ struct PartialSum<float> {
 // and store them to out[(blockIdx.y * ncols + col) * nacc + a].
 template <int NACC>
 __device__ __forceinline__ void block_column_reduce(const double (&acc)[NACC], double* out,
-                                                    int ncols, int cpb, int col) {
+                                                    int ncols, int cpb, int col, double* atomic_out = nullptr) {
     __shared__ double buf[256];
     const int rows = blockDim.x / cpb;
     const int cl = threadIdx.x % cpb, r = threadIdx.x / cpb;
@@ -186,7 +186,10 @@ __device__ __forceinline__ void block_column_reduce(const double (&acc)[NACC], d
         if (r == 0) {
             double s = 0.0;
             for (int q = 0; q < rows; ++q) s += buf[q * cpb + cl];
-            out[((int64_t)blockIdx.y * ncols + col) * NACC + a] = s;
+            if (atomic_out)   // fused iteration: one FP64 accumulator per column
+                atomicAdd(atomic_out + (int64_t)col * NACC + a, s);
+            else
+                out[((int64_t)blockIdx.y * ncols + col) * NACC + a] = s;
         }
         __syncthreads();
     }
@@ -231,7 +234,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
                                                   T* __restrict__ y, double* __restrict__ epart,
                                                   const int32_t* __restrict__ active, int ncols,
                                                   int cpb, const int32_t* __restrict__ list,
-                                                  const int32_t* __restrict__ n_list) {
+                                                  const int32_t* __restrict__ n_list,
+                                                  double* __restrict__ eacc) {
     constexpr int NE = Order<P>::NE;
     constexpr int NM = Order<P>::NM;
     // With a column list the block's threads are spread over the listed (active)
@@ -373,7 +377,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
                     V[m][k][c] = w;
                 }
         }
-        if (epart && !MACRO) energy.add(e_elem);
+        if ((epart || eacc) && !MACRO) energy.add(e_elem);
         // ---- backward and scatter: y_j,c = sum_m sum_k A[k][m][j] W[m][k][c]
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -402,9 +406,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P == 1) ? 4 : ((sizeof
             for (int c = 0; c < NC; ++c) atomicAdd(y + vix<NC>(dj, c, ncols, col), yj[c]);
         }
     }
-    if (epart) {
+    if (epart || eacc) {
         double acc[1] = {energy.value()};
-        block_column_reduce<1>(acc, epart, ncols, cpb_e, col);
+        block_column_reduce<1>(acc, epart, ncols, cpb_e, col,
+                               eacc ? eacc + (size_t)(blockIdx.y % ACC_SLOTS) * ncols : nullptr);
     }
 }
 
@@ -451,7 +456,7 @@ void launch_operator(int p, int nc, bool macro, const ElemView<T>& ev, const T* 
     if (p == PP && nc == NCC && macro == MM) {                                                  \
         k_operator<PP, NCC, T, MM><<<grid, block, 0, L.stream>>>(ev, x, y, energy_partial,      \
                                                                  active, L.ncols, L.cpb, list, \
-                                                                 n_list);                      \
+                                                                 n_list, L.energy_acc);        \
         return;                                                                                 \
     }
     RVE_OP_CASE(1, 3, false) RVE_OP_CASE(2, 3, false) RVE_OP_CASE(3, 3, false)
@@ -473,10 +478,10 @@ template void launch_operator<double>(int, int, bool, const ElemView<double>&, c
 // while some column is active and fewer than max_iter iterations have run; one
 // thread sets the condition, whose value the node reads when the body ends.
 template <bool CTL>
-__global__ void __launch_bounds__(256) k_compact_active(const int32_t* __restrict__ active, int ncols,
-                                                        int32_t* __restrict__ list, int32_t* __restrict__ n_list,
-                                                        cudaGraphConditionalHandle h, int32_t* __restrict__ counter,
-                                                        int max_iter) {
+__device__ __forceinline__ void compact_and_control(const int32_t* __restrict__ active, int ncols,
+                                                    int32_t* __restrict__ list, int32_t* __restrict__ n_list,
+                                                    cudaGraphConditionalHandle h, int32_t* __restrict__ counter,
+                                                    int max_iter) {
     __shared__ int counts[8];
     __shared__ int base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -504,6 +509,52 @@ __global__ void __launch_bounds__(256) k_compact_active(const int32_t* __restric
             cudaGraphSetConditional(h, (base > 0 && n < max_iter) ? 1u : 0u);
         }
     }
+}
+
+template <bool CTL>
+__global__ void __launch_bounds__(256) k_compact_active(const int32_t* __restrict__ active, int ncols,
+                                                        int32_t* __restrict__ list, int32_t* __restrict__ n_list,
+                                                        cudaGraphConditionalHandle h, int32_t* __restrict__ counter,
+                                                        int max_iter) {
+    compact_and_control<CTL>(active, ncols, list, n_list, h, counter, max_iter);
+}
+
+// Fused iteration, one block: per active column rz from the update's accumulator,
+// beta = rz / rz_old, the convergence test (the general path's beta kernel without
+// constraint rows); both accumulators cleared for the next iteration; then the
+// active list and, with CTL, the loop control.
+template <bool CTL>
+__global__ void __launch_bounds__(256) k_beta_compact(ColState cs, int ncols, cudaGraphConditionalHandle h,
+                                                      int32_t* __restrict__ counter, int max_iter) {
+    const double tol = *cs.tol;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        if (cs.active[c]) {
+            double rz = 0.0;
+            for (int k = 0; k < ACC_SLOTS; ++k) rz += cs.rz_acc[(size_t)k * ncols + c];
+            if (!isfinite(rz)) {
+                atomicOr(cs.flags, 1);
+                cs.active[c] = 0;
+            } else {
+                cs.beta[c] = rz / cs.rz[c];
+                cs.rz[c] = rz;
+                if (rz <= tol * tol * cs.rz0[c]) cs.active[c] = 0;
+            }
+        }
+        for (int k = 0; k < ACC_SLOTS; ++k) {
+            cs.rz_acc[(size_t)k * ncols + c] = 0.0;
+            cs.pq_acc[(size_t)k * ncols + c] = 0.0;
+        }
+    }
+    __syncthreads();
+    compact_and_control<CTL>(cs.active, ncols, cs.list, cs.n_list, h, counter, max_iter);
+}
+
+void launch_beta_compact_continue(ColState cs, int ncols, cudaGraphConditionalHandle h, int32_t* counter,
+                                  int max_iter, bool ctl, cudaStream_t s) {
+    if (ctl)
+        k_beta_compact<true><<<1, 256, 0, s>>>(cs, ncols, h, counter, max_iter);
+    else
+        k_beta_compact<false><<<1, 256, 0, s>>>(cs, ncols, 0, nullptr, 0);
 }
 
 void launch_compact_active(const int32_t* active, int ncols, int32_t* list, int32_t* n_list, cudaStream_t s) {
@@ -604,7 +655,7 @@ __global__ void __launch_bounds__(256, 2) k_residual_df(ElemView<float> ev, cons
                 float x0h[NC], x0l[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const int64_t i0 = ((int64_t)d0 * NC + c) * ncols + col;
+                    const uint32_t i0 = vix<NC>(d0, c, ncols, col);
                     x0h[c] = -xh[i0];
                     x0l[c] = -xl[i0];
                 }
@@ -613,7 +664,7 @@ __global__ void __launch_bounds__(256, 2) k_residual_df(ElemView<float> ev, cons
                     const int dk = __ldg(ed + k + 1);
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
-                        const int64_t ik = ((int64_t)dk * NC + c) * ncols + col;
+                        const uint32_t ik = vix<NC>(dk, c, ncols, col);
                         Vh[0][k][c] = xh[ik];
                         Vl[0][k][c] = xl[ik];
                         df_add(Vh[0][k][c], Vl[0][k][c], x0h[c], x0l[c]);
@@ -627,7 +678,7 @@ __global__ void __launch_bounds__(256, 2) k_residual_df(ElemView<float> ev, cons
                 float vh[NC], vl[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const int64_t ij = ((int64_t)dj * NC + c) * ncols + col;
+                    const uint32_t ij = vix<NC>(dj, c, ncols, col);
                     vh[c] = xh[ij];
                     vl[c] = xl[ij];
                 }
@@ -740,12 +791,12 @@ __global__ void __launch_bounds__(256, 2) k_residual_df(ElemView<float> ev, cons
                 float sh = Vh[0][0][c], sl = Vl[0][0][c];
                 df_add(sh, sl, Vh[0][1][c], Vl[0][1][c]);
                 df_add(sh, sl, Vh[0][2][c], Vl[0][2][c]);
-                const int64_t i0 = ((int64_t)__ldg(ed) * NC + c) * ncols + col;
+                const uint32_t i0 = vix<NC>(__ldg(ed), c, ncols, col);
                 atomicAdd(r + i0, (double)sh);
                 atomicAdd(rlo + i0, sl);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const int64_t ik = ((int64_t)__ldg(ed + k + 1) * NC + c) * ncols + col;
+                    const uint32_t ik = vix<NC>(__ldg(ed + k + 1), c, ncols, col);
                     atomicAdd(r + ik, (double)-Vh[0][k][c]);
                     atomicAdd(rlo + ik, -Vl[0][k][c]);
                 }
@@ -769,7 +820,7 @@ __global__ void __launch_bounds__(256, 2) k_residual_df(ElemView<float> ev, cons
             const int dj = __ldg(ed + j);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const int64_t ij = ((int64_t)dj * NC + c) * ncols + col;
+                const uint32_t ij = vix<NC>(dj, c, ncols, col);
                 atomicAdd(r + ij, (double)-yh[c]);
                 atomicAdd(rlo + ij, -yl[c]);
             }
@@ -1318,6 +1369,85 @@ template void launch_update<float>(const RowView<float>&, float*, float*, const 
                                    ColState, double*, bool, const Launch&, double*);
 template void launch_update<double>(const RowView<double>&, double*, double*, const double*,
                                     const double*, ColState, double*, bool, const Launch&, double*);
+
+// Fused iteration (no constraint rows): every thread forms its column's step
+// alpha = rz / pq from the operator's accumulated energy itself (the separate
+// alpha kernel of the general path is dropped), then x += alpha p, r -= alpha q
+// and (r, M^-1 r) into rz_acc.  Block (x, 0), row 0 records alpha and the
+// iteration, and deactivates a column whose pq is not positive or alpha not
+// finite; every other block reaches the same alpha = 0 for it on its own.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_update_fused(RowView<T> rv, T* __restrict__ x, T* __restrict__ r,
+                                                      const T* __restrict__ p, const T* __restrict__ q,
+                                                      ColState cs, int ncols, int cpb) {
+    const int rows = blockDim.x / cpb;
+    const int cl = threadIdx.x % cpb, rr = threadIdx.x / cpb;
+    const int col = blockIdx.x * cpb + cl;
+    // the block's first row of threads forms alpha for its columns (one FP64
+    // division per column and block: FP64 runs at a small fraction of the FP32 rate)
+    __shared__ double s_alpha[256];
+    __shared__ int s_state[256];
+    if (rr == 0) {
+        const bool act = cs.active[col] != 0 && !(cs.flags[0] & 4);
+        double a = 0.0;
+        int st = act ? 1 : 0;
+        if (act) {
+            double pq = 0.0;
+#pragma unroll
+            for (int k = 0; k < ACC_SLOTS; ++k) pq += cs.pq_acc[(size_t)k * ncols + col];
+            a = cs.rz[col] / pq;
+            if (!(pq > 0.0) || !isfinite(a)) {
+                a = 0.0;
+                st = 2;
+            }
+        }
+        s_alpha[cl] = a;
+        s_state[cl] = st;
+    }
+    __syncthreads();
+    const double a64 = s_alpha[cl];
+    const bool was_active = s_state[cl] != 0, bad = s_state[cl] == 2;
+    if (blockIdx.y == 0 && rr == 0) {
+        if (was_active && !bad) {
+            cs.alpha[col] = a64;
+            cs.iters[col] += 1;
+        } else {
+            cs.alpha[col] = 0.0;
+            if (bad) atomicOr(cs.flags, 1);
+            if (cs.active[col]) cs.active[col] = 0;
+        }
+    }
+    const T a = (T)a64;
+    const ColJacobi<T, NC> jac(rv, col);
+    PartialSum<T> acc;
+    const int64_t i_end = (was_active && !bad) ? rv.n_rows : 0;
+    const int64_t stride = (int64_t)gridDim.y * rows;
+    for (int64_t i = (int64_t)blockIdx.y * rows + rr; i < i_end; i += stride) {
+        const int64_t idx = i * ncols + col;
+        const T pv = p[idx], qv = q[idx], xv = x[idx];
+        T rv_ = r[idx];
+        x[idx] = fma(a, pv, xv);
+        rv_ = fma(-a, qv, rv_);
+        r[idx] = rv_;
+        const T w = jac.inv(i) * rv_;
+        acc.add(rv_ * w);
+    }
+    double accs[1] = {acc.value()};
+    block_column_reduce<1>(accs, nullptr, ncols, cpb, col, cs.rz_acc + (size_t)(blockIdx.y % ACC_SLOTS) * ncols);
+}
+
+template <typename T>
+void launch_update_fused(const RowView<T>& rv, T* x, T* r, const T* p, const T* q, ColState cs, const Launch& L) {
+    dim3 grid(L.ncols / L.cpb, L.nby), block(L.cpb * L.rows_per_block);
+    if (rv.nc == 3)
+        k_update_fused<T, 3><<<grid, block, 0, L.stream>>>(rv, x, r, p, q, cs, L.ncols, L.cpb);
+    else
+        k_update_fused<T, 1><<<grid, block, 0, L.stream>>>(rv, x, r, p, q, cs, L.ncols, L.cpb);
+}
+template void launch_update_fused<float>(const RowView<float>&, float*, float*, const float*, const float*, ColState,
+                                         const Launch&);
+template void launch_update_fused<double>(const RowView<double>&, double*, double*, const double*, const double*,
+                                          ColState, const Launch&);
 
 // partial C M^-1 r over the constraint support (m <= 12 rows)
 template <typename T>
@@ -1939,7 +2069,7 @@ template void launch_combine_columns<float>(int64_t, int, int, const int32_t*, c
 
 // b[row][6r + c] = -(s0 y0[row][c] + s1 y1[row][c]) with the column's phase scales
 __global__ void k_rhs_combine(int64_t n_rows, int nrve, const double* __restrict__ y,
-                              const double* __restrict__ scale, double* __restrict__ b) {
+                              const double* __restrict__ scale, double* __restrict__ b, int accumulate) {
     const int ncols = 6 * nrve;
     const int64_t n = n_rows * ncols;
     const double* y1 = y + n_rows * 6;
@@ -1947,16 +2077,17 @@ __global__ void k_rhs_combine(int64_t n_rows, int nrve, const double* __restrict
         const int64_t row = i / ncols;
         const int col = (int)(i % ncols);
         const int c = col % 6;
-        b[i] = -(scale[2 * col] * y[row * 6 + c] + scale[2 * col + 1] * y1[row * 6 + c]);
+        const double v = -(scale[2 * col] * y[row * 6 + c] + scale[2 * col + 1] * y1[row * 6 + c]);
+        b[i] = accumulate ? b[i] + v : v;
     }
 }
 
 void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool accumulate) {
     int64_t blocks = (n_rows * 6 * nrve + 255) / 256;
     if (blocks > sm_count() * 16) blocks = sm_count() * 16;
     if (blocks < 1) blocks = 1;
-    k_rhs_combine<<<(unsigned)blocks, 256, 0, s>>>(n_rows, nrve, y, scale, b);
+    k_rhs_combine<<<(unsigned)blocks, 256, 0, s>>>(n_rows, nrve, y, scale, b, accumulate ? 1 : 0);
 }
 
 // ---------------------------------------------------------- elementwise

@@ -20,6 +20,8 @@ struct Launch {
     int nby_op = 0;       // grid.y of the operator and rows of its energy partials (0: nby)
     int n_colour = 0;     // deterministic mode: element colours, one operator launch (and one
                           // block of op_rows() partial rows) per colour
+    double* energy_acc = nullptr;   // fused iteration: the operator adds its per-column energy
+                                    // here (FP64 atomics) instead of writing partial rows
     cudaStream_t stream = 0;
     int op_rows() const { return nby_op > 0 ? nby_op : nby; }
     int op_partials() const { return op_rows() * (n_colour > 0 ? n_colour : 1); }
@@ -87,7 +89,14 @@ struct ColState {
     int32_t* n_list;  // [1] their number
     const double* tol;  // [1] relative tolerance on sqrt(rz / rz0), in device memory so that a
                         // captured iteration graph can be reused with another tolerance
+    // fused iteration (no constraint rows, not deterministic): the operator adds its
+    // per-column energies into pq_acc and the update its (r, z) into rz_acc with FP64
+    // atomics, block y into slot y % ACC_SLOTS (fewer atomics per address); the
+    // loop-control kernel sums the slots and clears them
+    double* pq_acc = nullptr;   // [ACC_SLOTS][ncols]
+    double* rz_acc = nullptr;   // [ACC_SLOTS][ncols]
 };
+constexpr int ACC_SLOTS = 8;
 
 void upload_basis_tables();
 // SMs of the current device (cached per device ordinal)
@@ -183,12 +192,21 @@ void launch_split_d2ff(int64_t n, const double* x, float* xh, float* xl, cudaStr
 
 // the compaction above, plus the device-side PCG loop control: counter += 1;
 // condition = any active && counter < max_iter
+// Fused iteration: x += alpha p, r -= alpha q with alpha = rz / pq_acc formed by every
+// thread for its column (no separate alpha kernel), (r, M^-1 r) added into rz_acc.
+template <typename T>
+void launch_update_fused(const RowView<T>& rv, T* x, T* r, const T* p, const T* q, ColState cs, const Launch& L);
+// Fused iteration: beta, rz and convergence per column from rz_acc, both accumulators
+// cleared, then the active list and the loop control (one block).
+void launch_beta_compact_continue(ColState cs, int ncols, cudaGraphConditionalHandle h, int32_t* counter,
+                                  int max_iter, bool ctl, cudaStream_t s);
 void launch_compact_continue(const int32_t* active, int ncols, int32_t* list, int32_t* n_list,
                              cudaGraphConditionalHandle h, int32_t* counter, int max_iter, cudaStream_t s);
 
-// right-hand sides of a batch from the per-phase macro loads y = [2][n_rows][6]
+// right-hand sides of a batch from the per-phase macro loads y = [2][n_rows][6]:
+// b = -(scale_0 y_0 + scale_1 y_1) per column (accumulate: b += that instead)
 void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,
-                        cudaStream_t s);
+                        cudaStream_t s, bool accumulate = false);
 
 // elementwise helpers
 void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);

@@ -100,7 +100,8 @@ __device__ int g_gemm_timeout;   // set when a bounded wait of the GEMM gave up
 }  // namespace
 
 // epilogue: 0 = store FP32 only, 1 = bias + silu -> BF16 (pre-activation to Cf if non-null),
-//           2 = bias, FP32 out, 3 = accumulate FP32 into Cf (C += A B)
+//           2 = bias, FP32 out, 3 = accumulate FP32 into Cf (C += A B),
+//           4 = bias, FP32 out transposed (Cf[col * M + row])
 //
 // Persistent and warp-specialised: each CTA walks the output tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ... (the N tiles of one row block are
@@ -125,6 +126,8 @@ struct GemmShape {
     // epilogue warps: four lane quarters x column groups of 32
     static constexpr int EPI_WARPS = 4 * (NT / 32), THREADS = 64 + 32 * EPI_WARPS;
     static constexpr int NBAR = 2 * S + 5;
+    // bias vector staged in shared memory (N <= BIAS_MAX) behind the barriers
+    static constexpr int BIAS_OFF = ((8 * NBAR + 16 + 15) / 16) * 16, BIAS_MAX = 256;
 };
 
 template <int NT>
@@ -142,8 +145,12 @@ __global__ void __launch_bounds__(GemmShape<NT>::THREADS, 1)
     uint64_t* tempty = tfull + 2;   // [2]
     uint64_t* done = tempty + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    float* sbias = reinterpret_cast<float*>(base + S * G::STAGE + G::BIAS_OFF);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int KB = K / 64, n_tn = N / NT, n_tiles = ((M + 127) / 128) * n_tn;
+    const bool bias_smem = bias != nullptr && (epilogue == 1 || epilogue == 2 || epilogue == 4) && N <= G::BIAS_MAX;
+    if (bias_smem)
+        for (int i = t; i < N; i += blockDim.x) sbias[i] = __ldg(bias + i);
     if (t == 0) {
         for (int k = 0; k < G::NBAR; ++k) {
             const uint32_t cnt = (k == 2 * S + 2 || k == 2 * S + 3) ? (uint32_t)G::EPI_WARPS : 1u;
@@ -285,7 +292,16 @@ __global__ void __launch_bounds__(GemmShape<NT>::THREADS, 1)
                     }
                     continue;
                 }
-                if (bias && epilogue != 0)
+                if (bias_smem) {
+#pragma unroll
+                    for (int u = 0; u < 16; u += 4) {
+                        const float4 b4 = *reinterpret_cast<const float4*>(sbias + col0 + c + u);
+                        f[u] += b4.x;
+                        f[u + 1] += b4.y;
+                        f[u + 2] += b4.z;
+                        f[u + 3] += b4.w;
+                    }
+                } else if (bias && epilogue != 0 && epilogue != 3) {
 #pragma unroll
                     for (int u = 0; u < 16; u += 4) {
                         const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col0 + c + u));
@@ -294,6 +310,12 @@ __global__ void __launch_bounds__(GemmShape<NT>::THREADS, 1)
                         f[u + 2] += b4.z;
                         f[u + 3] += b4.w;
                     }
+                }
+                if (epilogue == 4) {   // bias, FP32, transposed: Cf[col][row] (rows adjacent across lanes)
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) Cf[(int64_t)(col0 + c + u) * M + row] = f[u];
+                    continue;
+                }
                 if (epilogue == 1) {
                     if (Cf)
 #pragma unroll
@@ -326,7 +348,8 @@ __global__ void __launch_bounds__(GemmShape<NT>::THREADS, 1)
 
 template <int NT>
 static size_t gemm_smem() {
-    return 1024 + (size_t)GemmShape<NT>::S * GemmShape<NT>::STAGE + 8 * GemmShape<NT>::NBAR + 16;
+    return 1024 + (size_t)GemmShape<NT>::S * GemmShape<NT>::STAGE + GemmShape<NT>::BIAS_OFF +
+           4 * GemmShape<NT>::BIAS_MAX;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
@@ -544,9 +567,9 @@ void launch_features(int n, int M, int kin, const double* feat, const float* mea
 }
 
 // L L^T of one lower-triangular factor of size NN stored row-major from L[OFF]
-// into out[OO ..] (compile-time indices keep L in registers).
+// into out[(OO + i NN + j) * n] (compile-time indices keep L in registers).
 template <int NN, int OFF, int OO>
-__device__ __forceinline__ void head_block(const float (&L)[33], float* out) {
+__device__ __forceinline__ void head_block_t(const float (&L)[33], float* __restrict__ out, int n) {
 #pragma unroll
     for (int i = 0; i < NN; ++i)
 #pragma unroll
@@ -555,47 +578,50 @@ __device__ __forceinline__ void head_block(const float (&L)[33], float* out) {
 #pragma unroll
             for (int q = 0; q <= (i < j ? i : j); ++q)
                 acc = fmaf(L[OFF + i * (i + 1) / 2 + q], L[OFF + j * (j + 1) / 2 + q], acc);
-            out[OO + i * NN + j] = acc;
+            out[(int64_t)(OO + i * NN + j) * n] = acc;
         }
 }
 
-// Head: z [M][noutp] of member e -> factor entries (softplus diagonals), member
-// tensors L L^T into Te [n][54] (C 36, K 9, D 9).  FP32 arithmetic (the network
-// itself is BF16 with FP32 accumulation; FP64 runs at a small fraction of the FP32
-// rate on this GPU).
-__global__ void k_head_tensors(int n, int noutp, const float* __restrict__ z, const uint8_t* __restrict__ diag,
-                               float* __restrict__ Te) {
+// Head: zT [noutp][ldz] (the last layer's output, transposed) of member e ->
+// factor entries (softplus diagonals), member tensors L L^T into TeT [54][n]
+// (C 36, K 9, D 9; transposed, so that adjacent threads touch adjacent words).
+// FP32 arithmetic (the network itself is BF16 with FP32 accumulation; FP64 runs
+// at a small fraction of the FP32 rate on this GPU).
+__global__ void k_head_tensors(int n, int ldz, const float* __restrict__ zT, const uint8_t* __restrict__ diag,
+                               float* __restrict__ TeT) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     float L[33];
 #pragma unroll
     for (int c = 0; c < 33; ++c) {
-        const float zz = z[(int64_t)r * noutp + c];
+        const float zz = zT[(int64_t)c * ldz + r];
         L[c] = diag[c] ? (zz > 20.f ? zz : log1pf(expf(zz))) : zz;
     }
-    float* out = Te + (int64_t)r * 54;
-    head_block<6, 0, 0>(L, out);
-    head_block<3, 21, 36>(L, out);
-    head_block<3, 27, 45>(L, out);
+    float* out = TeT + r;
+    head_block_t<6, 0, 0>(L, out, n);
+    head_block_t<3, 21, 36>(L, out, n);
+    head_block_t<3, 27, 45>(L, out, n);
 }
 
-void launch_head_tensors(int n, int noutp, const float* z, const uint8_t* diag, float* Te, cudaStream_t s) {
-    k_head_tensors<<<(n + 127) / 128, 128, 0, s>>>(n, noutp, z, diag, Te);
+void launch_head_tensors(int n, int ldz, const float* zT, const uint8_t* diag, float* TeT, cudaStream_t s) {
+    k_head_tensors<<<(n + 127) / 128, 128, 0, s>>>(n, ldz, zT, diag, TeT);
 }
 
-// Mean over the members of entries [LO, HI) of row r (written to Tm in FP64) and
-// the largest relative member deviation max_e ||T_e - mean|| / ||mean|| over them.
+// Mean over the members of entries [LO, HI) of point r (member tensors T
+// [members][54][n], transposed) into the block's staging rows, and the largest
+// relative member deviation max_e ||T_e - mean|| / ||mean|| over them.
+constexpr int ENS_BLOCK = 64, ENS_LD = 55;
 template <int LO, int HI>
 __device__ __forceinline__ float ensemble_block(int n, int r, int members, const float* __restrict__ T,
-                                                double* __restrict__ Tm) {
+                                                double* __restrict__ stage) {
     float mean[HI - LO];
     const float inv = 1.f / (float)members;
 #pragma unroll
     for (int c = 0; c < HI - LO; ++c) {
         float sacc = 0.f;
-        for (int e = 0; e < members; ++e) sacc += T[((int64_t)e * n + r) * 54 + LO + c];
+        for (int e = 0; e < members; ++e) sacc += T[((int64_t)e * 54 + LO + c) * n + r];
         mean[c] = sacc * inv;
-        Tm[(int64_t)r * 54 + LO + c] = (double)mean[c];
+        stage[LO + c] = (double)mean[c];
     }
     float den = 0.f;
 #pragma unroll
@@ -605,7 +631,7 @@ __device__ __forceinline__ float ensemble_block(int n, int r, int members, const
         float num = 0.f;
 #pragma unroll
         for (int c = 0; c < HI - LO; ++c) {
-            const float d = T[((int64_t)e * n + r) * 54 + LO + c] - mean[c];
+            const float d = T[((int64_t)e * 54 + LO + c) * n + r] - mean[c];
             num = fmaf(d, d, num);
         }
         const float q = den > 0.f ? sqrtf(num / den) : 0.f;
@@ -615,19 +641,28 @@ __device__ __forceinline__ float ensemble_block(int n, int r, int members, const
 }
 
 // Ensemble mean and spread: Tm [n][54] = mean over members (FP64 storage),
-// spread[n] = max over the three tensors of max_e ||T_e - Tm||_F / ||Tm||_F.
-__global__ void k_ensemble(int n, int members, const float* __restrict__ T, double* __restrict__ Tm,
-                           double* __restrict__ spread) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const float a = ensemble_block<0, 36>(n, r, members, T, Tm);
-    const float b = ensemble_block<36, 45>(n, r, members, T, Tm);
-    const float c = ensemble_block<45, 54>(n, r, members, T, Tm);
-    spread[r] = (double)fmaxf(a, fmaxf(b, c));
+// spread[n] = max over the three tensors of max_e ||T_e - Tm||_F / ||Tm||_F.  The
+// means of a block's points are staged in shared memory and stored as one
+// contiguous run of rows.
+__global__ void __launch_bounds__(ENS_BLOCK) k_ensemble(int n, int members, const float* __restrict__ T,
+                                                        double* __restrict__ Tm, double* __restrict__ spread) {
+    __shared__ double stage[ENS_BLOCK * ENS_LD];
+    const int r0 = blockIdx.x * ENS_BLOCK, r = r0 + threadIdx.x;
+    if (r < n) {
+        double* st = stage + threadIdx.x * ENS_LD;
+        const float a = ensemble_block<0, 36>(n, r, members, T, st);
+        const float b = ensemble_block<36, 45>(n, r, members, T, st);
+        const float c = ensemble_block<45, 54>(n, r, members, T, st);
+        spread[r] = (double)fmaxf(a, fmaxf(b, c));
+    }
+    __syncthreads();
+    const int rows = min(ENS_BLOCK, n - r0);
+    for (int i = threadIdx.x; i < rows * 54; i += ENS_BLOCK)
+        Tm[(int64_t)r0 * 54 + i] = stage[(i / 54) * ENS_LD + i % 54];
 }
 
 void launch_ensemble(int n, int members, const float* T, double* Tm, double* spread, cudaStream_t s) {
-    k_ensemble<<<(n + 127) / 128, 128, 0, s>>>(n, members, T, Tm, spread);
+    k_ensemble<<<(n + ENS_BLOCK - 1) / ENS_BLOCK, ENS_BLOCK, 0, s>>>(n, members, T, Tm, spread);
 }
 
 // Tm [n][54] (C 36, K 9, D 9 in the network's units) -> C [n][36], K [n][9], D [n][9] in SI units

@@ -103,8 +103,9 @@ int alloc_work(rve_surrogate s, int M) {
     return RVE_OK;
 }
 
-// forward pass of member e on M rows already in s->H[0] (BF16 [M][KIN]); z -> s->zout
-int forward(rve_surrogate s, int e, int M, bool keep_pre) {
+// forward pass of member e on M rows already in s->H[0] (BF16 [M][KIN]); z -> s->zout,
+// [M][NOUTP] (training) or transposed [NOUTP][M] (inference, transposed_out)
+int forward(rve_surrogate s, int e, int M, bool keep_pre, bool transposed_out = false) {
     cudaStream_t st = s->ctx->stream;
     for (int l = 0; l < NLAYER; ++l) {
         const int64_t o = layer_w_off(l);
@@ -115,8 +116,8 @@ int forward(rve_surrogate s, int e, int M, bool keep_pre) {
                                       s->H[l + 1].as<__nv_bfloat16>(), keep_pre ? s->Z[l].as<float>() : nullptr,
                                       st));
         else
-            RVE_CUDA(launch_gemm_bf16(M, LN[l], LK[l], s->H[l].as<__nv_bfloat16>(), wt, b, 2, nullptr,
-                                      s->zout.as<float>(), st));
+            RVE_CUDA(launch_gemm_bf16(M, LN[l], LK[l], s->H[l].as<__nv_bfloat16>(), wt, b, transposed_out ? 4 : 2,
+                                      nullptr, s->zout.as<float>(), st));
     }
     s->ctx->launches += NLAYER;
     return RVE_OK;
@@ -433,8 +434,8 @@ static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, doubl
         launch_features(nn, M, KIN, feat_dev + off * 8, dmean.as<float>(), dstd.as<float>(),
                         s->H[0].as<__nv_bfloat16>(), st);
         for (int e = 0; e < s->members; ++e) {
-            RVE_TRY(forward(s, e, M, false));
-            launch_head_tensors(nn, NOUTP, s->zout.as<float>(), s->d_diag.as<uint8_t>(),
+            RVE_TRY(forward(s, e, M, false, true));
+            launch_head_tensors(nn, M, s->zout.as<float>(), s->d_diag.as<uint8_t>(),
                                 s->Tmem.as<float>() + (size_t)e * nn * 54, st);
         }
         launch_ensemble(nn, s->members, s->Tmem.as<float>(), Tm_dev + off * 54, spread_dev + off, st);
