@@ -354,6 +354,13 @@ int rve_surrogate_gradients(rve_ctx ctx, rve_surrogate s, int member, int n, con
 int rve_surrogate_predict(rve_ctx ctx, rve_surrogate s, int64_t n, const double* feat, double* C,
                           double* K, double* D, double* spread);
 
+/* Inference path of rve_surrogate_predict[_dev] and the surrogate route: fused = 1
+ * (default) evaluates every member's five layers for 128-row tiles in one kernel
+ * with the activations kept in shared memory (ensembles of up to 4 members; larger
+ * ones use the other path); fused = 0 launches one tensor-core GEMM per member and
+ * layer.  Both compute the same products in the same order. */
+int rve_surrogate_set_fused(rve_ctx ctx, rve_surrogate s, int fused);
+
 /* The same on the device: feat_dev [n][8], outputs C_dev [n][36], K_dev [n][9],
  * D_dev [n][9] (SI units) and spread_dev [n], all on the context's device;
  * enqueued on the context's stream (the caller synchronises).  Uses a

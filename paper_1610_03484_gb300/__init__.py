@@ -157,6 +157,7 @@ _SIGS = {
     "rve_autotune_schedule": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int32),
                                         C.POINTER(C.c_int32), C.c_void_p]),
+    "rve_surrogate_set_fused": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "rve_surrogate_predict_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p]),
     "rve_autotune_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -492,6 +493,10 @@ class Surrogate:
         _check(self.ctx.lib.rve_surrogate_predict(self.ctx.h, self.h, n, _ptr(feat), _ptr(Cc), _ptr(Kk), _ptr(Dd),
                                                   _ptr(sp)), "rve_surrogate_predict")
         return Cc, Kk, Dd, sp
+
+    def set_fused(self, fused: bool):
+        """Inference path: the fused whole-network kernel (default) or one GEMM per layer."""
+        _check(self.ctx.lib.rve_surrogate_set_fused(self.ctx.h, self.h, int(bool(fused))), "rve_surrogate_set_fused")
 
     def predict_dev(self, n: int, feat_dev: int, C_dev: int, K_dev: int, D_dev: int, spread_dev: int):
         """Device-pointer inference (integer device addresses), on the context's stream."""

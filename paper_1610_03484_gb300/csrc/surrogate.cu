@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "kernels.h"
@@ -346,6 +347,231 @@ __global__ void __launch_bounds__(GemmShape<NT>::THREADS, 1)
     }
 }
 
+// ------------------------------------------- fused ensemble inference (sm_103a)
+// The whole network of up to MLP_MAXM members for 128-row tiles of features, with
+// the activations kept in shared memory between the layers (only the features come
+// in and the last layer's z goes out): per layer, kind::f16 MMAs (M = 128, N = 256
+// or 64, K = 16) from the activation tile (A, 128-byte-swizzled K-major chunks of
+// 64 values, written by the epilogue in that layout) and a weight chunk W^T
+// [N][64] (B, streamed by TMA through a two-stage ring from L2) into one FP32
+// accumulator of 256 tensor-memory columns; the epilogue adds the bias, applies
+// SiLU and writes BF16 activations into the other buffer, or, after the last
+// layer, stores z transposed (zT[member][col][row]) for the head.  Work items are
+// (tile, member) pairs, walked persistently; the roles are those of k_gemm_tc:
+// warp 0 TMA, warp 1 MMA, 16 epilogue warps (lane quarter w % 4, 64-column group
+// (w - 2) / 4).  Every wait is bounded.
+constexpr int MLP_MAXM = 4, MLP_EPI = 16, MLP_THREADS = 64 + 32 * MLP_EPI;
+constexpr int MLP_NL = 5;
+constexpr int MLP_OFF_ACT0 = 0, MLP_OFF_ACT1 = 65536, MLP_OFF_X = 131072, MLP_OFF_W = 147456,
+              MLP_OFF_BAR = 147456 + 2 * 32768, MLP_SMEM = 1024 + MLP_OFF_BAR + 128;
+
+struct MlpParams {
+    CUtensorMap x;                       // features [M][64] BF16, box {64, x_rows}
+    CUtensorMap w[MLP_MAXM][MLP_NL];     // member e, layer l: W^T [N_l][K_l] BF16, box {64, N_l}
+    const float* bias[MLP_MAXM][MLP_NL];
+    float* zT;                           // [members][64][ldz]
+    int M, ldz, members;
+    uint32_t x_tx;                       // bytes of one feature tile (x_rows x 128)
+};
+
+__device__ __forceinline__ int mlp_k(int l) { return l == 0 ? 64 : 256; }
+__device__ __forceinline__ int mlp_n(int l) { return l == 4 ? 64 : 256; }
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_fused(const __grid_constant__ MlpParams P) {
+    extern __shared__ uint8_t msm_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(msm_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + MLP_OFF_BAR);
+    // xfull, xempty, wfull[2], wempty[2], accfull, epidone, done
+    const uint32_t b_xfull = smem_addr(bars), b_xempty = smem_addr(bars + 1), b_wfull = smem_addr(bars + 2),
+                   b_wempty = smem_addr(bars + 4), b_acc = smem_addr(bars + 6), b_epi = smem_addr(bars + 7),
+                   b_done = smem_addr(bars + 8);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 9);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int n_tiles = (P.M + 127) / 128, n_items = n_tiles * P.members;
+    if (t == 0) {
+        for (int k = 0; k < 9; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + k)),
+                         "r"(k == 7 ? (uint32_t)MLP_EPI : 1u)
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t s_act0 = smem_addr(base + MLP_OFF_ACT0), s_act1 = smem_addr(base + MLP_OFF_ACT1),
+                   s_x = smem_addr(base + MLP_OFF_X), s_w = smem_addr(base + MLP_OFF_W);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer: the feature tile, then the 17 weight chunks of the item
+            int wit = 0, i = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++i) {
+                const int tile = item / P.members, e = item % P.members;
+                if (i >= 1 && !bar_wait(b_xempty, (i - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                bar_expect(b_xfull, P.x_tx);
+                tma_2d(s_x, &P.x, 0, tile * 128, b_xfull);
+                for (int l = 0; l < MLP_NL && ok; ++l)
+                    for (int kc = 0; kc < mlp_k(l) / 64; ++kc, ++wit) {
+                        const int st = wit & 1;
+                        if (wit >= 2 && !bar_wait(b_wempty + 8 * st, ((wit >> 1) & 1) ^ 1)) {
+                            ok = false;
+                            break;
+                        }
+                        bar_expect(b_wfull + 8 * st, (uint32_t)mlp_n(l) * 128u);
+                        tma_2d(s_w + st * 32768, &P.w[e][l], kc * 64, 0, b_wfull + 8 * st);
+                    }
+            }
+            if (!ok) atomicOr(&g_gemm_timeout, 1);
+            // copies that may still be in flight: the last feature tile and weight chunks
+            if (i >= 1 && !bar_wait(b_xfull, (i - 1) & 1)) atomicOr(&g_gemm_timeout, 1);
+            for (int k = wit - 1; k >= 0 && k >= wit - 2; --k)
+                if (!bar_wait(b_wfull + 8 * (k & 1), (k >> 1) & 1)) atomicOr(&g_gemm_timeout, 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: per item, the five layers in order; layer g (counted over
+            // the CTA's items) waits for the epilogue of layer g - 1, which both frees
+            // the accumulator and wrote this layer's input activations
+            int wit = 0, g = 0, i = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++i) {
+                if (!bar_wait(b_xfull, i & 1)) {
+                    ok = false;
+                    break;
+                }
+                for (int l = 0; l < MLP_NL; ++l, ++g) {
+                    if (g >= 1 && !bar_wait(b_epi, (g - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    // inputs: layer 0 the features, then act0, act1, act0, act1
+                    const uint32_t a_base = l == 0 ? s_x : ((l & 1) ? s_act0 : s_act1);
+                    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                           ((uint32_t)(mlp_n(l) >> 3) << 17) | ((128u >> 4) << 24);
+                    for (int kc = 0; kc < mlp_k(l) / 64; ++kc, ++wit) {
+                        const int st = wit & 1;
+                        if (!bar_wait(b_wfull + 8 * st, (wit >> 1) & 1)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a = a_base + kc * 16384, b = s_w + st * 32768;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_f16_tmem(tmem, desc_sw128(a + kk * 32), desc_sw128(b + kk * 32), idesc,
+                                         (kc > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(b_wempty + 8 * st);
+                    }
+                    if (!ok) break;
+                    if (l == 0) mma_commit(b_xempty);
+                    mma_commit(b_acc);
+                }
+            }
+            if (!ok) atomicOr(&g_gemm_timeout, 1);
+            // every MMA issued has completed once this commit arrives
+            mma_commit(b_done);
+            if (!bar_wait(b_done, 0)) atomicOr(&g_gemm_timeout, 1);
+        }
+    } else {
+        // ---- epilogue: lane quarter q of the accumulator, 64-column group grp (16 at N = 64)
+        const int q = warp & 3, grp = (warp - 2) >> 2;
+        const int r = 32 * q + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+        int g = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+            const int tile = item / P.members, e = item % P.members;
+            const int grow = tile * 128 + r;
+            for (int l = 0; l < MLP_NL; ++l, ++g) {
+                __syncwarp();
+                bool w = true;
+                if (lane == 0) w = bar_wait(b_acc, g & 1);
+                w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+                if (!w) {
+                    if (lane == 0) atomicOr(&g_gemm_timeout, 1);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const float* bias = P.bias[e][l];
+                if (l < MLP_NL - 1) {
+                    uint32_t v[64];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        tmem_ld16x(lane_base + (uint32_t)(grp * 64 + 16 * j),
+                                   *reinterpret_cast<uint32_t(*)[16]>(v + 16 * j));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    uint8_t* out = base + ((l & 1) ? MLP_OFF_ACT1 : MLP_OFF_ACT0) + grp * 16384 + r * 128;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float4 b0 = __ldg(reinterpret_cast<const float4*>(bias + grp * 64 + 8 * u));
+                        const float4 b1 = __ldg(reinterpret_cast<const float4*>(bias + grp * 64 + 8 * u + 4));
+                        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h)
+                            pk[h] = pack_bf16(
+                                __float2bfloat16(silu_f(__uint_as_float(v[8 * u + 2 * h]) + bb[2 * h])),
+                                __float2bfloat16(silu_f(__uint_as_float(v[8 * u + 2 * h + 1]) + bb[2 * h + 1])));
+                        // 128-byte swizzle of the K-major operand layout: 16-byte unit u of row r
+                        *reinterpret_cast<uint4*>(out + ((u ^ (r & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                    // the next layer's MMAs read these writes through the async proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                } else {
+                    uint32_t v[16];
+                    tmem_ld16x(lane_base + (uint32_t)(grp * 16), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (grow < P.M) {
+                        float* zt = P.zT + ((int64_t)e * 64 + grp * 16) * P.ldz + grow;
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            zt[(int64_t)u * P.ldz] = __uint_as_float(v[u]) + __ldg(bias + grp * 16 + u);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_epi) : "memory");
+            }
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+    }
+}
+
 template <int NT>
 static size_t gemm_smem() {
     return 1024 + (size_t)GemmShape<NT>::S * GemmShape<NT>::STAGE + GemmShape<NT>::BIAS_OFF +
@@ -387,6 +613,35 @@ static bool make_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, int co
 void gemm_tc_prepare() {
     cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
     cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<64>());
+    cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM);
+}
+
+int mlp_fused_max_members() { return MLP_MAXM; }
+
+// The fused inference of `members` networks on M feature rows (M a multiple of 64):
+// weights of member e at wt[e] + w_off[l] (W^T [N_l][K_l] BF16), biases bias[e * 5 + l].
+cudaError_t launch_mlp_fused(int M, int members, const __nv_bfloat16* X, const __nv_bfloat16* const* wt,
+                             const int64_t* w_off, const float* const* bias, float* zT, int ldz, cudaStream_t s) {
+    if (M <= 0 || M % 64 || members < 1 || members > MLP_MAXM || ldz < M) return cudaErrorInvalidValue;
+    static const int KL[MLP_NL] = {64, 256, 256, 256, 256}, NL[MLP_NL] = {256, 256, 256, 256, 64};
+    MlpParams P;
+    std::memset(&P, 0, sizeof(P));
+    const int x_rows = M < 128 ? M : 128;
+    if (!make_map(&P.x, X, M, 64, x_rows)) return cudaErrorInvalidValue;
+    for (int e = 0; e < members; ++e)
+        for (int l = 0; l < MLP_NL; ++l) {
+            if (!make_map(&P.w[e][l], wt[e] + w_off[l], NL[l], KL[l], NL[l])) return cudaErrorInvalidValue;
+            P.bias[e][l] = bias[e * MLP_NL + l];
+        }
+    P.zT = zT;
+    P.M = M;
+    P.ldz = ldz;
+    P.members = members;
+    P.x_tx = (uint32_t)x_rows * 128u;
+    const int items = ((M + 127) / 128) * members;
+    const int grid = std::min(items, sm_count());
+    k_mlp_fused<<<grid, MLP_THREADS, MLP_SMEM, s>>>(P);
+    return cudaGetLastError();
 }
 
 int gemm_tc_timed_out() {

@@ -15,6 +15,13 @@ int gemm_tc_timed_out();
 // C = A Bt^T on the tensor cores (TMA-fed); an error if a tensor map cannot be encoded
 cudaError_t launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt,
                              const float* bias, int epilogue, __nv_bfloat16* Cb, float* Cf, cudaStream_t s);
+// Fused ensemble inference: all layers of up to mlp_fused_max_members() members per
+// 128-row tile with the activations kept on chip; X [M][64] BF16 features, member e's
+// W^T of layer l at wt[e] + w_off[l], biases bias[e * 5 + l]; z of member e written
+// transposed to zT + e * 64 * ldz ([64][ldz]).  An error if a tensor map cannot be encoded.
+int mlp_fused_max_members();
+cudaError_t launch_mlp_fused(int M, int members, const __nv_bfloat16* X, const __nv_bfloat16* const* wt,
+                             const int64_t* w_off, const float* const* bias, float* zT, int ldz, cudaStream_t s);
 void launch_transpose_bf16(int rows, int cols, const __nv_bfloat16* in, __nv_bfloat16* out, cudaStream_t s);
 void launch_silu_backward(int64_t n, const float* dY, const float* Z, __nv_bfloat16* g, cudaStream_t s);
 void launch_head_loss(int M, int m_valid, int noutp, const float* z, const float* target, const float* sigma,

@@ -63,6 +63,10 @@ struct rve_surrogate_s {
     DevBuf d_norm, d_diag;
     // workspace
     DevBuf X, H[NLAYER], Z[NLAYER], zout, dz, G, Gt, Ht, dH, gradT, gradb, loss, feat_dev, Tmem, Tm, spr;
+    // inference: the fused kernel (all members' layers per tile, activations on chip)
+    // or one GEMM launch per member and layer
+    bool fused = true;
+    DevBuf zall;
 };
 
 namespace {
@@ -423,6 +427,19 @@ static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, doubl
     const int64_t chunk = 65536;
     RVE_TRY(alloc_work(s, (int)chunk));
     RVE_TRY(s->Tmem.ensure((size_t)s->members * chunk * 54 * 4));
+    const bool use_fused = s->fused && s->members <= mlp_fused_max_members();
+    std::vector<const __nv_bfloat16*> wt;
+    std::vector<const float*> bias;
+    int64_t w_off[NLAYER];
+    if (use_fused) {
+        RVE_TRY(s->zall.ensure((size_t)s->members * 64 * chunk * 4));
+        for (int l = 0; l < NLAYER; ++l) w_off[l] = layer_w_off(l);
+        for (int e = 0; e < s->members; ++e) {
+            wt.push_back(s->Wt[e].as<__nv_bfloat16>());
+            for (int l = 0; l < NLAYER; ++l)
+                bias.push_back(s->P[e].as<float>() + layer_w_off(l) + (int64_t)LK[l] * LN[l]);
+        }
+    }
     DevBuf dmean, dstd;
     std::vector<float> fis(8);
     for (int k = 0; k < 8; ++k) fis[k] = 1.f / s->feat_std[k];
@@ -433,10 +450,18 @@ static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, doubl
         const int M = ((nn + 63) / 64) * 64;
         launch_features(nn, M, KIN, feat_dev + off * 8, dmean.as<float>(), dstd.as<float>(),
                         s->H[0].as<__nv_bfloat16>(), st);
+        if (use_fused) {
+            RVE_CUDA(launch_mlp_fused(M, s->members, s->H[0].as<__nv_bfloat16>(), wt.data(), w_off,
+                                      bias.data(), s->zall.as<float>(), M, st));
+            s->ctx->launches += 1;
+        }
         for (int e = 0; e < s->members; ++e) {
-            RVE_TRY(forward(s, e, M, false, true));
-            launch_head_tensors(nn, M, s->zout.as<float>(), s->d_diag.as<uint8_t>(),
-                                s->Tmem.as<float>() + (size_t)e * nn * 54, st);
+            const float* zT = s->zout.as<float>();
+            if (use_fused)
+                zT = s->zall.as<float>() + (size_t)e * 64 * M;
+            else
+                RVE_TRY(forward(s, e, M, false, true));
+            launch_head_tensors(nn, M, zT, s->d_diag.as<uint8_t>(), s->Tmem.as<float>() + (size_t)e * nn * 54, st);
         }
         launch_ensemble(nn, s->members, s->Tmem.as<float>(), Tm_dev + off * 54, spread_dev + off, st);
         s->ctx->launches += 2 + s->members;
@@ -473,6 +498,13 @@ int rve_surrogate_predict(rve_ctx c, rve_surrogate s, int64_t n, const double* f
         set_error("a bounded wait inside the surrogate GEMM gave up");
         return RVE_ERR_TIMEOUT;
     }
+    return RVE_OK;
+}
+
+int rve_surrogate_set_fused(rve_ctx c, rve_surrogate s, int fused) {
+    RVE_TRY(check_ctx(c));
+    if (!s) return RVE_ERR_INVALID_ARGUMENT;
+    s->fused = fused != 0;
     return RVE_OK;
 }
 

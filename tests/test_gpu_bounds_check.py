@@ -34,7 +34,7 @@ import paper_1610_03484_gb300 as rve
 out = {}
 xyz, tets, phase, tangent = ri.weave_rve(6, 6, 4)
 for prec in (0, 1):
-    with rve.Context(precision=prec, rtol=1e-10 if prec == 0 else 1e-7, inner_rtol=5e-8) as ctx:
+    with rve.Context(precision=prec, rtol=1e-10 if prec == 0 else 1e-7) as ctx:
         m = ctx.mesh_load(xyz, tets, 2, phase, tangent)
         m.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN, T_C=70.0, c_wt=0.8, t_h=400.0)
         m.set_bc(1)
@@ -98,7 +98,7 @@ def test_checking_build_clean_and_planted(libs):
     rve.load_library()
     xyz, tets, phase, tangent = ri.weave_rve(6, 6, 4)
     for prec in (0, 1):
-        with rve.Context(precision=prec, rtol=1e-10 if prec == 0 else 1e-7, inner_rtol=5e-8) as ctx:
+        with rve.Context(precision=prec, rtol=1e-10 if prec == 0 else 1e-7) as ctx:
             m = ctx.mesh_load(xyz, tets, 2, phase, tangent)
             m.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN, T_C=70.0, c_wt=0.8, t_h=400.0)
             m.set_bc(1)

@@ -58,7 +58,7 @@ def test_colouring_is_proper(rve, p, bc):
 
 def _solve(rve, det, prec, grid, p, bc, states, rtol):
     xyz, tets, phase, tangent = ri.weave_rve(*grid)
-    with rve.Context(precision=prec, rtol=rtol, inner_rtol=min(1e-6, rtol * 0.5),
+    with rve.Context(precision=prec, rtol=rtol, inner_rtol=1e-6,
                      deterministic=det) as ctx:
         m = ctx.mesh_load(xyz, tets, p, phase, tangent)
         m.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)

@@ -335,3 +335,20 @@ def test_surrogate_gain_on_bench_class(rve):
     for P, R in ((Cs, Cp), (Ks, Kp), (Ds, Dp)):
         assert rel(P, R).max() < 1e-2
     assert sur_s < 0.5 * pcg_s, (sur_s, pcg_s, fb.mean())
+
+
+def test_fused_inference_matches_layer_by_layer(rve, trained):
+    """The fused whole-network kernel against one tensor-core GEMM per member and
+    layer: the same BF16 products in the same order, so the same tensors up to the
+    last bits of the FP32 head.  Sizes: a ragged 1 000-point set (a partial 128-row
+    tile, M = 1024 padded) and 64 points (a single 64-row tile)."""
+    s = trained["s"]
+    for n in (1000, 64):
+        f = trained["feat"][:n]
+        s.set_fused(True)
+        a = s.predict(f)
+        s.set_fused(False)
+        b = s.predict(f)
+        s.set_fused(True)
+        for x, y in zip(a, b):
+            np.testing.assert_allclose(x, y, rtol=1e-6, atol=1e-12 * np.abs(y).max())
