@@ -363,8 +363,8 @@ int rve_surrogate_set_fused(rve_ctx ctx, rve_surrogate s, int fused);
 
 /* The same on the device: feat_dev [n][8], outputs C_dev [n][36], K_dev [n][9],
  * D_dev [n][9] (SI units) and spread_dev [n], all on the context's device;
- * enqueued on the context's stream (the caller synchronises).  Uses a
- * library-owned work buffer of n x 54 doubles. */
+ * enqueued on the context's stream (the caller synchronises).  Uses library-owned
+ * work buffers sized for chunks of 65,536 points (allocated on first use). */
 int rve_surrogate_predict_dev(rve_ctx ctx, rve_surrogate s, int64_t n, const double* feat_dev, double* C_dev,
                               double* K_dev, double* D_dev, double* spread_dev);
 

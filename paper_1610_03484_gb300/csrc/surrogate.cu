@@ -350,20 +350,26 @@ __global__ void __launch_bounds__(GemmShape<NT>::THREADS, 1)
 // ------------------------------------------- fused ensemble inference (sm_103a)
 // The whole network of up to MLP_MAXM members for 128-row tiles of features, with
 // the activations kept in shared memory between the layers (only the features come
-// in and the last layer's z goes out): per layer, kind::f16 MMAs (M = 128, N = 256
-// or 64, K = 16) from the activation tile (A, 128-byte-swizzled K-major chunks of
-// 64 values, written by the epilogue in that layout) and a weight chunk W^T
-// [N][64] (B, streamed by TMA through a two-stage ring from L2) into one FP32
-// accumulator of 256 tensor-memory columns; the epilogue adds the bias, applies
-// SiLU and writes BF16 activations into the other buffer, or, after the last
-// layer, stores z transposed (zT[member][col][row]) for the head.  Work items are
-// (tile, member) pairs, walked persistently; the roles are those of k_gemm_tc:
-// warp 0 TMA, warp 1 MMA, 16 epilogue warps (lane quarter w % 4, 64-column group
-// (w - 2) / 4).  Every wait is bounded.
+// in and the last layer's z goes out).  Per layer: kind::f16 MMAs (M = 128, N = 256
+// or 64, K = 16) from the activation tile (A: 128-byte-swizzled K-major chunks of 64
+// values, written by the epilogue in that layout) and a weight chunk W^T [N][64] (B,
+// streamed by TMA through a two-stage ring from L2) into an FP32 accumulator of 256
+// tensor-memory columns; the epilogue adds the bias, applies SiLU and writes the BF16
+// activations back over the tile it came from (its layer's MMAs have completed), or,
+// after the last layer, stores z transposed (zT[member][col][row]) for the head.
+//
+// Work items are (tile, member) pairs, walked persistently.  Two items are in flight
+// per CTA, one per slot (own feature tile, activation tile and accumulator): the MMA
+// warp alternates between the slots layer by layer, so that one slot's MMAs run while
+// the other slot's epilogue works.  Warp 0 issues the TMA copies in the MMA's order,
+// warp 1 the MMAs, and epilogue warps 2-9 serve slot 0 and 10-17 slot 1 (lane quarter
+// w % 4, 128-column half).  Every wait is bounded.
 constexpr int MLP_MAXM = 4, MLP_EPI = 16, MLP_THREADS = 64 + 32 * MLP_EPI;
 constexpr int MLP_NL = 5;
-constexpr int MLP_OFF_ACT0 = 0, MLP_OFF_ACT1 = 65536, MLP_OFF_X = 131072, MLP_OFF_W = 147456,
-              MLP_OFF_BAR = 147456 + 2 * 32768, MLP_SMEM = 1024 + MLP_OFF_BAR + 128;
+constexpr int MLP_OFF_ACT = 0,        // [2][64 KB]
+    MLP_OFF_X = 131072,               // [2][16 KB]
+    MLP_OFF_W = 163840,               // [2][32 KB]
+    MLP_OFF_BAR = 229376, MLP_SMEM = 1024 + MLP_OFF_BAR + 128;
 
 struct MlpParams {
     CUtensorMap x;                       // features [M][64] BF16, box {64, x_rows}
@@ -395,24 +401,27 @@ __global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_fused(const __grid_const
     extern __shared__ uint8_t msm_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(msm_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + MLP_OFF_BAR);
-    // xfull, xempty, wfull[2], wempty[2], accfull, epidone, done
-    const uint32_t b_xfull = smem_addr(bars), b_xempty = smem_addr(bars + 1), b_wfull = smem_addr(bars + 2),
-                   b_wempty = smem_addr(bars + 4), b_acc = smem_addr(bars + 6), b_epi = smem_addr(bars + 7),
-                   b_done = smem_addr(bars + 8);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 9);
+    // per slot s: xfull[s], xempty[s], accfull[s], epidone[s]; the ring's wfull[2], wempty[2]; done
+    auto B = [&](int k) { return smem_addr(bars + k); };
+    const uint32_t b_xfull = B(0), b_xempty = B(2), b_acc = B(4), b_epi = B(6), b_wfull = B(8), b_wempty = B(10),
+                   b_done = B(12);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 13);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int n_tiles = (P.M + 127) / 128, n_items = n_tiles * P.members;
+    const int n_items = ((P.M + 127) / 128) * P.members;
+    // this CTA's items k = 0 .. n_cta - 1 are blockIdx.x + k gridDim.x; slot s takes k = s (mod 2)
+    const int n_cta = blockIdx.x < n_items ? (n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int ns0 = (n_cta + 1) / 2, ns1 = n_cta / 2;
     if (t == 0) {
-        for (int k = 0; k < 9; ++k)
+        for (int k = 0; k < 13; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + k)),
-                         "r"(k == 7 ? (uint32_t)MLP_EPI : 1u)
+                         "r"((k == 6 || k == 7) ? (uint32_t)(MLP_EPI / 2) : 1u)
                          : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
-                     "r"(256u)
+                     "r"(512u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -420,23 +429,29 @@ __global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_fused(const __grid_const
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const uint32_t s_act0 = smem_addr(base + MLP_OFF_ACT0), s_act1 = smem_addr(base + MLP_OFF_ACT1),
-                   s_x = smem_addr(base + MLP_OFF_X), s_w = smem_addr(base + MLP_OFF_W);
+    const uint32_t s_act = smem_addr(base + MLP_OFF_ACT), s_x = smem_addr(base + MLP_OFF_X),
+                   s_w = smem_addr(base + MLP_OFF_W);
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---- TMA producer: the feature tile, then the 17 weight chunks of the item
-            int wit = 0, i = 0;
+            // ---- TMA producer, in the MMA's order: round r gives slot 0, then slot 1,
+            // layer r % 5 of its item r / 5; a layer-0 step also loads the item's features
+            int wit = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++i) {
-                const int tile = item / P.members, e = item % P.members;
-                if (i >= 1 && !bar_wait(b_xempty, (i - 1) & 1)) {
-                    ok = false;
-                    break;
-                }
-                bar_expect(b_xfull, P.x_tx);
-                tma_2d(s_x, &P.x, 0, tile * 128, b_xfull);
-                for (int l = 0; l < MLP_NL && ok; ++l)
+            for (int r = 0; ok && r / 5 < ns0; ++r)
+                for (int sl = 0; sl < 2 && ok; ++sl) {
+                    const int idx = r / 5, l = r % 5;
+                    if (idx >= (sl ? ns1 : ns0)) continue;
+                    const int item = blockIdx.x + (2 * idx + sl) * gridDim.x;
+                    const int tile = item / P.members, e = item % P.members;
+                    if (l == 0) {
+                        if (idx >= 1 && !bar_wait(b_xempty + 8 * sl, (idx - 1) & 1)) {
+                            ok = false;
+                            break;
+                        }
+                        bar_expect(b_xfull + 8 * sl, P.x_tx);
+                        tma_2d(s_x + sl * 16384, &P.x, 0, tile * 128, b_xfull + 8 * sl);
+                    }
                     for (int kc = 0; kc < mlp_k(l) / 64; ++kc, ++wit) {
                         const int st = wit & 1;
                         if (wit >= 2 && !bar_wait(b_wempty + 8 * st, ((wit >> 1) & 1) ^ 1)) {
@@ -446,33 +461,39 @@ __global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_fused(const __grid_const
                         bar_expect(b_wfull + 8 * st, (uint32_t)mlp_n(l) * 128u);
                         tma_2d(s_w + st * 32768, &P.w[e][l], kc * 64, 0, b_wfull + 8 * st);
                     }
-            }
+                }
             if (!ok) atomicOr(&g_gemm_timeout, 1);
-            // copies that may still be in flight: the last feature tile and weight chunks
-            if (i >= 1 && !bar_wait(b_xfull, (i - 1) & 1)) atomicOr(&g_gemm_timeout, 1);
+            // copies that may still be in flight: each slot's last feature tile and the
+            // last weight chunks
+            for (int sl = 0; sl < 2; ++sl) {
+                const int n = sl ? ns1 : ns0;
+                if (n >= 1 && !bar_wait(b_xfull + 8 * sl, (n - 1) & 1)) atomicOr(&g_gemm_timeout, 1);
+            }
             for (int k = wit - 1; k >= 0 && k >= wit - 2; --k)
                 if (!bar_wait(b_wfull + 8 * (k & 1), (k >> 1) & 1)) atomicOr(&g_gemm_timeout, 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---- MMA issuer: per item, the five layers in order; layer g (counted over
-            // the CTA's items) waits for the epilogue of layer g - 1, which both frees
-            // the accumulator and wrote this layer's input activations
-            int wit = 0, g = 0, i = 0;
+            // ---- MMA issuer: the same round order as the producer.  A slot's step waits
+            // for the epilogue of the slot's previous step, which both freed the slot's
+            // accumulator and wrote this step's input activations.
+            int wit = 0, ks[2] = {0, 0};
             bool ok = true;
-            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++i) {
-                if (!bar_wait(b_xfull, i & 1)) {
-                    ok = false;
-                    break;
-                }
-                for (int l = 0; l < MLP_NL; ++l, ++g) {
-                    if (g >= 1 && !bar_wait(b_epi, (g - 1) & 1)) {
+            for (int r = 0; ok && r / 5 < ns0; ++r)
+                for (int sl = 0; sl < 2 && ok; ++sl) {
+                    const int idx = r / 5, l = r % 5;
+                    if (idx >= (sl ? ns1 : ns0)) continue;
+                    if (l == 0 && !bar_wait(b_xfull + 8 * sl, idx & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    if (ks[sl] >= 1 && !bar_wait(b_epi + 8 * sl, (ks[sl] - 1) & 1)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    // inputs: layer 0 the features, then act0, act1, act0, act1
-                    const uint32_t a_base = l == 0 ? s_x : ((l & 1) ? s_act0 : s_act1);
+                    const uint32_t a_base = l == 0 ? s_x + sl * 16384 : s_act + sl * 65536;
+                    const uint32_t d = tmem + (uint32_t)(256 * sl);
                     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                            ((uint32_t)(mlp_n(l) >> 3) << 17) | ((128u >> 4) << 24);
                     for (int kc = 0; kc < mlp_k(l) / 64; ++kc, ++wit) {
@@ -485,34 +506,37 @@ __global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_fused(const __grid_const
                         const uint32_t a = a_base + kc * 16384, b = s_w + st * 32768;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            mma_f16_tmem(tmem, desc_sw128(a + kk * 32), desc_sw128(b + kk * 32), idesc,
+                            mma_f16_tmem(d, desc_sw128(a + kk * 32), desc_sw128(b + kk * 32), idesc,
                                          (kc > 0 || kk > 0) ? 1u : 0u);
                         mma_commit(b_wempty + 8 * st);
                     }
                     if (!ok) break;
-                    if (l == 0) mma_commit(b_xempty);
-                    mma_commit(b_acc);
+                    if (l == 0) mma_commit(b_xempty + 8 * sl);
+                    mma_commit(b_acc + 8 * sl);
+                    ++ks[sl];
                 }
-            }
             if (!ok) atomicOr(&g_gemm_timeout, 1);
             // every MMA issued has completed once this commit arrives
             mma_commit(b_done);
             if (!bar_wait(b_done, 0)) atomicOr(&g_gemm_timeout, 1);
         }
     } else {
-        // ---- epilogue: lane quarter q of the accumulator, 64-column group grp (16 at N = 64)
-        const int q = warp & 3, grp = (warp - 2) >> 2;
+        // ---- epilogue: warps 2-9 serve slot 0, 10-17 slot 1; lane quarter q, column half h
+        const int sl = (warp - 2) >> 3, q = warp & 3, h = ((warp - 2) >> 2) & 1;
         const int r = 32 * q + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-        int g = 0;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(256 * sl);
+        uint8_t* act = base + MLP_OFF_ACT + sl * 65536;
+        const int n_slot = sl ? ns1 : ns0;
+        int ks = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+        for (int idx = 0; idx < n_slot && ok; ++idx) {
+            const int item = blockIdx.x + (2 * idx + sl) * gridDim.x;
             const int tile = item / P.members, e = item % P.members;
             const int grow = tile * 128 + r;
-            for (int l = 0; l < MLP_NL; ++l, ++g) {
+            for (int l = 0; l < MLP_NL; ++l, ++ks) {
                 __syncwarp();
                 bool w = true;
-                if (lane == 0) w = bar_wait(b_acc, g & 1);
+                if (lane == 0) w = bar_wait(b_acc + 8 * sl, ks & 1);
                 w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
                 if (!w) {
                     if (lane == 0) atomicOr(&g_gemm_timeout, 1);
@@ -522,43 +546,52 @@ __global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_fused(const __grid_const
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const float* bias = P.bias[e][l];
                 if (l < MLP_NL - 1) {
-                    uint32_t v[64];
+                    // columns 128 h + 64 j .. + 63: activation chunk 2 h + j
+#pragma unroll 1
+                    for (int j = 0; j < 2; ++j) {
+                        const int c0 = 128 * h + 64 * j;
+                        uint32_t v[64];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        tmem_ld16x(lane_base + (uint32_t)(grp * 64 + 16 * j),
-                                   *reinterpret_cast<uint32_t(*)[16]>(v + 16 * j));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    uint8_t* out = base + ((l & 1) ? MLP_OFF_ACT1 : MLP_OFF_ACT0) + grp * 16384 + r * 128;
+                        for (int jj = 0; jj < 4; ++jj)
+                            tmem_ld16x(lane_base + (uint32_t)(c0 + 16 * jj),
+                                       *reinterpret_cast<uint32_t(*)[16]>(v + 16 * jj));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        uint8_t* out = act + (c0 / 64) * 16384 + r * 128;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const float4 b0 = __ldg(reinterpret_cast<const float4*>(bias + grp * 64 + 8 * u));
-                        const float4 b1 = __ldg(reinterpret_cast<const float4*>(bias + grp * 64 + 8 * u + 4));
-                        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-                        uint32_t pk[4];
+                        for (int u = 0; u < 8; ++u) {
+                            const float4 b0 = __ldg(reinterpret_cast<const float4*>(bias + c0 + 8 * u));
+                            const float4 b1 = __ldg(reinterpret_cast<const float4*>(bias + c0 + 8 * u + 4));
+                            const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                            uint32_t pk[4];
 #pragma unroll
-                        for (int h = 0; h < 4; ++h)
-                            pk[h] = pack_bf16(
-                                __float2bfloat16(silu_f(__uint_as_float(v[8 * u + 2 * h]) + bb[2 * h])),
-                                __float2bfloat16(silu_f(__uint_as_float(v[8 * u + 2 * h + 1]) + bb[2 * h + 1])));
-                        // 128-byte swizzle of the K-major operand layout: 16-byte unit u of row r
-                        *reinterpret_cast<uint4*>(out + ((u ^ (r & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            for (int hh = 0; hh < 4; ++hh)
+                                pk[hh] = pack_bf16(
+                                    __float2bfloat16(silu_f(__uint_as_float(v[8 * u + 2 * hh]) + bb[2 * hh])),
+                                    __float2bfloat16(silu_f(__uint_as_float(v[8 * u + 2 * hh + 1]) + bb[2 * hh + 1])));
+                            // 128-byte swizzle of the K-major operand layout: 16-byte unit u of row r
+                            *reinterpret_cast<uint4*>(out + ((u ^ (r & 7)) << 4)) =
+                                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        }
                     }
                     // the next layer's MMAs read these writes through the async proxy
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 } else {
-                    uint32_t v[16];
-                    tmem_ld16x(lane_base + (uint32_t)(grp * 16), v);
+                    // N = 64: columns 32 h .. + 31
+                    uint32_t v[32];
+                    tmem_ld16x(lane_base + (uint32_t)(32 * h), *reinterpret_cast<uint32_t(*)[16]>(v));
+                    tmem_ld16x(lane_base + (uint32_t)(32 * h + 16), *reinterpret_cast<uint32_t(*)[16]>(v + 16));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (grow < P.M) {
-                        float* zt = P.zT + ((int64_t)e * 64 + grp * 16) * P.ldz + grow;
+                        float* zt = P.zT + ((int64_t)e * 64 + 32 * h) * P.ldz + grow;
 #pragma unroll
-                        for (int u = 0; u < 16; ++u)
-                            zt[(int64_t)u * P.ldz] = __uint_as_float(v[u]) + __ldg(bias + grp * 16 + u);
+                        for (int u = 0; u < 32; ++u)
+                            zt[(int64_t)u * P.ldz] = __uint_as_float(v[u]) + __ldg(bias + 32 * h + u);
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_epi) : "memory");
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_epi + 8 * sl) : "memory");
             }
         }
     }
@@ -568,7 +601,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_fused(const __grid_const
     if (warp == 0) {
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
     }
 }
 
@@ -873,8 +906,12 @@ __device__ __forceinline__ float ensemble_block(int n, int r, int members, const
     const float inv = 1.f / (float)members;
 #pragma unroll
     for (int c = 0; c < HI - LO; ++c) {
+        // up to four members in independent loads; more in a second loop
         float sacc = 0.f;
-        for (int e = 0; e < members; ++e) sacc += T[((int64_t)e * 54 + LO + c) * n + r];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (e < members) sacc += __ldg(T + ((int64_t)e * 54 + LO + c) * n + r);
+        for (int e = 4; e < members; ++e) sacc += __ldg(T + ((int64_t)e * 54 + LO + c) * n + r);
         mean[c] = sacc * inv;
         stage[LO + c] = (double)mean[c];
     }
@@ -886,7 +923,7 @@ __device__ __forceinline__ float ensemble_block(int n, int r, int members, const
         float num = 0.f;
 #pragma unroll
         for (int c = 0; c < HI - LO; ++c) {
-            const float d = T[((int64_t)e * 54 + LO + c) * n + r] - mean[c];
+            const float d = __ldg(T + ((int64_t)e * 54 + LO + c) * n + r) - mean[c];
             num = fmaf(d, d, num);
         }
         const float q = den > 0.f ? sqrtf(num / den) : 0.f;
@@ -895,12 +932,14 @@ __device__ __forceinline__ float ensemble_block(int n, int r, int members, const
     return worst;
 }
 
-// Ensemble mean and spread: Tm [n][54] = mean over members (FP64 storage),
-// spread[n] = max over the three tensors of max_e ||T_e - Tm||_F / ||Tm||_F.  The
-// means of a block's points are staged in shared memory and stored as one
-// contiguous run of rows.
-__global__ void __launch_bounds__(ENS_BLOCK) k_ensemble(int n, int members, const float* __restrict__ T,
-                                                        double* __restrict__ Tm, double* __restrict__ spread) {
+// Ensemble mean and spread: C [n][36], K [n][9], D [n][9] = mean over the members
+// times the reference scales (SI units, FP64), spread[n] = max over the three tensors
+// of max_e ||T_e - mean||_F / ||mean||_F.  The means of a block's points are staged
+// in shared memory and each output is stored as one contiguous run of rows.
+__global__ void __launch_bounds__(ENS_BLOCK) k_ensemble(int n, int members, const float* __restrict__ T, double rc,
+                                                        double rk, double rd, double* __restrict__ C,
+                                                        double* __restrict__ K, double* __restrict__ D,
+                                                        double* __restrict__ spread) {
     __shared__ double stage[ENS_BLOCK * ENS_LD];
     const int r0 = blockIdx.x * ENS_BLOCK, r = r0 + threadIdx.x;
     if (r < n) {
@@ -912,33 +951,17 @@ __global__ void __launch_bounds__(ENS_BLOCK) k_ensemble(int n, int members, cons
     }
     __syncthreads();
     const int rows = min(ENS_BLOCK, n - r0);
-    for (int i = threadIdx.x; i < rows * 54; i += ENS_BLOCK)
-        Tm[(int64_t)r0 * 54 + i] = stage[(i / 54) * ENS_LD + i % 54];
-}
-
-void launch_ensemble(int n, int members, const float* T, double* Tm, double* spread, cudaStream_t s) {
-    k_ensemble<<<(n + ENS_BLOCK - 1) / ENS_BLOCK, ENS_BLOCK, 0, s>>>(n, members, T, Tm, spread);
-}
-
-// Tm [n][54] (C 36, K 9, D 9 in the network's units) -> C [n][36], K [n][9], D [n][9] in SI units
-__global__ void k_split_tensors(int64_t n, const double* __restrict__ Tm, double rc, double rk, double rd,
-                                double* __restrict__ C, double* __restrict__ K, double* __restrict__ D) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * 54; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / 54;
-        const int c = (int)(i % 54);
-        const double v = Tm[i];
-        if (c < 36) C[r * 36 + c] = v * rc;
-        else if (c < 45) K[r * 9 + c - 36] = v * rk;
-        else D[r * 9 + c - 45] = v * rd;
+    for (int i = threadIdx.x; i < rows * 36; i += ENS_BLOCK)
+        C[(int64_t)r0 * 36 + i] = stage[(i / 36) * ENS_LD + i % 36] * rc;
+    for (int i = threadIdx.x; i < rows * 9; i += ENS_BLOCK) {
+        K[(int64_t)r0 * 9 + i] = stage[(i / 9) * ENS_LD + 36 + i % 9] * rk;
+        D[(int64_t)r0 * 9 + i] = stage[(i / 9) * ENS_LD + 45 + i % 9] * rd;
     }
 }
 
-void launch_split_tensors(int64_t n, const double* Tm, double rc, double rk, double rd, double* C, double* K,
-                          double* D, cudaStream_t s) {
-    int64_t b = (n * 54 + 255) / 256;
-    if (b > 8192) b = 8192;
-    if (b < 1) b = 1;
-    k_split_tensors<<<(unsigned)b, 256, 0, s>>>(n, Tm, rc, rk, rd, C, K, D);
+void launch_ensemble(int n, int members, const float* T, double rc, double rk, double rd, double* C, double* K,
+                     double* D, double* spread, cudaStream_t s) {
+    k_ensemble<<<(n + ENS_BLOCK - 1) / ENS_BLOCK, ENS_BLOCK, 0, s>>>(n, members, T, rc, rk, rd, C, K, D, spread);
 }
 
 }  // namespace rve

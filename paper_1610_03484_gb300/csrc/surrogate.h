@@ -35,9 +35,9 @@ void launch_features(int n, int M, int kin, const double* feat, const float* mea
                      __nv_bfloat16* X, cudaStream_t s);
 // zT [noutp][ldz] (transposed last-layer output) -> member tensors TeT [54][n]
 void launch_head_tensors(int n, int ldz, const float* zT, const uint8_t* diag, float* TeT, cudaStream_t s);
-void launch_split_tensors(int64_t n, const double* Tm, double rc, double rk, double rd, double* C, double* K,
-                          double* D, cudaStream_t s);
-// T [members][54][n] -> mean Tm [n][54] (FP64) and spread [n]
-void launch_ensemble(int n, int members, const float* T, double* Tm, double* spread, cudaStream_t s);
+// T [members][54][n] -> ensemble means C [n][36], K [n][9], D [n][9] (times the
+// reference scales rc, rk, rd; FP64) and spread [n]
+void launch_ensemble(int n, int members, const float* T, double rc, double rk, double rd, double* C, double* K,
+                     double* D, double* spread, cudaStream_t s);
 
 }  // namespace rve

@@ -62,7 +62,7 @@ struct rve_surrogate_s {
     std::vector<DevBuf> P, M1, M2, Wt, Wn;
     DevBuf d_norm, d_diag;
     // workspace
-    DevBuf X, H[NLAYER], Z[NLAYER], zout, dz, G, Gt, Ht, dH, gradT, gradb, loss, feat_dev, Tmem, Tm, spr;
+    DevBuf X, H[NLAYER], Z[NLAYER], zout, dz, G, Gt, Ht, dH, gradT, gradb, loss, feat_dev, Tmem, spr;
     // inference: the fused kernel (all members' layers per tile, activations on chip)
     // or one GEMM launch per member and layer
     bool fused = true;
@@ -421,7 +421,8 @@ int rve_surrogate_gradients(rve_ctx c, rve_surrogate s, int member, int n, const
 }
 
 // Ensemble prediction on device features: member tensors, mean and spread.
-static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, double* Tm_dev, double* spread_dev) {
+static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, double* C_dev, double* K_dev,
+                       double* D_dev, double* spread_dev) {
     NvtxRange nvtx_("surrogate inference: %lld points, %d members", (long long)n, s->members);
     cudaStream_t st = s->ctx->stream;
     const int64_t chunk = 65536;
@@ -463,7 +464,8 @@ static int predict_dev(rve_surrogate s, int64_t n, const double* feat_dev, doubl
                 RVE_TRY(forward(s, e, M, false, true));
             launch_head_tensors(nn, M, zT, s->d_diag.as<uint8_t>(), s->Tmem.as<float>() + (size_t)e * nn * 54, st);
         }
-        launch_ensemble(nn, s->members, s->Tmem.as<float>(), Tm_dev + off * 54, spread_dev + off, st);
+        launch_ensemble(nn, s->members, s->Tmem.as<float>(), s->ref[0], s->ref[1], s->ref[2], C_dev + off * 36,
+                        K_dev + off * 9, D_dev + off * 9, spread_dev + off, st);
         s->ctx->launches += 2 + s->members;
     }
     RVE_CUDA(cudaGetLastError());
@@ -480,20 +482,19 @@ int rve_surrogate_predict(rve_ctx c, rve_surrogate s, int64_t n, const double* f
     }
     if (n == 0) return RVE_OK;
     cudaStream_t st = c->stream;
-    DevBuf df, dT, dsp;
+    DevBuf df, dC, dK, dD, dsp;
     RVE_TRY(upload(df, feat, (size_t)n * 8, st));
-    RVE_TRY(dT.ensure((size_t)n * 54 * 8));
+    RVE_TRY(dC.ensure((size_t)n * 36 * 8));
+    RVE_TRY(dK.ensure((size_t)n * 9 * 8));
+    RVE_TRY(dD.ensure((size_t)n * 9 * 8));
     RVE_TRY(dsp.ensure((size_t)n * 8));
-    RVE_TRY(predict_dev(s, n, df.as<double>(), dT.as<double>(), dsp.as<double>()));
-    std::vector<double> T((size_t)n * 54);
-    RVE_CUDA(cudaMemcpyAsync(T.data(), dT.p, T.size() * 8, cudaMemcpyDeviceToHost, st));
+    RVE_TRY(predict_dev(s, n, df.as<double>(), dC.as<double>(), dK.as<double>(), dD.as<double>(),
+                        dsp.as<double>()));
+    RVE_CUDA(cudaMemcpyAsync(C, dC.p, (size_t)n * 36 * 8, cudaMemcpyDeviceToHost, st));
+    RVE_CUDA(cudaMemcpyAsync(K, dK.p, (size_t)n * 9 * 8, cudaMemcpyDeviceToHost, st));
+    RVE_CUDA(cudaMemcpyAsync(D, dD.p, (size_t)n * 9 * 8, cudaMemcpyDeviceToHost, st));
     RVE_CUDA(cudaMemcpyAsync(spread, dsp.p, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
     RVE_CUDA(cudaStreamSynchronize(st));
-    for (int64_t i = 0; i < n; ++i) {
-        for (int k = 0; k < 36; ++k) C[36 * i + k] = T[54 * i + k] * s->ref[0];
-        for (int k = 0; k < 9; ++k) K[9 * i + k] = T[54 * i + 36 + k] * s->ref[1];
-        for (int k = 0; k < 9; ++k) D[9 * i + k] = T[54 * i + 45 + k] * s->ref[2];
-    }
     if (gemm_tc_timed_out()) {
         set_error("a bounded wait inside the surrogate GEMM gave up");
         return RVE_ERR_TIMEOUT;
@@ -518,10 +519,7 @@ int rve_surrogate_predict_dev(rve_ctx c, rve_surrogate s, int64_t n, const doubl
         return RVE_ERR_STATE;
     }
     if (n == 0) return RVE_OK;
-    RVE_TRY(s->Tm.ensure((size_t)n * 54 * 8));
-    RVE_TRY(predict_dev(s, n, feat_dev, s->Tm.as<double>(), spread_dev));
-    launch_split_tensors(n, s->Tm.as<double>(), s->ref[0], s->ref[1], s->ref[2], C_dev, K_dev, D_dev, c->stream);
-    c->launches++;
+    RVE_TRY(predict_dev(s, n, feat_dev, C_dev, K_dev, D_dev, spread_dev));
     RVE_CUDA(cudaGetLastError());
     return RVE_OK;
 }
