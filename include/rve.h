@@ -83,8 +83,12 @@ typedef struct rve_options {
     int     profile;         /* 1: time every operator launch with CUDA events (rve_stats.op_*) */
     int     warm_start;      /* macro_update_gauss_points: >0 solves each mesh's points in order of
                                 their degradation factor and starts every batch from the previous
-                                batch of the same call: 1 the nearest solution, 2 (default) the
-                                line and 3 the parabola in the factor through 2 or 3 of them;
+                                batch of the same call: 1 the nearest solution, 2 the line and 3
+                                the parabola in the factor through 2 or 3 of them, 4 (default)
+                                the energy-optimal (Galerkin) combination of up to four of them
+                                for the mechanics without constraint rows (one operator pass over
+                                the sources and a few inner products per batch; otherwise the
+                                parabola, and the transport fields take the nearest);
                                 0 starts every batch from zero */
     int     transport_once;  /* macro_update_gauss_points: 1 solves the thermal and moisture cell
                                 problems once per mesh and call and gives all the mesh's points

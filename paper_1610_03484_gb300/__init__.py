@@ -261,14 +261,14 @@ class Context:
 
     def __init__(self, precision=PREC_FP64, rtol=1e-10, max_iter=20000, inner_rtol=1e-6,
                  max_refine=4, check_every=16, batch=0, stream=None, device=0, profile=False,
-                 warm_start=2, transport_once=False, operator_kernel=KERNEL_AUTO, deterministic=False):
+                 warm_start=4, transport_once=False, operator_kernel=KERNEL_AUTO, deterministic=False):
         lib = load_library()
         o = default_options()
         o.device, o.precision, o.rtol, o.max_iter = device, precision, rtol, max_iter
         o.inner_rtol, o.max_refine, o.check_every, o.batch = inner_rtol, max_refine, check_every, batch
         o.stream = stream
         o.profile = int(profile)
-        o.warm_start = (2 if warm_start else 0) if isinstance(warm_start, bool) else int(warm_start)
+        o.warm_start = (4 if warm_start else 0) if isinstance(warm_start, bool) else int(warm_start)
         o.transport_once = int(transport_once)
         o.operator_kernel = int(operator_kernel)
         o.deterministic = int(deterministic)

@@ -352,6 +352,13 @@ struct WarmStart {
     const double* dcoef = nullptr;  // [ncols][WARM_SOURCES] c_k (w - w_k)
     std::vector<double> alpha;      // [ncols]
     double degrade[2] = {0, 0};     // 1 for a phase whose modulus is proportional to w
+    // energy-optimal combination: minus the degraded and the other phases' operator
+    // applied to the sources (FP64, compact columns), and the column map and coefficients
+    // (in dcoef) that form r0 = b(w) + their combination
+    const double* nkx = nullptr;
+    int kx_cols = 0;
+    const int32_t* kx_map = nullptr;   // [ncols][WARM_SOURCES]
+    const double* ph_coef = nullptr;   // unused by the energy-optimal start
 };
 
 struct Solver {
@@ -837,9 +844,35 @@ struct Solver {
         RVE_CUDA(cudaMemcpyAsync(rz.data(), m->gsum.p, sizeof(double) * ncols, cudaMemcpyDeviceToHost, s));
         RVE_CUDA(cudaStreamSynchronize(s));
         worst = 0;
+        last_rel.assign(ncols, 0.0);
         for (int c = 0; c < ncols; ++c)
-            if (bnorm2[c] > 0) worst = std::max(worst, std::sqrt(std::max(rz[c], 0.0) / bnorm2[c]));
+            if (bnorm2[c] > 0) {
+                last_rel[c] = std::sqrt(std::max(rz[c], 0.0) / bnorm2[c]);
+                worst = std::max(worst, last_rel[c]);
+            }
         if (rz_out) *rz_out = rz;
+        return RVE_OK;
+    }
+
+    // Columns whose relative residual (last rel_residual) is already below half the
+    // tolerance take no part in the next solve: their residual in the solve's input v
+    // is zeroed, so the PCG starts them inactive instead of driving an already
+    // converged residual down into rounding (where p.Kp can lose its sign).
+    std::vector<double> last_rel;
+    template <typename T>
+    int skip_converged(T* v, double rtol) {
+        if ((int)last_rel.size() != ncols) return RVE_OK;
+        std::vector<int32_t> mask(ncols, 0);
+        bool any = false;
+        for (int c = 0; c < ncols; ++c)
+            if (last_rel[c] <= 0.5 * rtol) {
+                mask[c] = 1;
+                any = true;
+            }
+        if (!any) return RVE_OK;
+        RVE_TRY(upload(m->colmask, mask.data(), mask.size(), s));
+        launch_zero_columns<T>(n_rows, ncols, m->colmask.as<int32_t>(), v, s);
+        *launches += 1;
         return RVE_OK;
     }
 
@@ -892,17 +925,24 @@ struct Solver {
         out.converged = false;
         double rel = 1.0;
         if (warm) {
-            launch_combine_columns<double>(n_rows, ncols, warm->cols, warm->map, warm->coef, warm->x, x64, s);
+            launch_combine_columns<double, double>(n_rows, ncols, warm->cols, warm->map, warm->coef, warm->x, x64, s);
             *launches += 1;
-            if (mixed && warm->r) {
+            if (mixed && warm->nkx) {
+                // energy-optimal start: r0 = b(w) - sum_k c_k (K_o + w K_d) x_k from the
+                // sources' operator products (formed with the warm start, double-float)
+                RVE_CUDA(cudaMemcpyAsync(r64, b64, nv * 8, cudaMemcpyDeviceToDevice, s));
+                launch_combine_columns<double, double>(n_rows, ncols, warm->kx_cols, warm->kx_map, warm->dcoef,
+                                                       warm->nkx, r64, s, true);
+                *launches += 1;
+            } else if (mixed && warm->r) {
                 // the residual from the previous residuals (see WarmStart); a plain
                 // FP32 b - K x0 would be too noisy to set the inner tolerance from
-                launch_combine_columns<double>(n_rows, ncols, warm->cols, warm->map, warm->coef, warm->r, r64, s);
+                launch_combine_columns<double, double>(n_rows, ncols, warm->cols, warm->map, warm->coef, warm->r, r64, s);
                 *launches += 1;
                 if (warm->degrade[0] != 0.0 || warm->degrade[1] != 0.0) {
                     float* v32 = m->x32.as<float>();
                     float* y32 = m->r32.as<float>();
-                    launch_combine_columns<float>(n_rows, ncols, warm->cols, warm->map, warm->dcoef, warm->x, v32, s);
+                    launch_combine_columns<double, float>(n_rows, ncols, warm->cols, warm->map, warm->dcoef, warm->x, v32, s);
                     std::vector<float> sc32((size_t)ncols * 2);
                     for (int c = 0; c < ncols; ++c)
                         for (int ph = 0; ph < 2; ++ph) sc32[2 * c + ph] = (float)-warm->degrade[ph];
@@ -945,6 +985,7 @@ struct Solver {
             if (rel > o.rtol) {
                 int its = 0;
                 bool conv = false;
+                RVE_TRY(skip_converged<double>(r64, o.rtol));   // r64 is recomputed after the solve
                 RVE_TRY(pcg<double>(x64, r64, m->p64.as<double>(), m->q64.as<double>(), m->scale64,
                                     o.rtol / rel, o.max_iter, its, conv));
                 out.iterations = its;
@@ -970,6 +1011,7 @@ struct Solver {
                     launch_cast_d2f((int64_t)nv, r64, r32, s);
                     RVE_CUDA(cudaMemsetAsync(x32, 0, nv * 4, s));
                     *launches += 1;
+                    RVE_TRY(skip_converged<float>(r32, o.rtol));
                     int its = 0;
                     bool conv = false;
                     RVE_TRY(pcg<float>(x32, r32, m->p32.as<float>(), m->q32.as<float>(), m->scale32,
@@ -1093,6 +1135,200 @@ static int warm_sources(const std::vector<double>& pw, double w, int order, int*
     return nn;
 }
 
+// c = G^+ g for a small symmetric positive semi-definite G (n <= WARM_SOURCES):
+// cyclic Jacobi rotations, eigenvalues below `rel` of the largest dropped (the
+// sources are nearly parallel, so G is close to singular, and its entries carry the
+// rounding of the FP32 operator products).  False if G has no positive eigenvalue or
+// a value is not finite.
+static bool galerkin_solve(int n, const double* Gin, const double* g, double* c, double rel) {
+    double A[WARM_SOURCES][WARM_SOURCES], V[WARM_SOURCES][WARM_SOURCES];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            A[i][j] = 0.5 * (Gin[i * n + j] + Gin[j * n + i]);
+            V[i][j] = i == j ? 1.0 : 0.0;
+            if (!std::isfinite(A[i][j])) return false;
+        }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < n; ++i) {
+            diag += A[i][i] * A[i][i];
+            for (int j = i + 1; j < n; ++j) off += A[i][j] * A[i][j];
+        }
+        if (off <= 1e-30 * diag) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double th = 0.5 * (A[q][q] - A[p][p]) / A[p][q];
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = cs * akp - sn * akq;
+                    A[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = cs * apk - sn * aqk;
+                    A[q][k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {   // V <- V J
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = cs * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    double lmax = 0.0;
+    for (int i = 0; i < n; ++i) lmax = std::max(lmax, A[i][i]);
+    if (!(lmax > 0.0) || !std::isfinite(lmax)) return false;
+    for (int i = 0; i < n; ++i) c[i] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        if (!(A[k][k] > rel * lmax)) continue;
+        double vg = 0.0;
+        for (int i = 0; i < n; ++i) vg += V[i][k] * g[i];
+        const double a = vg / A[k][k];
+        for (int i = 0; i < n; ++i) c[i] += a * V[i][k];
+    }
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(c[i])) return false;
+    return true;
+}
+
+// Energy-optimal warm start of the mechanics (warm_start >= 4).  With A(w) = K_o + w
+// K_d (K_d: the degraded phases at unit modulus, K_o the others) and b(w) =
+// -A(w) u_macro, the start for a column at w is x0 = sum_k c_k x_k over ns previous
+// solutions of the same load case with G c = g, G_pk = x_p . A(w) x_k, g_p =
+// x_p . b(w): the Galerkin projection onto their span (the energy minimisation of
+// Sec. 2 restricted to it).  K_d x_k and K_o x_k come from one pass of the operator
+// that defines the solve (double-float in mixed mode), so G is exact to rounding and
+// its nearly singular directions (the extrapolation in w) survive; its residual
+// r0 = b(w) - sum_k c_k (K_o + w K_d) x_k needs no further operator pass.
+static int warm_galerkin(rve_mesh m, int B, const double* w_host, bool mixed, cudaStream_t s, WarmStart& ws,
+                         bool& used) {
+    used = false;
+    const std::vector<double>& pw = m->warm_w[0];
+    const int Bp = m->warm_cols[0] / 6;
+    FieldDev& f = m->mech;
+    if (Bp < 1 || (int)pw.size() != Bp || !m->bph_valid[0] || B < 1 || f.m != 0) return RVE_OK;
+    const int64_t n_rows = f.n_rows;
+    const double deg[2] = {ws.degrade[0], ws.degrade[1]};
+    auto sph = [&](double w, int ph) { return deg[ph] != 0.0 ? w : 1.0; };
+    // the operator of a mixed solve scales the phases by the FP32 column scales (the
+    // right-hand side by the FP64 ones)
+    auto wop = [&](double w) { return mixed ? (double)(float)w : w; };
+    // sources: ns previous RVEs spread evenly over the previous batch's range of the
+    // factor (its ends included), so that their span holds the line through the ends
+    std::vector<int> ord(Bp);
+    for (int q = 0; q < Bp; ++q) ord[q] = q;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return pw[a] < pw[b]; });
+    const int ns = std::min(WARM_GALERKIN, Bp), kc = 6 * ns, k2 = 2 * kc;
+    std::vector<int32_t> src(ns);
+    for (int k = 0; k < ns; ++k) src[k] = ord[ns > 1 ? (int)std::lround((double)k * (Bp - 1) / (ns - 1)) : 0];
+    // compact copy: columns h kc + 6 t + lc hold source t, load case lc, for h = 0 (the
+    // degraded phases' product) and h = 1 (the other phases')
+    std::vector<int32_t> omap((size_t)k2 * WARM_SOURCES, 0);
+    std::vector<double> ocoef((size_t)k2 * WARM_SOURCES, 0.0);
+    for (int h = 0; h < 2; ++h)
+        for (int t = 0; t < ns; ++t)
+            for (int lc = 0; lc < 6; ++lc) {
+                omap[(size_t)(h * kc + 6 * t + lc) * WARM_SOURCES] = 6 * src[t] + lc;
+                ocoef[(size_t)(h * kc + 6 * t + lc) * WARM_SOURCES] = 1.0;
+            }
+    RVE_TRY(upload(m->warm_src, src.data(), src.size(), s));
+    RVE_TRY(upload(m->warm_omap, omap.data(), omap.size(), s));
+    RVE_TRY(upload(m->warm_ocoef, ocoef.data(), ocoef.size(), s));
+    RVE_TRY(m->warm_xs64.ensure((size_t)n_rows * k2 * 8));
+    RVE_TRY(m->warm_xs.ensure((size_t)n_rows * k2 * 8));   // FP32 high and low words
+    RVE_TRY(m->warm_kx.ensure((size_t)n_rows * k2 * 8));
+    RVE_TRY(m->warm_klo.ensure((size_t)n_rows * k2 * 4));
+    double* xs64 = m->warm_xs64.as<double>();
+    float* xh = m->warm_xs.as<float>();
+    float* xl = xh + (size_t)n_rows * k2;
+    double* kx = m->warm_kx.as<double>();
+    float* klo = m->warm_klo.as<float>();
+    launch_combine_columns<double, double>(n_rows, k2, m->warm_cols[0], m->warm_omap.as<int32_t>(),
+                                           m->warm_ocoef.as<double>(), m->warm[0].as<double>(), xs64, s);
+    std::vector<float> sc((size_t)k2 * 2);
+    std::vector<double> nsc((size_t)k2 * 2);
+    for (int c = 0; c < k2; ++c)
+        for (int ph = 0; ph < 2; ++ph) {
+            const double v = c < kc ? deg[ph] : 1.0 - deg[ph];
+            sc[2 * c + ph] = (float)v;
+            nsc[2 * c + ph] = -v;
+        }
+    RVE_CUDA(cudaMemsetAsync(kx, 0, (size_t)n_rows * k2 * 8, s));
+    Solver sk(m, f, 2 * ns);
+    if (mixed) {
+        // kx + klo = -K_part (x_t + u_macro) in double-float; then + K_part u_macro
+        // from the cached per-phase loads (rhs_combine adds -(s0 y0 + s1 y1))
+        launch_split_d2ff((int64_t)n_rows * k2, xs64, xh, xl, s);
+        RVE_TRY(upload(m->warm_ksc, sc.data(), sc.size(), s));
+        RVE_TRY(upload(m->warm_phs, nsc.data(), nsc.size(), s));
+        RVE_CUDA(cudaMemsetAsync(klo, 0, (size_t)n_rows * k2 * 4, s));
+        launch_residual_df(m->p, f.nc, sk.ev<float>(m->warm_ksc), xh, xl, kx, klo, sk.L);
+        launch_axpy_f2d((int64_t)n_rows * k2, klo, kx, s);
+        launch_rhs_combine(n_rows, 2 * ns, m->bph[0].as<double>(), m->warm_phs.as<double>(), kx, s, true);
+    } else {
+        // FP64 operator with the scales -K_part
+        RVE_TRY(upload(m->warm_phs, nsc.data(), nsc.size(), s));
+        launch_operator<double>(m->p, f.nc, false, sk.ev<double>(m->warm_phs), xs64, kx, nullptr, sk.L);
+    }
+    const int splits = 16, nout = 2 * ns + 2;
+    RVE_TRY(m->warm_gram.ensure((size_t)splits * 6 * ns * nout * 8));
+    launch_warm_gram(n_rows, ns, m->warm_src.as<int32_t>(), m->warm_cols[0], m->warm[0].as<double>(), kx,
+                     m->bph[0].as<double>(), m->warm_gram.as<double>(), splits, s);
+    m->ctx->launches += 7;
+    std::vector<double> h((size_t)splits * 6 * ns * nout), P((size_t)6 * ns * nout, 0.0);
+    RVE_CUDA(cudaMemcpyAsync(h.data(), m->warm_gram.p, h.size() * 8, cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(cudaStreamSynchronize(s));
+    for (int sp = 0; sp < splits; ++sp)
+        for (size_t i = 0; i < P.size(); ++i) P[i] += h[(size_t)sp * P.size() + i];
+    const size_t n = (size_t)6 * B * WARM_SOURCES;
+    std::vector<int32_t> cmap(n, 0), kmap(n, 0);
+    std::vector<double> ccoef(n, 0.0), kcoef(n, 0.0);
+    for (int b = 0; b < B; ++b) {
+        const double w = w_host[b], wf = wop(w);
+        for (int lc = 0; lc < 6; ++lc) {
+            double G[WARM_GALERKIN * WARM_GALERKIN], g[WARM_GALERKIN], c[WARM_GALERKIN];
+            for (int p = 0; p < ns; ++p) {
+                const double* Pp = &P[((size_t)lc * ns + p) * nout];
+                g[p] = -(sph(w, 0) * Pp[2 * ns] + sph(w, 1) * Pp[2 * ns + 1]);
+                for (int t = 0; t < ns; ++t) G[p * ns + t] = -(Pp[ns + t] + wf * Pp[t]);   // x_p . (K_o + w K_d) x_t
+            }
+            // exact to rounding: directions below 1e-12 of the largest are noise
+            if (!galerkin_solve(ns, G, g, c, 1e-12)) return RVE_OK;   // the caller falls back to the polynomial
+            const int col = 6 * b + lc;
+            for (int k = 0; k < ns; ++k) {
+                const size_t i = (size_t)col * WARM_SOURCES + k;
+                cmap[i] = 6 * src[k] + lc;
+                ccoef[i] = c[k];
+                // r0 = b(w) + sum_k c_k (-K_o x_k) + sum_k c_k w (-K_d x_k)
+                kmap[i] = kc + 6 * k + lc;
+                kcoef[i] = c[k];
+                kmap[i + ns] = 6 * k + lc;
+                kcoef[i + ns] = c[k] * wf;
+            }
+        }
+    }
+    RVE_TRY(upload(m->warm_map, cmap.data(), n, s));
+    RVE_TRY(upload(m->warm_coef, ccoef.data(), n, s));
+    RVE_TRY(upload(m->warm_kxmap, kmap.data(), n, s));
+    RVE_TRY(upload(m->warm_dcoef, kcoef.data(), n, s));
+    ws.x = m->warm[0].as<double>();
+    ws.r = mixed ? m->warm_r[0].as<double>() : nullptr;
+    ws.cols = m->warm_cols[0];
+    ws.map = m->warm_map.as<int32_t>();
+    ws.coef = m->warm_coef.as<double>();
+    ws.dcoef = m->warm_dcoef.as<double>();
+    ws.alpha.assign((size_t)6 * B, 0.0);
+    ws.nkx = kx;
+    ws.kx_cols = k2;
+    ws.kx_map = m->warm_kxmap.as<int32_t>();
+    ws.ph_coef = nullptr;
+    used = true;
+    return RVE_OK;
+}
+
 // Solve B RVEs of one mesh whose degradation factors are in d_w (device).
 int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, double* K, double* D,
                           rve_stats* st, const double* w_host) {
@@ -1116,6 +1352,11 @@ int rve::homogenise_batch(rve_mesh m, int B, const double* d_w, double* C, doubl
         ws.degrade[1] = (f == 0 && m->deg.apply_to_yarn) ? 1.0 : 0.0;
         // a field that does not degrade has one solution for every w: the nearest will do
         const bool degrades = ws.degrade[0] != 0.0 || ws.degrade[1] != 0.0;
+        if (f == 0 && degrades && m->ctx->opt.warm_start >= 4 && m->bph_prec[0] == prec) {
+            bool used = false;
+            RVE_TRY(warm_galerkin(m, B, w_host, mixed, s, ws, used));
+            if (used) return RVE_OK;
+        }
         const int order = degrades ? std::max(1, std::min(m->ctx->opt.warm_start, WARM_SOURCES)) : 1;
         const size_t n = (size_t)6 * B * WARM_SOURCES;
         std::vector<int32_t> cmap(n, 0);
@@ -1296,7 +1537,7 @@ void rve_default_options(rve_options* o) {
     o->batch = 0;
     o->stream = nullptr;
     o->profile = 0;
-    o->warm_start = 2;
+    o->warm_start = 4;
     o->transport_once = 0;
     o->operator_kernel = 0;
     o->deterministic = 0;

@@ -232,9 +232,14 @@ struct rve_mesh_s {
     rve::DevBuf x64f[2], r64f[2];
     rve::DevBuf b64, p64, q64, x32, r32, p32, q32;
     rve::DevBuf epart, rzp, cpart, gpart, mpart, gsum, msum;
-    rve::DevBuf colstate, scale64, scale32, wdev;
+    rve::DevBuf colstate, scale64, scale32, wdev, colmask;
     // warm start: the previous batch's FP64 solutions per field and their factors
     rve::DevBuf warm[2], warm_r[2], warm_map, warm_coef, warm_dcoef;
+    // energy-optimal warm start: source list, one-hot map of the compact source copy,
+    // the sources in FP32 and -K_deg of them, their inner products, the column map into
+    // the compact products and the per-column macro-load coefficients
+    rve::DevBuf warm_src, warm_omap, warm_ocoef, warm_ksc, warm_phs, warm_xs64, warm_xs, warm_kx, warm_klo, warm_gram,
+        warm_kxmap, warm_phcoef;
     rve::DevBuf dscale32, dscale64;   // per-column phase scales of the warm-start residual
     // per field: K_ph u_macro for each phase at unit modulus, [2][n_rows][6] (FP64),
     // so that a batch's right-hand side is a per-column combination of them

@@ -2033,13 +2033,13 @@ void launch_scatter_results(int B, const int64_t* idx, const double* res, double
     k_scatter_results<<<B, 64, 0, s>>>(B, idx, res, C, K, D, status);
 }
 
-// x[row][col] = src[row][map[col]]  (warm start from a previous batch's solution)
 // x[:, col] = sum_k coef[col][k] src[:, map[col][k]] over WARM_SOURCES previous
-// solutions (a polynomial in the degradation factor through them), stored as TO
-template <typename TO>
+// solutions (warm starts: a polynomial in the degradation factor through them, or
+// their energy-optimal combination), read as TI and stored as TO
+template <typename TI, typename TO>
 __global__ void k_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* __restrict__ map,
-                                  const double* __restrict__ coef, const double* __restrict__ src,
-                                  TO* __restrict__ x) {
+                                  const double* __restrict__ coef, const TI* __restrict__ src,
+                                  TO* __restrict__ x, int accumulate) {
     const int64_t n = n_rows * ncols;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = i / ncols;
@@ -2048,24 +2048,78 @@ __global__ void k_combine_columns(int64_t n_rows, int ncols, int src_cols, const
 #pragma unroll
         for (int k = 0; k < WARM_SOURCES; ++k) {
             const double c = coef[col * WARM_SOURCES + k];
-            if (c != 0.0) v = fma(c, src[row * src_cols + map[col * WARM_SOURCES + k]], v);
+            if (c != 0.0) v = fma(c, (double)src[row * src_cols + map[col * WARM_SOURCES + k]], v);
         }
-        x[i] = (TO)v;
+        x[i] = accumulate ? (TO)((double)x[i] + v) : (TO)v;
     }
 }
 
-template <typename TO>
+template <typename TI, typename TO>
 void launch_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* coef,
-                            const double* src, TO* x, cudaStream_t s) {
+                            const TI* src, TO* x, cudaStream_t s, bool accumulate) {
     int64_t b = (n_rows * ncols + 255) / 256;
     if (b > sm_count() * 16) b = sm_count() * 16;
     if (b < 1) b = 1;
-    k_combine_columns<TO><<<(unsigned)b, 256, 0, s>>>(n_rows, ncols, src_cols, map, coef, src, x);
+    k_combine_columns<TI, TO><<<(unsigned)b, 256, 0, s>>>(n_rows, ncols, src_cols, map, coef, src, x,
+                                                          accumulate ? 1 : 0);
 }
-template void launch_combine_columns<double>(int64_t, int, int, const int32_t*, const double*, const double*,
-                                             double*, cudaStream_t);
-template void launch_combine_columns<float>(int64_t, int, int, const int32_t*, const double*, const double*,
-                                            float*, cudaStream_t);
+template void launch_combine_columns<double, double>(int64_t, int, int, const int32_t*, const double*,
+                                                     const double*, double*, cudaStream_t, bool);
+template void launch_combine_columns<double, float>(int64_t, int, int, const int32_t*, const double*,
+                                                    const double*, float*, cudaStream_t, bool);
+
+// Inner products of the energy-optimal warm start, per load case lc and source p
+// (ns sources, the columns 6 src[p] + lc of the previous batch): x_p . k_t and
+// x_p . k'_t (t < ns; k_t, k'_t minus the degraded and the other phases' operator on
+// source t, FP64, compact [n_rows][12 ns] with the k' columns from 6 ns on) and
+// x_p . y_ph (the unit-modulus macro load of phase ph, [2][n_rows][6]).
+// Block (lc * ns + p, split) sums its rows; out[split][lc][p][2 ns + 2].
+__global__ void __launch_bounds__(256) k_warm_gram(int64_t n_rows, int ns, const int32_t* __restrict__ src,
+                                                   int src_cols, const double* __restrict__ X,
+                                                   const double* __restrict__ Kc, const double* __restrict__ Y,
+                                                   double* __restrict__ out) {
+    const int lc = blockIdx.x / ns, p = blockIdx.x % ns;
+    const int nout = 2 * ns + 2, kst = 12 * ns;
+    double am[WARM_GALERKIN], ay[WARM_GALERKIN], ay0 = 0.0, ay1 = 0.0;
+#pragma unroll
+    for (int t = 0; t < WARM_GALERKIN; ++t) am[t] = ay[t] = 0.0;
+    const int cp = 6 * src[p] + lc;
+    for (int64_t row = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; row < n_rows;
+         row += (int64_t)gridDim.y * blockDim.x) {
+        const double xp = X[row * src_cols + cp];
+#pragma unroll
+        for (int t = 0; t < WARM_GALERKIN; ++t)
+            if (t < ns) {
+                am[t] = fma(xp, Kc[row * kst + 6 * t + lc], am[t]);
+                ay[t] = fma(xp, Kc[row * kst + 6 * ns + 6 * t + lc], ay[t]);
+            }
+        ay0 = fma(xp, Y[row * 6 + lc], ay0);
+        ay1 = fma(xp, Y[n_rows * 6 + row * 6 + lc], ay1);
+    }
+    double* o = out + ((int64_t)blockIdx.y * 6 * ns + blockIdx.x) * nout;
+#pragma unroll
+    for (int t = 0; t < WARM_GALERKIN; ++t)
+        if (t < ns) {
+            const double a = block_sum(am[t]);
+            const double b = block_sum(ay[t]);
+            if (threadIdx.x == 0) {
+                o[t] = a;
+                o[ns + t] = b;
+            }
+        }
+    const double y0 = block_sum(ay0);
+    const double y1 = block_sum(ay1);
+    if (threadIdx.x == 0) {
+        o[2 * ns] = y0;
+        o[2 * ns + 1] = y1;
+    }
+}
+
+void launch_warm_gram(int64_t n_rows, int ns, const int32_t* src, int src_cols, const double* X, const double* Kc,
+                      const double* Y, double* out, int splits, cudaStream_t s) {
+    dim3 grid(6 * ns, splits);
+    k_warm_gram<<<grid, 256, 0, s>>>(n_rows, ns, src, src_cols, X, Kc, Y, out);
+}
 
 // b[row][6r + c] = -(s0 y0[row][c] + s1 y1[row][c]) with the column's phase scales
 __global__ void k_rhs_combine(int64_t n_rows, int nrve, const double* __restrict__ y,
@@ -2089,6 +2143,24 @@ void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double*
     if (blocks < 1) blocks = 1;
     k_rhs_combine<<<(unsigned)blocks, 256, 0, s>>>(n_rows, nrve, y, scale, b, accumulate ? 1 : 0);
 }
+
+// v[row][col] = 0 for the columns with mask[col] != 0 (columns already converged)
+template <typename T>
+__global__ void k_zero_columns(int64_t n_rows, int ncols, const int32_t* __restrict__ mask, T* __restrict__ v) {
+    const int64_t n = n_rows * ncols;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (mask[i % ncols]) v[i] = T(0);
+}
+
+template <typename T>
+void launch_zero_columns(int64_t n_rows, int ncols, const int32_t* mask, T* v, cudaStream_t s) {
+    int64_t b = (n_rows * ncols + 255) / 256;
+    if (b > sm_count() * 16) b = sm_count() * 16;
+    if (b < 1) b = 1;
+    k_zero_columns<T><<<(unsigned)b, 256, 0, s>>>(n_rows, ncols, mask, v);
+}
+template void launch_zero_columns<float>(int64_t, int, const int32_t*, float*, cudaStream_t);
+template void launch_zero_columns<double>(int64_t, int, const int32_t*, double*, cudaStream_t);
 
 // ---------------------------------------------------------- elementwise
 __global__ void k_cast_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {

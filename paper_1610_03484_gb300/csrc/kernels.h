@@ -178,10 +178,17 @@ void launch_scatter_results(int B, const int64_t* idx, const double* res, double
                             int32_t* status, cudaStream_t s);
 
 // previous solutions combined per column (warm starts); map and coef are [ncols][WARM_SOURCES]
-constexpr int WARM_SOURCES = 3;
-template <typename TO>
+constexpr int WARM_SOURCES = 8;
+constexpr int WARM_GALERKIN = 4;   // previous solutions spanning the energy-optimal start
+template <typename TI, typename TO>
 void launch_combine_columns(int64_t n_rows, int ncols, int src_cols, const int32_t* map, const double* coef,
-                            const double* src, TO* x, cudaStream_t s);
+                            const TI* src, TO* x, cudaStream_t s, bool accumulate = false);
+// inner products of the energy-optimal warm start (ns <= WARM_GALERKIN sources of the
+// previous batch, columns 6 src[p] + lc): out[split][lc][p][t] for t < ns x_p . Kc_t,
+// t in [ns, 2 ns) x_p . Kc_{6 ns + (t - ns)} (Kc: [n_rows][12 ns], the degraded and the
+// other phases' products), then x_p . Y_0 and x_p . Y_1
+void launch_warm_gram(int64_t n_rows, int ns, const int32_t* src, int src_cols, const double* X,
+                      const double* Kc, const double* Y, double* out, int splits, cudaStream_t s);
 
 // r_hi + r_lo += -K32 (x_h + x_l + u_macro) in double-float arithmetic (FP32 element
 // data; x_h = nullptr: x = 0); the caller adds r_lo (FP32) into r_hi (FP64) afterwards
@@ -203,6 +210,9 @@ void launch_beta_compact_continue(ColState cs, int ncols, cudaGraphConditionalHa
 void launch_compact_continue(const int32_t* active, int ncols, int32_t* list, int32_t* n_list,
                              cudaGraphConditionalHandle h, int32_t* counter, int max_iter, cudaStream_t s);
 
+// v[:, col] = 0 where mask[col] != 0
+template <typename T>
+void launch_zero_columns(int64_t n_rows, int ncols, const int32_t* mask, T* v, cudaStream_t s);
 // right-hand sides of a batch from the per-phase macro loads y = [2][n_rows][6]:
 // b = -(scale_0 y_0 + scale_1 y_1) per column (accumulate: b += that instead)
 void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,

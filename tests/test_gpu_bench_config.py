@@ -1,7 +1,7 @@
 """Parity at the benchmark's own settings: the batched mixed-precision path
 with the tolerances bench.py times (true-residual rtol 1e-5, inner rtol 5e-6),
-warm-started batches (the line in the degradation factor through the previous
-batch's solutions) of the size the batch-size autotuner picks, on Gauss points
+warm-started batches (the energy-optimal combination of the previous batch's
+solutions, bench.WARM_START) of the size the batch-size autotuner picks, on Gauss points
 from the benchmark's seeded draw, against the FP64 oracle (<= 1e-6 per tensor,
 the mixed-precision bound), for all six size/order classes of the workload.
 
@@ -67,7 +67,7 @@ def test_bench_settings_match_oracle_all_classes():
     jobs, results = {}, {}
     try:
         with rve.Context(precision=rve.PREC_MIXED, rtol=bench.RTOL, inner_rtol=bench.INNER_RTOL,
-                         max_refine=4, warm_start=2) as ctx:
+                         max_refine=4, warm_start=bench.WARM_START) as ctx:
             for (si, p) in classes:
                 grid = ri.SIZE_CLASSES[si]
                 xyz, tets, phase, tangent = ri.weave_rve(*grid)

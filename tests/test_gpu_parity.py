@@ -202,13 +202,14 @@ def test_error_codes(rve, ctx64):
 
 def test_warm_started_batches_match_cold_and_oracle(rve):
     """Batches ordered by degradation factor and started from the previous
-    batch's solutions (nearest, line, parabola in the factor) give the same
-    tensors as cold starts (and the oracle)."""
+    batch's solutions (nearest, line, parabola in the factor, and the
+    energy-optimal combination of up to four of them) give the same tensors as
+    cold starts (and the oracle)."""
     grid, p = (6, 6, 4), 2
     xyz, tets, phase, tangent = ri.weave_rve(*grid)
     T, c, t, _, _ = ri.gauss_point_states(24, seed=9)
     out = {}
-    for warm in (0, 1, 2, 3):
+    for warm in (0, 1, 2, 3, 4):
         with rve.Context(precision=rve.PREC_MIXED, rtol=1e-7, inner_rtol=1e-6, batch=4, warm_start=warm) as ctx:
             mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
             mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
@@ -217,14 +218,41 @@ def test_warm_started_batches_match_cold_and_oracle(rve):
             assert (st == 0).all()
             out[warm] = (Cb, Kb, Db, stats)
             mesh.free()
-    for warm in (1, 2, 3):
+    for warm in (1, 2, 3, 4):
         for a, b in zip(out[warm][:3], out[0][:3]):
             for g in range(24):
                 assert rel(a[g], b[g]) < 1e-6
     for g in (0, 11, 23):
         w = float(mt.one_minus_omega(T[g], c[g], t[g]))
         Co, Ko, Do = oracle_tensors(xyz, tets, grid, p, 1, phase, tangent, w)
-        for warm in (1, 3):
+        for warm in (1, 3, 4):
             assert rel(out[warm][0][g], Co) < TOL_MIXED
             assert rel(out[warm][1][g], Ko) < TOL_MIXED
             assert rel(out[warm][2][g], Do) < TOL_MIXED
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_energy_optimal_warm_start(rve, prec):
+    """warm_start = 4 on a 12x12x6 p = 2 weave, 48 points in batches of 8: the
+    tensors equal the cold-started ones to the solver tolerance, and the
+    Galerkin start needs fewer operator launches than the line in w."""
+    grid, p = (12, 12, 6), 2
+    xyz, tets, phase, tangent = ri.weave_rve(*grid)
+    T, c, t, _, _ = ri.gauss_point_states(48, seed=21)
+    out = {}
+    rtol = 1e-10 if prec == 0 else 1e-6
+    for warm in (0, 2, 4):
+        with rve.Context(precision=prec, rtol=rtol, inner_rtol=5e-7, batch=8, warm_start=warm) as ctx:
+            mesh = ctx.mesh_load(xyz, tets, p, phase, tangent)
+            mesh.set_materials(ri.NOMINAL_MATRIX, ri.NOMINAL_YARN)
+            mesh.set_bc(1)
+            Cb, Kb, Db, st, stats, rc = ctx.macro_update([mesh], T, c, t, np.zeros(48, np.int32))
+            assert (st == 0).all()
+            out[warm] = (Cb, Kb, Db, stats)
+            mesh.free()
+    tol = 1e-8 if prec == 0 else 1e-5
+    for warm in (2, 4):
+        for a, b in zip(out[warm][:3], out[0][:3]):
+            for g in range(48):
+                assert rel(a[g], b[g]) < tol
+    assert out[4][3]["kernel_launches"] < out[2][3]["kernel_launches"], (out[4][3], out[2][3])
