@@ -570,7 +570,7 @@ struct Solver {
 
     template <typename T>
     int pcg(T* x, T* r, T* p, T* q, const DevBuf& scale, double tol, int max_iter, int& iters_out,
-            bool& conv) {
+            bool& conv, const std::vector<double>* tolc = nullptr) {
         // profile mode launches one iteration at a time so that the byte and flop
         // counts follow the set of columns still iterating
         const bool prof = m->ctx->opt.profile != 0;
@@ -603,6 +603,11 @@ struct Solver {
         launch_schur<T>(rvw, cs, L);
         launch_update<T>(rvw, x, r, p, q, cs, m->rzp.as<double>(), false, L, m->cpart.as<double>());
         launch_finalize_beta(f.m, m->rzp.as<double>(), m->cpart.as<double>(), cs, true, L);
+        if (tolc) {
+            RVE_TRY(upload(m->coltol, tolc->data(), tolc->size(), s));
+            launch_column_tol(ncols, m->coltol.as<double>(), cs, s);
+            *launches += 1;
+        }
         launch_compact_active(cs.active, ncols, cs.list, cs.n_list, s);
         launch_pupdate<T>(rvw, r, p, q, cs, true, L);
         *launches += 6;
@@ -854,26 +859,17 @@ struct Solver {
         return RVE_OK;
     }
 
-    // Columns whose relative residual (last rel_residual) is already below half the
-    // tolerance take no part in the next solve: their residual in the solve's input v
-    // is zeroed, so the PCG starts them inactive instead of driving an already
-    // converged residual down into rounding (where p.Kp can lose its sign).
+    // per-column relative residuals of the last rel_residual call
     std::vector<double> last_rel;
-    template <typename T>
-    int skip_converged(T* v, double rtol) {
-        if ((int)last_rel.size() != ncols) return RVE_OK;
-        std::vector<int32_t> mask(ncols, 0);
-        bool any = false;
-        for (int c = 0; c < ncols; ++c)
-            if (last_rel[c] <= 0.5 * rtol) {
-                mask[c] = 1;
-                any = true;
-            }
-        if (!any) return RVE_OK;
-        RVE_TRY(upload(m->colmask, mask.data(), mask.size(), s));
-        launch_zero_columns<T>(n_rows, ncols, m->colmask.as<int32_t>(), v, s);
-        *launches += 1;
-        return RVE_OK;
+
+    // Per-column tolerances of an FP64 solve: a column already at rtol takes no part
+    // (tolerance 1), the others are reduced by rtol / rel_c, so that no column whose
+    // start is much better than the worst is driven down into rounding.
+    std::vector<double> column_tolerances(double rtol) const {
+        std::vector<double> t(ncols, 1.0);
+        for (int c = 0; c < ncols && c < (int)last_rel.size(); ++c)
+            if (last_rel[c] > rtol) t[c] = rtol / last_rel[c];
+        return t;
     }
 
     // warm: optional starting data from the previous batch (see WarmStart).
@@ -979,15 +975,17 @@ struct Solver {
             RVE_CUDA(cudaMemcpyAsync(r64, b64, nv * 8, cudaMemcpyDeviceToDevice, s));
             RVE_CUDA(cudaMemsetAsync(x64, 0, nv * 8, s));
             RVE_TRY(zero_noise_columns());
+            last_rel.assign(ncols, 1.0);
+            for (int c : zero_cols) last_rel[c] = 0.0;
         }
         out.rel_res = rel;
         if (!mixed) {
             if (rel > o.rtol) {
                 int its = 0;
                 bool conv = false;
-                RVE_TRY(skip_converged<double>(r64, o.rtol));   // r64 is recomputed after the solve
+                const std::vector<double> tolc = column_tolerances(o.rtol);
                 RVE_TRY(pcg<double>(x64, r64, m->p64.as<double>(), m->q64.as<double>(), m->scale64,
-                                    o.rtol / rel, o.max_iter, its, conv));
+                                    o.rtol / rel, o.max_iter, its, conv, &tolc));
                 out.iterations = its;
                 RVE_TRY(residual64(x64, r64));
                 RVE_TRY(zero_noise_columns());
@@ -1011,7 +1009,6 @@ struct Solver {
                     launch_cast_d2f((int64_t)nv, r64, r32, s);
                     RVE_CUDA(cudaMemsetAsync(x32, 0, nv * 4, s));
                     *launches += 1;
-                    RVE_TRY(skip_converged<float>(r32, o.rtol));
                     int its = 0;
                     bool conv = false;
                     RVE_TRY(pcg<float>(x32, r32, m->p32.as<float>(), m->q32.as<float>(), m->scale32,

@@ -232,7 +232,7 @@ struct rve_mesh_s {
     rve::DevBuf x64f[2], r64f[2];
     rve::DevBuf b64, p64, q64, x32, r32, p32, q32;
     rve::DevBuf epart, rzp, cpart, gpart, mpart, gsum, msum;
-    rve::DevBuf colstate, scale64, scale32, wdev, colmask;
+    rve::DevBuf colstate, scale64, scale32, wdev, coltol;
     // warm start: the previous batch's FP64 solutions per field and their factors
     rve::DevBuf warm[2], warm_r[2], warm_map, warm_coef, warm_dcoef;
     // energy-optimal warm start: source list, one-hot map of the compact source copy,

@@ -1555,6 +1555,22 @@ void launch_finalize_beta(int m, const double* rz_partial, const double* c_parti
                                                    first ? 1 : 0);
 }
 
+// Per-column tolerances: column c stops once rz <= tolc[c]^2 rz0, which the
+// convergence tests (rz <= tol^2 rz0 with the scalar tol) see through rz0 scaled
+// by (tolc[c] / tol)^2; a column with tolc[c] >= 1 has converged already and starts
+// inactive.  Runs after the initial residual's finalisation.
+__global__ void k_column_tol(int ncols, const double* __restrict__ tolc, ColState cs) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const double t = tolc[c] / *cs.tol;
+    cs.rz0[c] *= t * t;
+    if (tolc[c] >= 1.0) cs.active[c] = 0;
+}
+
+void launch_column_tol(int ncols, const double* tolc, ColState cs, cudaStream_t s) {
+    k_column_tol<<<(ncols + 127) / 128, 128, 0, s>>>(ncols, tolc, cs);
+}
+
 void launch_constraint_multipliers(int m, const double* c_partial, ColState cs, const Launch& L) {
     if (m == 0) return;
     k_finalize_beta<<<L.ncols, 256, 0, L.stream>>>(m, c_partial, c_partial, L.nby, L.ncols, cs, 2);
@@ -2143,24 +2159,6 @@ void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double*
     if (blocks < 1) blocks = 1;
     k_rhs_combine<<<(unsigned)blocks, 256, 0, s>>>(n_rows, nrve, y, scale, b, accumulate ? 1 : 0);
 }
-
-// v[row][col] = 0 for the columns with mask[col] != 0 (columns already converged)
-template <typename T>
-__global__ void k_zero_columns(int64_t n_rows, int ncols, const int32_t* __restrict__ mask, T* __restrict__ v) {
-    const int64_t n = n_rows * ncols;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        if (mask[i % ncols]) v[i] = T(0);
-}
-
-template <typename T>
-void launch_zero_columns(int64_t n_rows, int ncols, const int32_t* mask, T* v, cudaStream_t s) {
-    int64_t b = (n_rows * ncols + 255) / 256;
-    if (b > sm_count() * 16) b = sm_count() * 16;
-    if (b < 1) b = 1;
-    k_zero_columns<T><<<(unsigned)b, 256, 0, s>>>(n_rows, ncols, mask, v);
-}
-template void launch_zero_columns<float>(int64_t, int, const int32_t*, float*, cudaStream_t);
-template void launch_zero_columns<double>(int64_t, int, const int32_t*, double*, cudaStream_t);
 
 // ---------------------------------------------------------- elementwise
 __global__ void k_cast_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {

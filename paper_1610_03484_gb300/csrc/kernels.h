@@ -154,6 +154,9 @@ void launch_finalize_beta(int m, const double* rz_partial, const double* c_parti
 template <typename T>
 void launch_pupdate(const RowView<T>& rv, T* r, T* p, T* q, ColState cs, bool first,
                     const Launch& L);
+// per-column tolerances tolc [ncols] (after the initial finalisation): rz0 scaled by
+// (tolc / tol)^2, columns with tolc >= 1 inactive
+void launch_column_tol(int ncols, const double* tolc, ColState cs, cudaStream_t s);
 void launch_constraint_multipliers(int m, const double* c_partial, ColState cs, const Launch& L);
 // FP64 r projected in place; (r, M^-1 r) partials from the FP32 preconditioner view rv32
 void launch_project_residual(const RowView<double>& rv, const RowView<float>& rv32, double* r, ColState cs,
@@ -210,9 +213,6 @@ void launch_beta_compact_continue(ColState cs, int ncols, cudaGraphConditionalHa
 void launch_compact_continue(const int32_t* active, int ncols, int32_t* list, int32_t* n_list,
                              cudaGraphConditionalHandle h, int32_t* counter, int max_iter, cudaStream_t s);
 
-// v[:, col] = 0 where mask[col] != 0
-template <typename T>
-void launch_zero_columns(int64_t n_rows, int ncols, const int32_t* mask, T* v, cudaStream_t s);
 // right-hand sides of a batch from the per-phase macro loads y = [2][n_rows][6]:
 // b = -(scale_0 y_0 + scale_1 y_1) per column (accumulate: b += that instead)
 void launch_rhs_combine(int64_t n_rows, int nrve, const double* y, const double* scale, double* b,
