@@ -182,7 +182,7 @@ void launch_scatter_results(int B, const int64_t* idx, const double* res, double
 
 // previous solutions combined per column (warm starts); map and coef are [ncols][WARM_SOURCES]
 constexpr int WARM_SOURCES = 8;
-constexpr int WARM_GALERKIN = 4;   // previous solutions spanning the energy-optimal start
+constexpr int WARM_GALERKIN = 3;   // previous solutions spanning the energy-optimal start
 // the energy-optimal start's residual map holds two entries per source in a column's row
 static_assert(2 * WARM_GALERKIN <= WARM_SOURCES, "WARM_SOURCES must hold 2 * WARM_GALERKIN entries");
 template <typename TI, typename TO>
