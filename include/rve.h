@@ -85,7 +85,7 @@ typedef struct rve_options {
                                 their degradation factor and starts every batch from the previous
                                 batch of the same call: 1 the nearest solution, 2 the line and 3
                                 the parabola in the factor through 2 or 3 of them, 4 (default)
-                                the energy-optimal (Galerkin) combination of up to four of them
+                                the energy-optimal (Galerkin) combination of up to three of them
                                 for the mechanics without constraint rows (one operator pass over
                                 the sources and a few inner products per batch; otherwise the
                                 parabola, and the transport fields take the nearest);
