@@ -358,7 +358,6 @@ struct WarmStart {
     const double* nkx = nullptr;
     int kx_cols = 0;
     const int32_t* kx_map = nullptr;   // [ncols][WARM_SOURCES]
-    const double* ph_coef = nullptr;   // unused by the energy-optimal start
 };
 
 struct Solver {
@@ -1321,7 +1320,6 @@ static int warm_galerkin(rve_mesh m, int B, const double* w_host, bool mixed, cu
     ws.nkx = kx;
     ws.kx_cols = k2;
     ws.kx_map = m->warm_kxmap.as<int32_t>();
-    ws.ph_coef = nullptr;
     used = true;
     return RVE_OK;
 }

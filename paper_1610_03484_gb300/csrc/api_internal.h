@@ -236,10 +236,12 @@ struct rve_mesh_s {
     // warm start: the previous batch's FP64 solutions per field and their factors
     rve::DevBuf warm[2], warm_r[2], warm_map, warm_coef, warm_dcoef;
     // energy-optimal warm start: source list, one-hot map of the compact source copy,
-    // the sources in FP32 and -K_deg of them, their inner products, the column map into
-    // the compact products and the per-column macro-load coefficients
+    // the phase scales of the product pass (FP32 and negated FP64), the sources (FP64 and
+    // split into FP32 high and low words), minus the degraded and the other phases'
+    // products of them (FP64 plus FP32 low words), their inner products, and the column
+    // map of r0 into the products
     rve::DevBuf warm_src, warm_omap, warm_ocoef, warm_ksc, warm_phs, warm_xs64, warm_xs, warm_kx, warm_klo, warm_gram,
-        warm_kxmap, warm_phcoef;
+        warm_kxmap;
     rve::DevBuf dscale32, dscale64;   // per-column phase scales of the warm-start residual
     // per field: K_ph u_macro for each phase at unit modulus, [2][n_rows][6] (FP64),
     // so that a batch's right-hand side is a per-column combination of them
