@@ -105,7 +105,7 @@ void bounds_begin(cudaStream_t s) {
     bounds_reset();
 }
 
-int bounds_verdict(int rc, cudaStream_t s) {
+int bounds_outcome(int rc, cudaStream_t s) {
     if (!bounds_check_built()) return rc;
     cudaStreamSynchronize(s);
     unsigned long long n = 0;
@@ -1883,7 +1883,7 @@ int rve_homogenise(rve_ctx c, rve_mesh m, double* C, double* K, double* D, rve_s
     const ProfCounters pc0 = c->prof;
     int rc = homogenise_batch(m, 1, d + 3, C, K, D, st);
     RVE_CUDA(cudaStreamSynchronize(s));
-    rc = bounds_verdict(rc, s);
+    rc = bounds_outcome(rc, s);
     if (st) {
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st->kernel_launches = c->launches - l0;
@@ -2299,7 +2299,7 @@ int macro_update_gauss_points_dev(rve_ctx c, const rve_mesh* meshes, int n_meshe
     const ProfCounters pc0 = c->prof;
     int rc = macro_update_impl(c, meshes, n_meshes, G, T_dev, c_dev, t_dev, mesh_id_host, C_dev, K_dev,
                                D_dev, status_dev, st);
-    rc = bounds_verdict(rc, c->stream);
+    rc = bounds_outcome(rc, c->stream);
     if (st) {
         cudaStreamSynchronize(c->stream);
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -2360,7 +2360,7 @@ int macro_update_gauss_points_w_dev(rve_ctx c, const rve_mesh* meshes, int n_mes
     const ProfCounters pc0 = c->prof;
     int rc = macro_update_impl(c, meshes, n_meshes, G, nullptr, nullptr, nullptr, mesh_id_host, C_dev, K_dev,
                                D_dev, status_dev, st, W_dev);
-    rc = bounds_verdict(rc, c->stream);
+    rc = bounds_outcome(rc, c->stream);
     if (st) {
         cudaStreamSynchronize(c->stream);
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
