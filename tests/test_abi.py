@@ -54,3 +54,31 @@ def test_no_device_is_reported_not_faked(lib):
 def test_strerror(lib):
     assert lib.rve_strerror(-2) == b"bad mesh"
     assert lib.rve_strerror(0) == b"ok"
+
+
+def test_default_options_agree_with_header_binding_and_bench(lib):
+    """rve_default_options (no GPU needed) gives the defaults the header documents,
+    the Python binding's keyword defaults repeat them, and the struct layouts agree."""
+    import inspect
+
+    import ctypes as C
+    import paper_1610_03484_gb300 as pkg
+    o = pkg.default_options()
+    assert C.sizeof(o) == C.sizeof(pkg.Options)
+    documented = {}
+    hdr = open(os.path.join(ROOT, "include", "rve.h")).read()
+    body = hdr[hdr.index("typedef struct rve_options"):hdr.index("} rve_options;")]
+    for name, default in re.findall(r"\b(\w+);\s*/\*(?:(?!\*/).)*?\(default ([0-9.e+-]+)\)", body, flags=re.S):
+        documented[name] = float(default)
+    for name in ("device", "rtol", "max_iter", "inner_rtol", "max_refine"):
+        assert name in documented, name
+    for name, v in documented.items():
+        assert getattr(o, name) == pytest.approx(v), name
+    # warm_start's default is documented as "4 (default)" inside its list of modes
+    assert re.search(r"4 \(default\)", body[body.index("warm_start"):])
+    assert o.warm_start == 4 and o.precision == pkg.PREC_FP64 and o.deterministic == 0
+    sig = inspect.signature(pkg.Context.__init__).parameters
+    for name in ("rtol", "max_iter", "inner_rtol", "max_refine", "check_every", "batch", "warm_start"):
+        assert sig[name].default == getattr(o, name), name
+    import bench
+    assert bench.WARM_START == o.warm_start
