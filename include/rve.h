@@ -632,6 +632,16 @@ int rve_debug_bounds(rve_ctx ctx, int32_t* checking_build, int64_t* violations, 
  * while every access that does run stays inside the mesh's arrays. */
 int rve_debug_set_node_bound(rve_ctx ctx, rve_mesh mesh, int64_t n_nodes);
 
+/* The small solve of the energy-optimal warm start (warm_start = 4): the energy
+ * minimisation of Sec. 2 restricted to the span of n previous solutions gives
+ * G c = g with G_pk = x_p . A x_k and g_p = x_p . b.  c = G^+ g for the symmetric part
+ * of G (n x n, row-major), by cyclic Jacobi rotations, with the eigenvalues at or
+ * below rel times the largest dropped.  Host only: needs no context and no device.
+ * RVE_ERR_INVALID_ARGUMENT for n outside [1, 8], a null pointer or rel < 0;
+ * RVE_ERR_NUMERIC (c untouched) when G has a non-finite entry, no positive
+ * eigenvalue, or the result is not finite. */
+int rve_debug_galerkin_solve(int n, const double* G, const double* g, double rel, double* c);
+
 #ifdef __cplusplus
 }
 #endif

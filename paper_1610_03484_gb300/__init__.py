@@ -178,6 +178,7 @@ _SIGS = {
     "rve_debug_bounds": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int32), C.c_int]),
     "rve_debug_set_node_bound": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "rve_debug_galerkin_solve": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     "rve_operator_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                               C.c_void_p]),
     "rve_surrogate_create": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.POINTER(C.c_void_p)]),
@@ -238,6 +239,20 @@ def _check(rc: int, where: str, allow=()):
 
 def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def galerkin_solve(G, g, rel: float = 1e-12) -> np.ndarray:
+    """c = G^+ g as the energy-optimal warm start solves it (rve_debug_galerkin_solve);
+    host only."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    n = g.shape[0]
+    if G.shape != (n, n):
+        raise ValueError("G must be n x n with n = len(g)")
+    c = np.zeros(n)
+    _check(load_library().rve_debug_galerkin_solve(n, _ptr(G), _ptr(g), float(rel), _ptr(c)),
+           "rve_debug_galerkin_solve")
+    return c
 
 
 def default_options() -> Options:
@@ -662,7 +677,7 @@ class Mesh:
         _check(self.ctx.lib.rve_debug_set_node_bound(self.ctx.h, self.h, int(n_nodes)), "rve_debug_set_node_bound")
 
 
-__all__ = ["Context", "Mesh", "Surrogate", "RveError", "load_library", "exported_symbols", "BC_DIRICHLET", "BC_PERIODIC",
+__all__ = ["Context", "Mesh", "Surrogate", "RveError", "load_library", "exported_symbols", "galerkin_solve", "BC_DIRICHLET", "BC_PERIODIC",
            "BC_NEUMANN", "PREC_FP64", "PREC_MIXED", "Options", "Stats"]
 
 

@@ -1132,10 +1132,10 @@ static int warm_sources(const std::vector<double>& pw, double w, int order, int*
 }
 
 // c = G^+ g for a small symmetric positive semi-definite G (n <= WARM_SOURCES):
-// cyclic Jacobi rotations, eigenvalues below `rel` of the largest dropped (the
+// cyclic Jacobi rotations, eigenvalues at or below `rel` of the largest dropped (the
 // sources are nearly parallel, so G is close to singular, and its entries carry the
-// rounding of the FP32 operator products).  False if G has no positive eigenvalue or
-// a value is not finite.
+// rounding of the double-float operator products).  False if G has no positive
+// eigenvalue or a value is not finite.
 static bool galerkin_solve(int n, const double* Gin, const double* g, double* c, double rel) {
     double A[WARM_SOURCES][WARM_SOURCES], V[WARM_SOURCES][WARM_SOURCES];
     for (int i = 0; i < n; ++i)
@@ -1188,6 +1188,20 @@ static bool galerkin_solve(int n, const double* Gin, const double* g, double* c,
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(c[i])) return false;
     return true;
+}
+
+int rve_debug_galerkin_solve(int n, const double* G, const double* g, double rel, double* c) {
+    if (n < 1 || n > WARM_SOURCES || !G || !g || !c || !(rel >= 0.0)) {
+        set_error("rve_debug_galerkin_solve: invalid argument");
+        return RVE_ERR_INVALID_ARGUMENT;
+    }
+    double out[WARM_SOURCES];
+    if (!galerkin_solve(n, G, g, out, rel)) {
+        set_error("rve_debug_galerkin_solve: non-finite entry or no positive eigenvalue");
+        return RVE_ERR_NUMERIC;
+    }
+    for (int i = 0; i < n; ++i) c[i] = out[i];
+    return RVE_OK;
 }
 
 // Energy-optimal warm start of the mechanics (warm_start >= 4).  With A(w) = K_o + w
